@@ -1,0 +1,205 @@
+"""Pins of the oracle's four-level Maxwell-Bloch gain model and noise (no GPU).
+
+The lasing model (paper, Secs. "Sample and numerical approach" and "3+1D
+simulation of lasing": four-level system, three degenerate levels coupled to
+the three field components, external pump, spontaneous-emission noise) is
+checked against:
+
+* the rate matrix conserving sum N and the closed-form steady state;
+* zero field: the population relaxation against exp(t A) N(0) (scipy) and the
+  Bateman cascade solution, with second-order convergence of Crank-Nicolson;
+* a one-cell periodic box (no curl): the coupled E / P / N system against an
+  independent high-accuracy ODE integration of the continuum equations, with
+  second-order convergence, and exact conservation of D = eps_r E + P~;
+* Philox4x32-10 published known-answer vectors and Gaussian statistics.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.integrate
+import scipy.linalg
+import scipy.stats
+
+from oracle import C0, EPS0, HBAR, Oracle
+from oracle import gain as G
+from oracle.philox import gain_noise, philox4x32_10
+
+GAIN_BYTE = np.uint8(0b1101010)  # all three E components class 2, gain bit set
+
+
+def one_cell(courant, eps_sphere=2.25, **gain):
+    o = Oracle((1, 1, 1), 20, courant=courant, periodic=(True, True, True), eps=(1.0, 1.0, eps_sphere))
+    o.set_material(np.full((1, 1, 1), GAIN_BYTE))
+    o.set_gain(**gain)
+    return o
+
+
+def test_rate_matrix_and_equilibrium():
+    W, t32, t21, t10 = 3e10, 100e-15, 1e-9, 100e-15
+    A = G.rate_matrix(W, t32, t21, t10)
+    assert np.allclose(A.sum(axis=0), 0.0, atol=0)
+    Neq = G.equilibrium(1e24, W, t32, t21, t10)
+    assert abs(Neq.sum() - 1e24) < 1e24 * 1e-15
+    assert np.max(np.abs(A @ Neq)) < 1e24 * 1e-15 / t10
+    # flux balance around the cycle 0 -> 3 -> 2 -> 1 -> 0
+    assert math.isclose(W * Neq[0], Neq[3] / t32, rel_tol=1e-14)
+    assert math.isclose(Neq[3] / t32, Neq[2] / t21, rel_tol=1e-14)
+    assert math.isclose(Neq[2] / t21, Neq[1] / t10, rel_tol=1e-14)
+    # Crank-Nicolson keeps sum N: 1^T (M - I) = 0 and 1^T w = 0
+    MmI, w = G.crank_nicolson(A, 1e-17)
+    assert np.max(np.abs(MmI.sum(axis=0))) < 1e-18
+    assert abs(w.sum()) < 1e-15
+
+
+def _relax(courant, steps_time, W, taus):
+    o = one_cell(courant, n_total=1e24, fa_hat=0.8, dw_rel=0.02, tau32=taus[0], tau21=taus[1],
+                 tau10=taus[2], pump=W, init="ground")
+    nsteps = int(round(steps_time / o.dt))
+    o.step(nsteps)
+    return o.populations()[:, 0, 0, 0], nsteps * o.dt, o
+
+
+@pytest.mark.parametrize("W", [0.0, 2e12])
+def test_relaxation_matches_matrix_exponential(W):
+    taus = (100e-15, 300e-15, 50e-15)
+    t_end = 0.4e-12
+    N, t, o = _relax(0.5, t_end, W, taus)
+    A = G.rate_matrix(W, *taus)
+    ref = scipy.linalg.expm(t * A) @ np.array([1e24, 0, 0, 0])
+    err = np.max(np.abs(N - ref)) / 1e24
+    assert err < 1e-7
+    assert abs(N.sum() - 1e24) / 1e24 < 1e-13
+    # second-order convergence in dt
+    N2, t2, _ = _relax(0.25, t_end, W, taus)
+    ref2 = scipy.linalg.expm(t2 * A) @ np.array([1e24, 0, 0, 0])
+    err2 = np.max(np.abs(N2 - ref2)) / 1e24
+    if err > 1e-12:
+        assert 3.3 < err / err2 < 4.7
+
+
+def test_relaxation_bateman_cascade():
+    # all population in level 3, no pump: 3 -> 2 -> 1 -> 0 cascade in closed form
+    taus = (100e-15, 300e-15, 50e-15)
+    o = one_cell(0.5, n_total=1e24, fa_hat=0.8, dw_rel=0.02, tau32=taus[0], tau21=taus[1],
+                 tau10=taus[2], pump=0.0, init="steady")
+    # steady state without pump is the ground state; move everything to level 3
+    o.dN[:, 0, 0, 0] = np.array([-1e24, 0.0, 0.0, 1e24])
+    n = 9000
+    o.step(n)
+    t = n * o.dt
+    a, b, c = 1 / taus[0], 1 / taus[1], 1 / taus[2]
+    N3 = math.exp(-a * t)
+    N2 = a / (b - a) * (math.exp(-a * t) - math.exp(-b * t))
+    N1 = a * b * (math.exp(-a * t) / ((b - a) * (c - a)) + math.exp(-b * t) / ((a - b) * (c - b))
+                  + math.exp(-c * t) / ((a - c) * (b - c)))
+    ref = 1e24 * np.array([1 - N1 - N2 - N3, N1, N2, N3])
+    assert np.max(np.abs(o.populations()[:, 0, 0, 0] - ref)) / 1e24 < 1e-7
+
+
+def _zero_d_reference(t_end, eps_r, pars, drive):
+    """Continuum E/P/N equations of a uniform field (no curl), integrated by DOP853.
+
+    drive(t) is the source current term, in V/m per second, entering
+    eps_r dE/dt = -dP~/dt - drive(t).
+    """
+    omega_a = 2 * math.pi * pars["fa_hat"] * C0 / 480e-9
+    dw = pars["dw_rel"] * omega_a
+    kappa = G.default_kappa(omega_a, pars["tau21"])
+    A = G.rate_matrix(pars["pump"], pars["tau32"], pars["tau21"], pars["tau10"])
+    Neq = G.equilibrium(pars["n_total"], pars["pump"], pars["tau32"], pars["tau21"], pars["tau10"])
+
+    def rhs(t, y):
+        E, P, Q, N = y[0:3], y[3:6], y[6:9], y[9:13]   # P = P~ = P/eps0, Q = dP~/dt
+        dQ = -dw * Q - omega_a ** 2 * P + (kappa / EPS0) * (N[1] - N[2]) * E
+        dE = -(Q + drive(t)) / eps_r
+        R = EPS0 * float(E @ Q) / (HBAR * omega_a)
+        dN = A @ N + R * np.array([0.0, -1.0, 1.0, 0.0])
+        return np.concatenate([dE, Q, dQ, dN])
+
+    y0 = np.concatenate([np.zeros(9), Neq])
+    return scipy.integrate.solve_ivp(rhs, (0, t_end), y0, method="DOP853", rtol=1e-11, atol=1e-30,
+                                     dense_output=True, max_step=t_end / 400)
+
+
+@pytest.mark.parametrize("pump", [3e12, 1e8])
+def test_zero_dimensional_maxwell_bloch_against_ode(pump):
+    """Field driven from rest by a smooth pulse in a one-cell box with gain."""
+    pars = dict(n_total=1e24, fa_hat=0.8, dw_rel=0.02, tau32=100e-15, tau21=1e-9, tau10=100e-15, pump=pump)
+    rate = np.array([2e21, -3e21, 1e21])        # V/m/s: amplitude of the current term
+    f0_hat, bw = 0.8, 0.5
+    f0 = f0_hat * C0 / 480e-9
+    tau = math.sqrt(math.log(2)) / (math.pi * bw * f0)
+
+    def drive(t):
+        x = t - 5 * tau
+        return rate * math.exp(-x * x / (2 * tau * tau)) * math.sin(2 * math.pi * f0 * x)
+
+    t_end = 25e-15
+    errs, nerrs = [], []
+    for courant in (0.5, 0.25):
+        o = one_cell(courant, **pars, init="steady")
+        for c in range(3):
+            # amplitude is the per-step kick: rate * dt; pulse centred at 5 tau in steps
+            o.add_source(kind="point", comp=c, pos=(0, 0, 0), amplitude=rate[c] * o.dt, f0_hat=f0_hat, rel_bw=bw)
+        o.add_probe(0, 0, 0)
+        n = int(round(t_end / o.dt))
+        o.step(n)
+        sol = _zero_d_reference(n * o.dt, 2.25, pars, drive)
+        times = (np.arange(n) + 1) * o.dt
+        Eref = sol.sol(times)[0:3].T
+        Egot = o.probe_series()[:, 0, :]
+        errs.append(np.max(np.abs(Egot - Eref)) / np.max(np.abs(Eref)))
+        # D = eps_r E + P~ changes only through the source
+        g = np.array([o.sources[c]["w"][0, 0, 0] for c in range(3)])
+        from oracle import waveform
+        gsum = waveform(np.arange(n), f0_hat, bw, o.S, o.res).sum()
+        D = 2.25 * o.E[:, 0, 0, 0] + o.P[:, 0, 0, 0]
+        assert np.max(np.abs(D + g * gsum)) < 1e-9 * np.max(np.abs(g * gsum))
+        Nref = sol.y[9:13, -1]
+        dN_ref = Nref - G.equilibrium(1e24, pump, 100e-15, 1e-9, 100e-15)
+        nerrs.append(np.max(np.abs(o.dN[:, 0, 0, 0] - dN_ref)) / np.max(np.abs(dN_ref)))
+    assert errs[1] < 2e-3 and nerrs[1] < 2e-3
+    assert 3.3 < errs[0] / errs[1] < 4.7
+    # the stimulated-exchange rate is centred in time: populations converge at second order too
+    assert 3.3 < nerrs[0] / nerrs[1] < 4.7
+
+
+def test_philox_known_answers(golden_dir):
+    rows = []
+    with open(os.path.join(golden_dir, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(x, 16) for x in line.split()])
+    assert len(rows) == 3
+    for r in rows:
+        out = philox4x32_10(r[0:4], r[4:6])
+        assert [int(x) for x in out] == r[6:10]
+
+
+def test_noise_is_standard_normal():
+    xi = gain_noise(seed=12345, step=7, cells=np.arange(200000))
+    assert xi.shape == (3, 200000)
+    for c in range(3):
+        assert abs(xi[c].mean()) < 5 / math.sqrt(2e5)
+        assert abs(xi[c].var() - 1) < 5 * math.sqrt(2 / 2e5)
+        assert scipy.stats.kstest(xi[c], "norm").pvalue > 1e-4
+    # different steps and seeds give independent draws
+    xi2 = gain_noise(seed=12345, step=8, cells=np.arange(200000))
+    xi3 = gain_noise(seed=12346, step=7, cells=np.arange(200000))
+    assert abs(np.corrcoef(xi[0], xi2[0])[0, 1]) < 0.02
+    assert abs(np.corrcoef(xi[0], xi3[0])[0, 1]) < 0.02
+
+
+def test_noise_kick_statistics_in_gain_cells():
+    # with the field held at zero by a huge permittivity the kicks accumulate in P
+    o = Oracle((6, 5, 4), 20, periodic=(True, True, True), eps=(1.0, 1.0, 1e30))
+    o.set_material(np.full((4, 5, 6), GAIN_BYTE))
+    o.set_gain(n_total=1e24, fa_hat=0.8, dw_rel=0.02, tau32=100e-15, tau21=1e-9, tau10=100e-15,
+               pump=0.0, noise_amp=1e-6)
+    o.seed = 99
+    o.step(1)
+    xi = gain_noise(99, 0, np.arange(120))
+    got = o.P.transpose(0, 3, 2, 1).reshape(3, -1)
+    np.testing.assert_allclose(got, 1e-6 * xi, rtol=1e-15, atol=0)

@@ -1,0 +1,164 @@
+"""Pins of the oracle's flux, source, absorbing layer and rasterizer (no GPU).
+
+* Poynting flux T^n of a discrete travelling eigenmode through a plane has the
+  closed form  dx^2 N_faces E0^2 sqrt(eps_r) cos(k/2) cos(omega dt/2)
+  cos^2(k p - omega n) / eta0  (the transmitted power T(t) of Sec. "Dynamical
+  diffusion and localization" is this flux through the output face);
+* the source waveform has the stated centre frequency and power-spectrum FWHM
+  (single-cycle / 100 fs pulses of Secs. "Wide-band excitation" and
+  "Dynamical diffusion");
+* a soft source in a one-cell periodic box drives E = -(A/eps_r) sum_n g(n);
+* CPML reflection (the paper's absorbing layer, Sec. "Sample and numerical
+  approach"): a probe near the layer agrees with a run in a much larger box
+  to better than -40 dB until the outer box's echo returns;
+* rasterizer: brute force with scalar Python arithmetic on tiny grids equals the
+  oracle bit for bit; touching fcc spheres fill pi/(3 sqrt 2) = 0.7405 of space.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ETA0, Oracle, waveform
+from oracle.rasterize import rasterize
+from paper_0802_3775_gb300 import inputs
+
+
+@pytest.mark.parametrize("axis,pol,eps_r", [(2, 0, 1.0), (2, 1, 2.0), (0, 1, 1.0), (0, 2, 3.0), (1, 2, 1.0), (1, 0, 1.5)])
+def test_flux_of_travelling_eigenmode(axis, pol, eps_r):
+    shape = [5, 6, 7]
+    shape[axis] = 24
+    shape = tuple(shape)
+    o = Oracle(shape, 12, courant=0.5, periodic=(True, True, True), eps=(eps_r,) * 3)
+    S = o.S
+    kk = 2 * math.pi * 2 / shape[axis]
+    k = np.zeros(3); k[axis] = kk
+    K = 2 * np.sin(k / 2)
+    E_hat = np.zeros(3); E_hat[pol] = 1.7
+    Om = S * np.linalg.norm(K) / math.sqrt(eps_r)
+    w = 2 * math.asin(Om / 2)
+    H_hat = (S / Om) * np.cross(K, E_hat)
+    NODE = [(0.5, 0, 0), (0, 0.5, 0), (0, 0, 0.5), (0, 0.5, 0.5), (0.5, 0, 0.5), (0.5, 0.5, 0)]
+    for c in range(6):
+        X = np.meshgrid(*[np.arange(shape[d]) + NODE[c][d] for d in range(3)], indexing="ij")
+        ph = k[0] * X[0] + k[1] * X[1] + k[2] * X[2]
+        if c < 3:
+            o.E[c] = E_hat[c] * np.cos(ph)
+        else:
+            o.H[c - 3] = H_hat[c - 3] * np.cos(ph + 0.5 * w)
+    d1, d2 = (axis + 1) % 3, (axis + 2) % 3
+    p = 9
+    u = (1, shape[d1] - 2)
+    v = (0, shape[d2] - 1)
+    o.add_flux(axis, p, 1.0, u, v)
+    N = 120
+    o.step(N)
+    T = o.flux_series()[0]
+    nfaces = (u[1] - u[0]) * (v[1] - v[0])
+    n = np.arange(N)
+    ref = o.dx ** 2 * nfaces * 1.7 ** 2 * math.sqrt(eps_r) * math.cos(kk / 2) * math.cos(w / 2) * np.cos(kk * p - w * n) ** 2 / ETA0
+    np.testing.assert_allclose(T, ref, rtol=0, atol=1e-10 * np.max(np.abs(ref)))
+
+
+def test_waveform_centre_and_bandwidth():
+    S, res, f0_hat, bw = 0.5 / math.sqrt(3), 20, 0.8, 0.1
+    N = 1 << 16
+    g = waveform(np.arange(N), f0_hat, bw, S, res)
+    P = np.abs(np.fft.rfft(g)) ** 2
+    f = np.fft.rfftfreq(N)
+    f0 = f0_hat * S / res
+    i = int(np.argmax(P))
+    assert abs(f[i] - f0) / f0 < 0.01
+    half = P >= 0.5 * P[i]
+    lo = f[np.argmax(half)]
+    hi = f[len(half) - 1 - np.argmax(half[::-1])]
+    assert abs((hi - lo) / f0 - bw) / bw < 0.02
+    # pulse centred at t0 = 5 tau: the envelope is below 1e-5 at n = 0
+    tau = math.sqrt(math.log(2)) / (math.pi * bw * f0)
+    assert abs(g[0]) < math.exp(-12.4)
+    assert abs(np.argmax(np.abs(g)) + 0.5 - 5 * tau) < 1 / f0
+
+
+def test_soft_source_in_one_cell_box():
+    o = Oracle((1, 1, 1), 12, periodic=(True, True, True), eps=(1.0, 2.5, 1.0))
+    o.add_source(kind="point", comp=1, pos=(0, 0, 0), amplitude=3.0, f0_hat=0.8, rel_bw=0.5)
+    N = 700
+    o.step(N)
+    g = waveform(np.arange(N), 0.8, 0.5, o.S, 12)
+    assert abs(o.E[1, 0, 0, 0] - (-(3.0 / 2.5) * g.sum())) < 1e-12
+    assert o.E[0, 0, 0, 0] == 0.0 and o.E[2, 0, 0, 0] == 0.0
+
+
+@pytest.mark.slow
+def test_cpml_reflection_below_minus_40db():
+    res, npml, interior, pad = 10, 8, 20, 16
+
+    def run(n_extra):
+        n = interior + 2 * npml + 2 * n_extra
+        o = Oracle((n, n, n), res, npml=(npml,) * 6, eps=(1.0, 1.0, 1.0), cpml_f_hat=0.6)
+        c = n // 2
+        o.add_source(kind="point", comp=2, pos=(c, c, c), f0_hat=0.6, rel_bw=1.0)
+        # probe two cells inside the small box's absorbing layer boundary
+        o.add_probe(c, c, n_extra + npml + 2)
+        o.add_probe(n_extra + npml + 2, c + 3, c)
+        o.step(150)
+        return o.probe_series()
+
+    small = run(0)
+    big = run(pad)
+    err = np.max(np.abs(small - big))
+    ref = np.max(np.abs(big))
+    # the bar is -40 dB; this layer reaches about -80 dB, so a broken
+    # coefficient (which lands near the -20 dB of a bare PEC wall) cannot pass
+    assert 20 * math.log10(err / ref) < -60.0
+
+
+def _brute_force_material(shape, spheres, lo, hi):
+    nx, ny, nz = shape
+    offs = ((0.5, 0.0, 0.0), (0.0, 0.5, 0.0), (0.0, 0.0, 0.5), (0.5, 0.5, 0.5))
+    out = np.zeros((nz, ny, nx), dtype=np.uint8)
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                byte = 0
+                for s, (ox, oy, oz) in enumerate(offs):
+                    p = (i + ox, j + oy, k + oz)
+                    in_box = all(lo[d] <= p[d] < hi[d] for d in range(3))
+                    ins = False
+                    for (cx, cy, cz, r) in spheres:
+                        dx = p[0] - cx; dy = p[1] - cy; dz = p[2] - cz
+                        if (dx * dx + dy * dy) + dz * dz < r * r:
+                            ins = True
+                    if s < 3:
+                        byte |= ((2 if ins else 1) if in_box else 0) << (2 * s)
+                    elif ins and in_box:
+                        byte |= 64
+                out[k, j, i] = byte
+    return out
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_rasterizer_brute_force(seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = (7, 5, 6)
+    spheres = [(float(rng.uniform(-1, 8)), float(rng.uniform(-1, 6)), float(rng.uniform(-1, 7)), float(rng.uniform(0.5, 3)))
+               for _ in range(4)]
+    # a sphere whose surface passes exactly through sample points
+    spheres.append((2.0, 2.0, 2.0, 1.5))
+    lo, hi = (1, 0.5, 1), (6, 5, 5.5)
+    ref = _brute_force_material(shape, spheres, lo, hi)
+    got = rasterize(shape, np.array(spheres), lo, hi)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("res", [48, 64])
+def test_touching_fcc_fill_fraction(res):
+    n = res  # one conventional cube
+    spheres = inputs.fcc_opal_spheres((0, 0, 0), (n, n, n), res, sigma=0.0)
+    mat = rasterize((n, n, n), spheres, (0, 0, 0), (n, n, n))
+    target = math.pi / (3 * math.sqrt(2))
+    assert abs(float(np.mean((mat >> 6) & 1)) - target) < 0.005
+    for c in range(3):
+        cls = (mat >> (2 * c)) & 3
+        assert set(np.unique(cls)) <= {1, 2}
+        assert abs(float(np.mean(cls == 2)) - target) < 0.005
