@@ -18,7 +18,8 @@ Counter / key layout used by the gain noise (shared reading of both sides):
   key = (seed & 0xffffffff, seed >> 32)
   ctr = (cell & 0xffffffff, cell >> 32, step & 0xffffffff, step >> 32)
 with cell = (k*ny + j)*nx + i and `step` the index n of the update n -> n+1.
-Uniforms: u = ((x >> 8) + 0.5) * 2^-24, exactly representable in binary32.
+Uniforms: u = ((x >> 9) + 0.5) * 2^-23 in (0, 1): 24 significant bits, so the
+value is exact in binary32 as well as in binary64.
 Normals (Box-Muller): rho = sqrt(-2 ln u0); xi_x = rho cos(2 pi u1),
 xi_y = rho sin(2 pi u1); xi_z = sqrt(-2 ln u2) cos(2 pi u3).
 """
@@ -51,8 +52,8 @@ def philox4x32_10(ctr, key):
 
 
 def uniforms24(x):
-    """((x >> 8) + 0.5) * 2^-24 in float64 (exact)."""
-    return ((np.asarray(x, dtype=np.uint64) >> np.uint64(8)).astype(np.float64) + 0.5) * (2.0 ** -24)
+    """((x >> 9) + 0.5) * 2^-23 in float64 (exact, and exact in binary32)."""
+    return ((np.asarray(x, dtype=np.uint64) >> np.uint64(9)).astype(np.float64) + 0.5) * (2.0 ** -23)
 
 
 def gain_noise(seed: int, step: int, cells):
