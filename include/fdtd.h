@@ -1,0 +1,243 @@
+/*
+ * fdtd.h -- C ABI of the GB300 Maxwell-Bloch FDTD library (libfdtd.so).
+ *
+ * The library steps the 3D Yee finite-difference time-domain leapfrog over a
+ * per-node permittivity map of an fcc inverted opal, with absorbing (CPML),
+ * PEC or periodic faces, a Gaussian-pulse source, field probes and Poynting
+ * flux planes, coupled cell by cell to a four-level Maxwell-Bloch gain medium
+ * (polarization oscillator per field component, rate equations for the four
+ * level populations, pump and seeded spontaneous-emission noise).
+ * Paper: Conti & Fratalocchi, "Dynamic light diffusion, Anderson localization
+ * and lasing in disordered inverted opals: 3D ab-initio Maxwell-Bloch
+ * computation", Sec. "Sample and numerical approach" (method, geometry,
+ * disorder), Secs. "Wide-band excitation" and "Dynamical diffusion" (pulses,
+ * probes, transmitted flux T(t)), Sec. "3+1D simulation of lasing" (pumped gain).
+ *
+ * Units (normalized, exact rescalings of SI):
+ *   E in V/m; H~ = eta0 H in V/m; P~ = P / eps0 in V/m; populations in m^-3.
+ *   S = c dt / dx = courant / sqrt(3).   Cell (i,j,k) spans [i,i+1)x[j,j+1)x[k,k+1)
+ *   in grid units; Ex at (i+1/2,j,k), Ey at (i,j+1/2,k), Ez at (i,j,k+1/2),
+ *   H~x at (i,j+1/2,k+1/2), H~y at (i+1/2,j,k+1/2), H~z at (i+1/2,j+1/2,k).
+ * Arrays crossing the ABI are in memory order [k][j][i] (x fastest).
+ *
+ * Conventions
+ *   - Every function returns 0 (FDTD_OK) or a negative FDTD_E_* code;
+ *     fdtd_last_error() gives a message for the calling thread.  No C++
+ *     exception crosses the ABI.
+ *   - Handles are opaque and owned by the library.  Input arrays are owned by
+ *     the caller and copied before return.  Output buffers are caller-owned
+ *     HOST memory unless stated otherwise.
+ *   - Device memory comes from the optional allocator (NULL: cudaMalloc /
+ *     cudaFree).  Streams are cudaStream_t passed as void* (NULL: the legacy
+ *     default stream).  Work is enqueued asynchronously on the grid's stream;
+ *     read functions synchronize that stream.
+ *   - The library runs on the device current at fdtd_create_grid.  There is no
+ *     CPU fallback: without a usable CUDA device every call that needs one
+ *     returns FDTD_E_CUDA.
+ */
+#ifndef FDTD_H
+#define FDTD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+enum {
+  FDTD_OK = 0,
+  FDTD_E_INVAL = -1,     /* bad argument (size, index, range, NULL)            */
+  FDTD_E_NOMEM = -2,     /* allocator returned NULL                            */
+  FDTD_E_CUDA = -3,      /* CUDA runtime error (message has the CUDA string)   */
+  FDTD_E_STATE = -4,     /* call not allowed in the object's current state     */
+  FDTD_E_NONFINITE = -5, /* a probe, flux or energy value became NaN or Inf    */
+  FDTD_E_BUSY = -6,      /* request still pending                              */
+  FDTD_E_TIMEOUT = -7,   /* a bounded wait ran out                             */
+  FDTD_E_BUDGET = -8     /* request can never fit the server's memory budget   */
+};
+
+enum { FDTD_FP32 = 0, FDTD_FP64 = 1 };
+enum { FDTD_INIT_STEADY = 0, FDTD_INIT_GROUND = 1 };
+enum { FDTD_SRC_POINT = 0, FDTD_SRC_SHEET = 1 };
+
+typedef struct fdtd_grid fdtd_grid;
+
+/* Device allocator.  alloc returns device memory of `bytes` usable on
+ * `stream` or NULL; free releases it.  ctx is passed through. */
+typedef struct fdtd_allocator {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
+  void* ctx;
+} fdtd_allocator;
+
+/* Grid description (paper, Sec. "Sample and numerical approach": a box of
+ * n^3 Yee cells with an absorbing layer, Courant step half the 3D limit).
+ *   nx, ny, nz       cells per axis (each >= 1)
+ *   npml[6]          absorbing-slab thickness on faces x-,x+,y-,y+,z-,z+
+ *                    (0 = bare PEC wall; must be 0 on periodic axes)
+ *   periodic[3]      1 = wrap the axis
+ *   precision        FDTD_FP32 (fields, polarization, populations in binary32
+ *                    with compensated population sums) or FDTD_FP64
+ *   res, a           cells per lattice constant; lattice constant in metres
+ *   courant          fraction of the 3D stability limit (S = courant/sqrt 3)
+ *   eps[3]           relative permittivity of classes outside / background /
+ *                    sphere (see fdtd_set_eps_from_spheres)
+ *   cpml_*           grading order m, sigma_max factor (sigma_max dt/eps0 =
+ *                    factor (m+1) S / sqrt(eps_outside)), kappa_max, alpha_max
+ *                    (alpha dt/eps0 = alpha_max 2 pi f_ref dt), f_ref (a/lambda)
+ *   seed             64-bit key of the spontaneous-emission noise
+ *   record_capacity  probe / flux history kept on the device (steps, >= 1);
+ *                    older entries are overwritten (ring) */
+typedef struct fdtd_grid_desc {
+  int32_t nx, ny, nz;
+  int32_t npml[6];
+  int32_t periodic[3];
+  int32_t precision;
+  int32_t reserved;   /* set to 0 (keeps the record free of padding) */
+  double res, a, courant;
+  double eps[3];
+  double cpml_m, cpml_sigma_factor, cpml_kappa_max, cpml_alpha_max, cpml_f_hat;
+  uint64_t seed;
+  int64_t record_capacity;
+} fdtd_grid_desc;
+
+/* Create a grid: allocates the Yee fields (two time levels, ping-pong), the
+ * material bytes, the CPML auxiliary slabs and the recorders, all zeroed.
+ * The material starts as background class everywhere.
+ * Errors: E_INVAL (sizes, npml on a periodic axis, npml >= axis length),
+ * E_NOMEM, E_CUDA. */
+int fdtd_create_grid(const fdtd_grid_desc* desc, const fdtd_allocator* alloc, void* stream,
+                     fdtd_grid** out);
+
+/* Release every device buffer (after synchronizing the grid's stream). NULL is a no-op. */
+int fdtd_destroy_grid(fdtd_grid* g);
+
+/* Rasterize the inverted opal on the device (paper, Sec. "Sample and
+ * numerical approach": air spheres of radius r0 = a/(2 sqrt 2) in the fcc
+ * lattice, disorder on radii).  spheres: n rows (cx, cy, cz, r) in grid units
+ * (double, host).  box_lo/box_hi: structure box in grid units.  Per cell byte:
+ * bits 2c..2c+1 = class of the E_c node (0 outside the box, 1 background,
+ * 2 inside a sphere: strict (dx*dx+dy*dy)+dz*dz < r*r in FP64, each operation
+ * rounded), bit 6 = cell centre inside a sphere and the box (gain cell).
+ * Allowed before the first step only (E_STATE after). */
+int fdtd_set_eps_from_spheres(fdtd_grid* g, const double* spheres, int64_t n, const double box_lo[3],
+                              const double box_hi[3]);
+
+/* Set / read the material bytes directly (uint8[nz][ny][nx], host).
+ * set: before the first step only. */
+int fdtd_set_material(fdtd_grid* g, const uint8_t* mat);
+int fdtd_get_material(fdtd_grid* g, uint8_t* mat);
+
+/* Four-level gain medium in the cells whose bit 6 is set (paper, Secs.
+ * "Sample and numerical approach" and "3+1D simulation of lasing").
+ *   n_total    number density (m^-3)          fa_hat   transition a/lambda
+ *   dw_rel     linewidth / omega_a            tau32, tau21, tau10  lifetimes (s)
+ *   pump       rate 0 -> 3 (s^-1)             kappa    coupling (0: 6 pi eps0 c^3/(omega_a^2 tau21))
+ *   noise_amp  std of the P~ kick per step (V/m) in gain cells
+ *   init       FDTD_INIT_STEADY (N = N_eq) or FDTD_INIT_GROUND (all in level 0)
+ * Polarization: P~^{n+1} = a1 P~^n - a2 P~^{n-1} + a3 (N1-N2) E^n + noise_amp xi.
+ * Populations: Crank-Nicolson, stored as deviations from the pumped
+ * equilibrium (FP32 runs add a compensation word per population).
+ * Before the first step only; E_INVAL on non-positive lifetimes or density. */
+typedef struct fdtd_gain_params {
+  double n_total, fa_hat, dw_rel, tau32, tau21, tau10, pump, kappa, noise_amp;
+  int32_t init;
+} fdtd_gain_params;
+int fdtd_set_gain(fdtd_grid* g, const fdtd_gain_params* p);
+
+/* Soft current source (paper, Secs. "Wide-band excitation" and "Dynamical
+ * diffusion": single-cycle and 100 fs Gaussian pulses).  Waveform
+ * g(n) = exp(-(t-t0)^2/(2 tau^2)) sin(2 pi f0 (t-t0)) at t = (n+1/2) dt,
+ * tau = sqrt(ln 2)/(pi rel_bw f0), t0 = 5 tau unless t0_steps > 0.  The update
+ * of E_comp subtracts amplitude * profile * g(n) / eps_r at the source nodes.
+ * POINT: node (i,j,k).  SHEET: plane `index` normal to `axis`, over the
+ * non-absorbing interior of the two transverse axes, profile
+ * exp(-(du^2+dv^2)/waist^2) about the interior centre (waist 0 = uniform).
+ * At most 8 sources; before the first step only. */
+typedef struct fdtd_source_desc {
+  int32_t kind, comp;
+  int32_t i, j, k;
+  int32_t axis, index;
+  double waist, f0_hat, rel_bw, t0_steps, amplitude;
+} fdtd_source_desc;
+int fdtd_add_source(fdtd_grid* g, const fdtd_source_desc* s, int32_t* id);
+
+/* Field probe at cell (i,j,k): after update n it records E^{n+1} (three
+ * components) of that cell (paper, Sec. "Wide-band excitation": field in a
+ * low-symmetry point).  At most 64 probes; before the first step only. */
+int fdtd_add_probe(fdtd_grid* g, int32_t i, int32_t j, int32_t k, int32_t* id);
+
+/* Poynting flux plane (paper, Sec. "Dynamical diffusion": transversely
+ * integrated Poynting vector T(t) at the output face).  Plane `index` normal
+ * to `axis`; faces at ((u+1/2), (v+1/2)) for u in [u0,u1), v in [v0,v1) along
+ * the cyclic transverse axes (axis+1)%3, (axis+2)%3.  During update n it
+ * records T^n = sign dx^2 sum (E x H).n in watts, E at time n averaged onto the
+ * face, H averaged over the two half steps and the two planes around it.
+ * Requires 1 <= index <= n_axis-1 and ranges within [0, n-1].  At most 16
+ * planes; before the first step only. */
+int fdtd_add_flux_plane(fdtd_grid* g, int32_t axis, int32_t index, double sign, int32_t u0, int32_t u1,
+                        int32_t v0, int32_t v1, int32_t* id);
+
+/* Advance the grid by n >= 0 time steps (asynchronous on the grid's stream).
+ * The first call freezes the set-up (sources, probes, flux planes, gain).
+ * E_STATE if no permittivity map was set.  The recorders are rings: stepping
+ * past record_capacity overwrites the oldest entries. */
+int fdtd_step_n(fdtd_grid* g, int64_t n);
+
+/* Launch shape of the step kernel: blocks of bx x by threads own tiles of
+ * (bx-1) x (by-1) columns and march z-ranges of `zdepth` planes (0: chosen
+ * from the grid size); grid_blocks > 0 makes the launch persistent with that
+ * many blocks looping over the tiles (0: one block per tile).  Results do not
+ * depend on the shape.  Needs bx, by >= 2, bx*by a multiple of 32, <= 512. */
+int fdtd_set_launch(fdtd_grid* g, int32_t bx, int32_t by, int32_t zdepth, int32_t grid_blocks);
+
+/* Wait for the grid's stream; returns E_NONFINITE if the device raised the
+ * non-finite flag (checked on probes, flux and energy). */
+int fdtd_sync(fdtd_grid* g);
+
+/* Steps completed (host-side count of enqueued steps). */
+int fdtd_steps_done(fdtd_grid* g, int64_t* n);
+
+/* Probe history: out[count][3] (double, host) for updates t0 .. t0+count-1.
+ * E_INVAL if the range is not within the last record_capacity steps. */
+int fdtd_read_probes(fdtd_grid* g, int32_t id, int64_t t0, int64_t count, double* out);
+
+/* Flux history: out[count] (double, host) of T^n for n = t0 .. t0+count-1. */
+int fdtd_read_flux(fdtd_grid* g, int32_t id, int64_t t0, int64_t count, double* out);
+
+/* Current fields, comp 0..5 = Ex, Ey, Ez, H~x, H~y, H~z: E at time n, H~ at
+ * time n-1/2 (n = steps done), as double[nz][ny][nx] (host). */
+int fdtd_read_fields(fdtd_grid* g, int32_t comp, double* out);
+/* Overwrite one field component of the current time level (before the first
+ * step only), same layout. */
+int fdtd_write_fields(fdtd_grid* g, int32_t comp, const double* in);
+
+/* Gain state as double[3][nz][ny][nx] (host): what = 0 -> P~^n, 1 -> P~^{n-1},
+ * 2 -> populations N1, N2, N3 (m^-3; N0 = n_total - N1 - N2 - N3 in gain
+ * cells), 3 -> deviations N1..N3 - N_eq (m^-3) as carried by the update;
+ * zero outside gain cells.  E_STATE without gain. */
+int fdtd_read_gain(fdtd_grid* g, int32_t what, double* out);
+
+/* Field energy 1/2 eps0 dx^3 (sum eps_r E^2 + sum H~^2) in joules at the
+ * current time level (E^n, H~^{n-1/2}), reduced on the device in FP64 in a
+ * fixed order (bitwise reproducible for a given grid size). */
+int fdtd_field_energy(fdtd_grid* g, double* out);
+
+/* Checkpoint: write / read every state array (fields, CPML slabs, gain state,
+ * step count, recorders) to / from a file.  load requires a grid created
+ * with the same description. */
+int fdtd_save_state(fdtd_grid* g, const char* path);
+int fdtd_load_state(fdtd_grid* g, const char* path);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* fdtd_last_error(void);
+
+/* Library build information (static string). */
+const char* fdtd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDTD_H */

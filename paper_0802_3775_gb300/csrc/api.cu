@@ -1,0 +1,590 @@
+// Host side of the C ABI (include/fdtd.h): grid lifecycle, coefficient
+// set-up, launch planning, stepping and read-backs.
+//
+// The per-cell and per-step arithmetic runs in the kernels of kernels.cu; the
+// host computes the grid's constant tables once (CPML grading profiles,
+// material-class coefficients, the 4x4 Crank-Nicolson matrices of the gain
+// model) and plans the launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fdtd.h"
+#include "fdtd_api_internal.h"
+#include "fdtd_internal.cuh"
+
+namespace fdtd {
+
+thread_local std::string g_last_error;
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* where) {
+  return set_error(FDTD_E_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------ memory
+void* DeviceMemory::get(size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (alloc.alloc) {
+    p = alloc.alloc(bytes, stream, alloc.ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) blocks.push_back({p, bytes});
+  return p;
+}
+
+void DeviceMemory::release_all() {
+  for (auto& b : blocks) {
+    if (alloc.free) alloc.free(b.first, b.second, stream, alloc.ctx);
+    else cudaFree(b.first);
+  }
+  blocks.clear();
+}
+
+size_t DeviceMemory::total() const {
+  size_t s = 0;
+  for (auto& b : blocks) s += b.second;
+  return s;
+}
+
+// ------------------------------------------------------------------ CPML profile
+// (1/kappa, b, c) at the nodes of one axis (integer nodes for E-curl terms,
+// half-integer nodes for H-curl terms).  Depth rho = (L0 - x)/L0 below L0 and
+// (x - (n - L1))/L1 above n - L1; sigma dt/eps0 = factor (m+1) S rho^m /
+// sqrt(eps_edge); kappa = 1 + (kappa_max - 1) rho^m; alpha dt/eps0 =
+// alpha_max 2 pi f_ref dt (1 - rho); b = exp(-(sigma/kappa + alpha) dt/eps0),
+// c = sigma (b - 1)/(sigma kappa + kappa^2 alpha).
+static void cpml_profile(const fdtd_grid_desc& d, int axis, bool half, double S, std::vector<double>& ik,
+                         std::vector<double>& b, std::vector<double>& c) {
+  const int n = axis == 0 ? d.nx : axis == 1 ? d.ny : d.nz;
+  const int L0 = d.npml[2 * axis], L1 = d.npml[2 * axis + 1];
+  ik.assign(n, 1.0);
+  b.assign(n, 1.0);
+  c.assign(n, 0.0);
+  const double sig_max = d.cpml_sigma_factor * (d.cpml_m + 1.0) * S / std::sqrt(d.eps[0]);
+  const double alpha_max = d.cpml_alpha_max * 2.0 * M_PI * d.cpml_f_hat * S / d.res;
+  for (int q = 0; q < n; ++q) {
+    const double x = q + (half ? 0.5 : 0.0);
+    double rho = 0.0;
+    if (L0 > 0 && x < L0) rho = (L0 - x) / L0;
+    if (L1 > 0 && x > n - L1) rho = (x - (n - L1)) / L1;
+    if (rho <= 0.0) continue;
+    const double rm = std::pow(rho, d.cpml_m);
+    const double sig = sig_max * rm;
+    const double kap = 1.0 + (d.cpml_kappa_max - 1.0) * rm;
+    const double alp = alpha_max * (1.0 - rho);
+    b[q] = std::exp(-(sig / kap + alp));
+    c[q] = sig * (b[q] - 1.0) / (sig * kap + kap * kap * alp);
+    ik[q] = 1.0 / kap;
+  }
+}
+
+// Solve the 4x4 system L X = B (columns of B) by Gaussian elimination with
+// partial pivoting, in FP64.
+static void solve4(const double Lin[4][4], double B[4][5], int ncol) {
+  double L[4][4];
+  std::memcpy(L, Lin, sizeof(L));
+  for (int col = 0; col < 4; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < 4; ++r)
+      if (std::fabs(L[r][col]) > std::fabs(L[piv][col])) piv = r;
+    if (piv != col) {
+      for (int q = 0; q < 4; ++q) std::swap(L[col][q], L[piv][q]);
+      for (int q = 0; q < ncol; ++q) std::swap(B[col][q], B[piv][q]);
+    }
+    for (int r = col + 1; r < 4; ++r) {
+      const double f = L[r][col] / L[col][col];
+      for (int q = col; q < 4; ++q) L[r][q] -= f * L[col][q];
+      for (int q = 0; q < ncol; ++q) B[r][q] -= f * B[col][q];
+    }
+  }
+  for (int col = 3; col >= 0; --col) {
+    for (int q = 0; q < ncol; ++q) {
+      double s = B[col][q];
+      for (int r = col + 1; r < 4; ++r) s -= L[col][r] * B[r][q];
+      B[col][q] = s / L[col][col];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ grid
+template <typename T>
+struct GridImpl final : GridBase {
+  StepGrid<T> sg{};
+  ObsGrid<T> og{};
+  StepGrid<T>* d_sg = nullptr;
+  ObsGrid<T>* d_og = nullptr;
+  int4* d_items = nullptr;
+  int4* d_oitems = nullptr;
+  std::vector<int4> items, oitems;
+  int* d_err = nullptr;
+  double* d_energy = nullptr;
+  double* d_epart = nullptr;
+  unsigned int* d_ecount = nullptr;
+  T* d_F = nullptr;
+  T* d_gain = nullptr;
+  size_t gain_words = 0;
+  T* d_psi = nullptr;
+  size_t psi_words = 0;
+  T* d_prof = nullptr;
+  double n_total = 0.0, neq[4] = {0, 0, 0, 0};
+
+  int precision() const override { return sizeof(T) == 4 ? FDTD_FP32 : FDTD_FP64; }
+  size_t word() const override { return sizeof(T); }
+
+  int init() {
+    const long long nc = ncell;
+    d_F = (T*)mem.get(sizeof(T) * 12 * (size_t)nc);
+    uint8_t* mat = (uint8_t*)mem.get((size_t)nc);
+    d_err = (int*)mem.get(sizeof(int) * 4);
+    d_energy = (double*)mem.get(sizeof(double) * 4);
+    d_epart = (double*)mem.get(sizeof(double) * kEnergyBlocks);
+    d_ecount = (unsigned int*)mem.get(sizeof(unsigned int) * 4);
+    d_sg = (StepGrid<T>*)mem.get(sizeof(StepGrid<T>));
+    d_og = (ObsGrid<T>*)mem.get(sizeof(ObsGrid<T>));
+    if (!d_F || !mat || !d_err || !d_energy || !d_epart || !d_ecount || !d_sg || !d_og)
+      return set_error(FDTD_E_NOMEM, "device allocation failed (%lld cells)", nc);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(d_F, 0, sizeof(T) * 12 * (size_t)nc, stream)) != cudaSuccess) return cuda_error(e, "memset fields");
+    if ((e = cudaMemsetAsync(mat, 0x15, (size_t)nc, stream)) != cudaSuccess) return cuda_error(e, "memset material");
+    if ((e = cudaMemsetAsync(d_err, 0, sizeof(int) * 4, stream)) != cudaSuccess) return cuda_error(e, "memset err");
+    if ((e = cudaMemsetAsync(d_ecount, 0, sizeof(unsigned) * 4, stream)) != cudaSuccess) return cuda_error(e, "memset");
+    d_mat = mat;
+
+    sg.nx = og.nx = desc.nx;
+    sg.ny = og.ny = desc.ny;
+    sg.nz = og.nz = desc.nz;
+    sg.per = (desc.periodic[0] ? 1 : 0) | (desc.periodic[1] ? 2 : 0) | (desc.periodic[2] ? 4 : 0);
+    for (int q = 0; q < 6; ++q) sg.L[q] = desc.npml[q];
+    for (int s = 0; s < 2; ++s)
+      for (int c = 0; c < 6; ++c) {
+        sg.F[s][c] = d_F + (size_t)(s * 6 + c) * nc;
+        og.F[s][c] = sg.F[s][c];
+      }
+    sg.mat = mat;
+    sg.step = 0;
+    sg.step_end = (long long)0x7fffffffffffffffLL;
+    og.step = 0;
+    og.step_end = sg.step_end;
+    og.err = d_err;
+    og.dx2_over_eta0 = dx * dx / eta0();
+
+    // CPML memory: per axis with a slab, 2 E-side arrays and 2x2 H-side arrays
+    const int n3[3] = {desc.nx, desc.ny, desc.nz};
+    psi_words = 0;
+    size_t slab[3] = {0, 0, 0};
+    for (int d = 0; d < 3; ++d) {
+      sg.Sd[d] = desc.npml[2 * d] + desc.npml[2 * d + 1];
+      if (sg.Sd[d]) {
+        slab[d] = (size_t)sg.Sd[d] * ((size_t)nc / n3[d]);
+        psi_words += 6 * slab[d];
+      }
+    }
+    if (psi_words) {
+      d_psi = (T*)mem.get(sizeof(T) * psi_words);
+      if (!d_psi) return set_error(FDTD_E_NOMEM, "device allocation failed (CPML memory)");
+      if ((e = cudaMemsetAsync(d_psi, 0, sizeof(T) * psi_words, stream)) != cudaSuccess) return cuda_error(e, "memset psi");
+      T* p = d_psi;
+      for (int d = 0; d < 3; ++d) {
+        if (!slab[d]) continue;
+        sg.psiE[d][0] = p; p += slab[d];
+        sg.psiE[d][1] = p; p += slab[d];
+        for (int s = 0; s < 2; ++s) {
+          sg.psiH[s][d][0] = p; p += slab[d];
+          sg.psiH[s][d][1] = p; p += slab[d];
+        }
+      }
+    }
+    // grading profiles
+    const size_t prof_words = (size_t)6 * (desc.nx + desc.ny + desc.nz);
+    d_prof = (T*)mem.get(sizeof(T) * prof_words);
+    if (!d_prof) return set_error(FDTD_E_NOMEM, "device allocation failed (profiles)");
+    std::vector<T> hprof(prof_words);
+    size_t off = 0;
+    for (int d = 0; d < 3; ++d)
+      for (int h = 0; h < 2; ++h) {
+        std::vector<double> ik, b, c;
+        cpml_profile(desc, d, h == 1, S, ik, b, c);
+        const std::vector<double>* arr[3] = {&ik, &b, &c};
+        for (int q = 0; q < 3; ++q) {
+          sg.prof[d][h][q] = d_prof + off;
+          for (int x = 0; x < n3[d]; ++x) hprof[off + x] = (T)(*arr[q])[x];
+          off += n3[d];
+        }
+      }
+    if ((e = cudaMemcpyAsync(d_prof, hprof.data(), sizeof(T) * prof_words, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+      return cuda_error(e, "upload profiles");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "init");
+    sg.cH = (T)S;
+    for (int q = 0; q < 3; ++q) {
+      sg.cE[q] = (T)(S / desc.eps[q]);
+      sg.cP[q] = (T)(1.0 / desc.eps[q]);
+    }
+    sg.seed = desc.seed;
+    return FDTD_OK;
+  }
+
+  int set_gain(const fdtd_gain_params& p) override {
+    const double e0 = eps0();
+    const double omega_a = 2.0 * M_PI * p.fa_hat * kC0 / desc.a;
+    const double dw = p.dw_rel * omega_a;
+    const double kappa = p.kappa != 0.0 ? p.kappa : 6.0 * M_PI * e0 * kC0 * kC0 * kC0 / (omega_a * omega_a * p.tau21);
+    const double g = 0.5 * dw * dt;
+    const double a1 = (2.0 - (omega_a * dt) * (omega_a * dt)) / (1.0 + g);
+    const double a2 = (1.0 - g) / (1.0 + g);
+    const double a3 = kappa * dt * dt / (e0 * (1.0 + g));
+    const double W = p.pump;
+    const double A[4][4] = {{-W, 1.0 / p.tau10, 0.0, 0.0},
+                            {0.0, -1.0 / p.tau10, 1.0 / p.tau21, 0.0},
+                            {0.0, 0.0, -1.0 / p.tau21, 1.0 / p.tau32},
+                            {W, 0.0, 0.0, -1.0 / p.tau32}};
+    double L[4][4];
+    double B[4][5];
+    for (int r = 0; r < 4; ++r) {
+      for (int c = 0; c < 4; ++c) {
+        L[r][c] = (r == c ? 1.0 : 0.0) - 0.5 * dt * A[r][c];
+        B[r][c] = A[r][c];
+      }
+      B[r][4] = r == 1 ? -1.0 : r == 2 ? 1.0 : 0.0;
+    }
+    solve4(L, B, 5);  // B[:, 0:4] = L^-1 A,  B[:, 4] = L^-1 b
+    const double n0 = p.n_total / (1.0 + W * (p.tau32 + p.tau21 + p.tau10));
+    neq[0] = n0;
+    neq[1] = W * p.tau10 * n0;
+    neq[2] = W * p.tau21 * n0;
+    neq[3] = W * p.tau32 * n0;
+    n_total = p.n_total;
+    sg.a1 = (T)a1;
+    sg.a2 = (T)a2;
+    sg.a3 = (T)(a3 * p.n_total);
+    sg.n12eq = (T)((neq[1] - neq[2]) / p.n_total);
+    sg.q = (T)(e0 / (kHbar * omega_a * p.n_total));
+    sg.noise = (T)p.noise_amp;
+    for (int k = 0; k < 3; ++k) {
+      for (int j = 0; j < 3; ++j) sg.D[k][j] = (T)(dt * (B[k + 1][j + 1] - B[k + 1][0]));
+      sg.w[k] = (T)B[k + 1][4];
+    }
+    // state: P (2 slots x 3), dN (3), compensation (3, binary32 only)
+    const size_t nw = (sizeof(T) == 4 ? 12 : 9);
+    if (!d_gain) {
+      gain_words = nw * (size_t)ncell;
+      d_gain = (T*)mem.get(sizeof(T) * gain_words);
+      if (!d_gain) return set_error(FDTD_E_NOMEM, "device allocation failed (gain state)");
+    }
+    for (int s = 0; s < 2; ++s)
+      for (int c = 0; c < 3; ++c) sg.P[s][c] = d_gain + (size_t)(s * 3 + c) * ncell;
+    for (int c = 0; c < 3; ++c) sg.dN[c] = d_gain + (size_t)(6 + c) * ncell;
+    for (int c = 0; c < 3; ++c) sg.cmp[c] = sizeof(T) == 4 ? d_gain + (size_t)(9 + c) * ncell : nullptr;
+    sg.gain = 1;
+    T d1 = 0, d2 = 0, d3 = 0;
+    if (p.init == FDTD_INIT_GROUND) {
+      d1 = (T)(-neq[1] / p.n_total);
+      d2 = (T)(-neq[2] / p.n_total);
+      d3 = (T)(-neq[3] / p.n_total);
+    }
+    cudaError_t e = launch_gain_init<T>(&sg, ncell, d1, d2, d3, stream);
+    if (e != cudaSuccess) return cuda_error(e, "gain init");
+    return FDTD_OK;
+  }
+
+  int add_source(const fdtd_source_desc& s) override {
+    if (sg.nsrc >= kMaxSrc) return set_error(FDTD_E_INVAL, "at most %d sources", kMaxSrc);
+    SrcDev d{};
+    d.kind = s.kind;
+    d.comp = s.comp;
+    d.amp = s.amplitude;
+    const int n3[3] = {desc.nx, desc.ny, desc.nz};
+    if (s.kind == FDTD_SRC_POINT) {
+      d.i = s.i; d.j = s.j; d.k = s.k;
+      d.axis = 0; d.index = -1;
+    } else {
+      d.axis = s.axis;
+      d.index = s.index;
+      const int d1 = (s.axis + 1) % 3, d2 = (s.axis + 2) % 3;
+      d.lo1 = desc.npml[2 * d1];
+      d.hi1 = n3[d1] - desc.npml[2 * d1 + 1];
+      d.lo2 = desc.npml[2 * d2];
+      d.hi2 = n3[d2] - desc.npml[2 * d2 + 1];
+      d.uc = 0.5 * (d.lo1 + d.hi1 - 1);
+      d.vc = 0.5 * (d.lo2 + d.hi2 - 1);
+      d.inv_w2 = s.waist > 0 ? 1.0 / (s.waist * s.waist) : 0.0;
+      d.i = d.j = d.k = -1;
+    }
+    d.f0dt = s.f0_hat * S / desc.res;
+    d.tau = std::sqrt(std::log(2.0)) / (M_PI * s.rel_bw * d.f0dt);
+    d.t0 = s.t0_steps > 0 ? s.t0_steps : 5.0 * d.tau;
+    sg.src[sg.nsrc++] = d;
+    return FDTD_OK;
+  }
+
+  int add_probe(int i, int j, int k) override {
+    if (og.nprobe >= kMaxProbes) return set_error(FDTD_E_INVAL, "at most %d probes", kMaxProbes);
+    og.probe[og.nprobe][0] = i;
+    og.probe[og.nprobe][1] = j;
+    og.probe[og.nprobe][2] = k;
+    og.nprobe++;
+    return FDTD_OK;
+  }
+
+  int add_flux(int axis, int index, double sign, int u0, int u1, int v0, int v1) override {
+    if (og.nflux >= kMaxFlux) return set_error(FDTD_E_INVAL, "at most %d flux planes", kMaxFlux);
+    const int f = og.nflux++;
+    og.flux_axis[f] = axis;
+    og.flux_index[f] = index;
+    og.flux_sign[f] = sign;
+    og.flux_u0[f] = u0;
+    og.flux_u1[f] = u1;
+    og.flux_v0[f] = v0;
+    og.flux_v1[f] = v1;
+    const long long faces = (long long)(u1 - u0) * (v1 - v0);
+    int parts = (int)((faces + 2047) / 2048);
+    og.flux_parts[f] = std::max(1, std::min(kMaxFluxParts, parts));
+    return FDTD_OK;
+  }
+
+  // Work items of one time step for a tile of (bx-1) x (by-1) owned columns
+  // and z-ranges of `zdepth` planes.
+  void plan_items() {
+    items.clear();
+    const int ox = bx - 1, oy = by - 1;
+    const int tnx = (desc.nx + ox - 1) / ox, tny = (desc.ny + oy - 1) / oy;
+    int depth = zdepth;
+    if (depth <= 0) {
+      const int target = 4 * 152;
+      const int chunks = std::max(1, (target + tnx * tny - 1) / (tnx * tny));
+      depth = std::max(8, (desc.nz + chunks - 1) / chunks);
+    }
+    depth = std::min(depth, desc.nz);
+    for (int z0 = 0; z0 < desc.nz; z0 += depth) {
+      const int z1 = std::min(desc.nz, z0 + depth);
+      for (int ty = 0; ty < tny; ++ty)
+        for (int tx = 0; tx < tnx; ++tx) items.push_back(make_int4(0, tx * ox, ty * oy, z0 | (z1 << 16)));
+    }
+    oitems.clear();
+    if (og.nprobe) oitems.push_back(make_int4(0, -1, 0, 1));
+    for (int f = 0; f < og.nflux; ++f)
+      for (int p = 0; p < og.flux_parts[f]; ++p) oitems.push_back(make_int4(0, f, p, og.flux_parts[f]));
+  }
+
+  int finalize() override {
+    cudaError_t e;
+    // recorders
+    const long long cap = desc.record_capacity;
+    og.cap = cap;
+    if (og.nprobe) {
+      og.probe_ring = (T*)mem.get(sizeof(T) * (size_t)cap * og.nprobe * 3);
+      if (!og.probe_ring) return set_error(FDTD_E_NOMEM, "device allocation failed (probe ring)");
+    }
+    if (og.nflux) {
+      og.flux_ring = (double*)mem.get(sizeof(double) * (size_t)cap * og.nflux);
+      og.partials = (double*)mem.get(sizeof(double) * kMaxFlux * kMaxFluxParts);
+      og.counters = (unsigned int*)mem.get(sizeof(unsigned int) * kMaxFlux);
+      if (!og.flux_ring || !og.partials || !og.counters)
+        return set_error(FDTD_E_NOMEM, "device allocation failed (flux recorder)");
+      if ((e = cudaMemsetAsync(og.counters, 0, sizeof(unsigned) * kMaxFlux, stream)) != cudaSuccess)
+        return cuda_error(e, "memset counters");
+    }
+    return replan();
+  }
+
+  size_t items_cap = 0, oitems_cap = 0;
+
+  int replan() override {
+    cudaError_t e;
+    plan_items();
+    if (items.size() > items_cap) {
+      d_items = (int4*)mem.get(sizeof(int4) * items.size());
+      items_cap = items.size();
+    }
+    if (!d_items) return set_error(FDTD_E_NOMEM, "device allocation failed (items)");
+    if ((e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+      return cuda_error(e, "upload items");
+    if (!oitems.empty()) {
+      if (oitems.size() > oitems_cap) {
+        d_oitems = (int4*)mem.get(sizeof(int4) * oitems.size());
+        oitems_cap = oitems.size();
+      }
+      if (!d_oitems) return set_error(FDTD_E_NOMEM, "device allocation failed (items)");
+      if ((e = cudaMemcpyAsync(d_oitems, oitems.data(), sizeof(int4) * oitems.size(), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return cuda_error(e, "upload items");
+    }
+    return upload_tables();
+  }
+
+  int upload_tables() {
+    cudaError_t e;
+    sg.step = og.step = steps;
+    if ((e = cudaMemcpyAsync(d_sg, &sg, sizeof(sg), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return cuda_error(e, "upload grid");
+    if ((e = cudaMemcpyAsync(d_og, &og, sizeof(og), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return cuda_error(e, "upload grid");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "upload grid");
+    return FDTD_OK;
+  }
+
+  int step(long long n) override {
+    cudaError_t e;
+    long long done = 0;
+    while (done < n) {
+      const int chunk = (int)std::min<long long>(n - done, 1 << 20);
+      for (int s = 0; s < chunk; ++s) {
+        if ((e = launch_step<T>(d_sg, d_items, (int)items.size(), s, bx, by, sg.gain != 0, grid_blocks, stream)) != cudaSuccess)
+          return cuda_error(e, "step kernel");
+        if (!oitems.empty() && (e = launch_observe<T>(d_og, d_oitems, (int)oitems.size(), s, stream)) != cudaSuccess)
+          return cuda_error(e, "observe kernel");
+      }
+      if ((e = launch_advance<T>(d_sg, d_og, 1, chunk, stream)) != cudaSuccess) return cuda_error(e, "advance");
+      done += chunk;
+      steps += chunk;
+    }
+    sg.step = og.step = steps;
+    return FDTD_OK;
+  }
+
+  int read_field(int comp, double* out) override {
+    const int sel = (int)(steps & 1);
+    return copy_out(sg.F[sel][comp], ncell, out);
+  }
+
+  int copy_out(const T* src, long long count, double* out) {
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "sync");
+    std::vector<T> h((size_t)count);
+    if ((e = cudaMemcpy(h.data(), src, sizeof(T) * count, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_error(e, "read");
+    for (long long q = 0; q < count; ++q) out[q] = (double)h[q];
+    return FDTD_OK;
+  }
+
+  int write_field(int comp, const double* in) override {
+    std::vector<T> h((size_t)ncell);
+    for (long long q = 0; q < ncell; ++q) h[q] = (T)in[q];
+    cudaError_t e;
+    if ((e = cudaMemcpy(sg.F[0][comp], h.data(), sizeof(T) * ncell, cudaMemcpyHostToDevice)) != cudaSuccess) return cuda_error(e, "write");
+    return FDTD_OK;
+  }
+
+  int read_gain(int what, double* out) override {
+    if (!sg.gain) return set_error(FDTD_E_STATE, "no gain medium");
+    int r;
+    if (what == 0 || what == 1) {
+      const int slot = (int)((steps + (what == 1 ? 1 : 0)) & 1);
+      for (int c = 0; c < 3; ++c)
+        if ((r = copy_out(sg.P[slot][c], ncell, out + (size_t)c * ncell)) != FDTD_OK) return r;
+      return FDTD_OK;
+    }
+    std::vector<uint8_t> m((size_t)ncell);
+    if ((r = get_material(m.data())) != FDTD_OK) return r;
+    for (int c = 0; c < 3; ++c) {
+      if ((r = copy_out(sg.dN[c], ncell, out + (size_t)c * ncell)) != FDTD_OK) return r;
+      for (long long q = 0; q < ncell; ++q) {
+        double& v = out[(size_t)c * ncell + q];
+        if (!((m[q] >> 6) & 1)) v = 0.0;
+        else if (what == 2) v = n_total * (neq[c + 1] / n_total + v);
+        else v = n_total * v;
+      }
+    }
+    return FDTD_OK;
+  }
+
+  int read_probe(int id, long long t0, long long count, double* out) override {
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "sync");
+    std::vector<T> ring((size_t)og.cap * og.nprobe * 3);
+    if ((e = cudaMemcpy(ring.data(), og.probe_ring, sizeof(T) * ring.size(), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_error(e, "read probes");
+    for (long long q = 0; q < count; ++q) {
+      const size_t base = (size_t)((((t0 + q) % og.cap) * og.nprobe + id) * 3);
+      for (int c = 0; c < 3; ++c) out[q * 3 + c] = (double)ring[base + c];
+    }
+    return FDTD_OK;
+  }
+
+  int read_flux(int id, long long t0, long long count, double* out) override {
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "sync");
+    std::vector<double> ring((size_t)og.cap * og.nflux);
+    if ((e = cudaMemcpy(ring.data(), og.flux_ring, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_error(e, "read flux");
+    for (long long q = 0; q < count; ++q) out[q] = ring[(size_t)(((t0 + q) % og.cap) * og.nflux + id)];
+    return FDTD_OK;
+  }
+
+  int nprobes() const override { return og.nprobe; }
+  int nfluxes() const override { return og.nflux; }
+  long long capacity() const override { return og.cap; }
+
+  int energy(double* out) override {
+    const int sel = (int)(steps & 1);
+    const T* F6[6];
+    for (int c = 0; c < 6; ++c) F6[c] = sg.F[sel][c];
+    cudaError_t e = launch_energy<T>(F6, d_mat, desc.eps[0], desc.eps[1], desc.eps[2], ncell, d_epart, d_ecount,
+                                     d_energy, d_err, stream);
+    if (e != cudaSuccess) return cuda_error(e, "energy kernel");
+    double v = 0;
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "sync");
+    if ((e = cudaMemcpy(&v, d_energy, sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_error(e, "read energy");
+    *out = 0.5 * eps0() * dx * dx * dx * v;
+    return FDTD_OK;
+  }
+
+  int error_flags(int* flags) override {
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "sync");
+    if ((e = cudaMemcpy(flags, d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_error(e, "read flags");
+    return FDTD_OK;
+  }
+
+  // state blobs for checkpointing: (device pointer, bytes)
+  void state_blobs(std::vector<std::pair<void*, size_t>>& v) override {
+    v.clear();
+    v.push_back({d_F, sizeof(T) * 12 * (size_t)ncell});
+    v.push_back({(void*)d_mat, (size_t)ncell});
+    if (d_psi) v.push_back({d_psi, sizeof(T) * psi_words});
+    if (d_gain) v.push_back({d_gain, sizeof(T) * gain_words});
+    if (og.probe_ring) v.push_back({og.probe_ring, sizeof(T) * (size_t)og.cap * og.nprobe * 3});
+    if (og.flux_ring) v.push_back({og.flux_ring, sizeof(double) * (size_t)og.cap * og.nflux});
+  }
+
+  void set_steps(long long s) override {
+    steps = s;
+    sg.step = og.step = s;
+  }
+
+  // batch access
+  const void* step_record() const override { return &sg; }
+  const void* obs_record() const override { return &og; }
+  size_t step_record_size() const override { return sizeof(sg); }
+  size_t obs_record_size() const override { return sizeof(og); }
+  int has_gain() const override { return sg.gain; }
+};
+
+GridBase* make_grid(const fdtd_grid_desc& d) {
+  if (d.precision == FDTD_FP32) return new (std::nothrow) GridImpl<float>();
+  return new (std::nothrow) GridImpl<double>();
+}
+
+int init_grid(GridBase* g) {
+  if (g->precision() == FDTD_FP32) return static_cast<GridImpl<float>*>(g)->init();
+  return static_cast<GridImpl<double>*>(g)->init();
+}
+
+}  // namespace fdtd

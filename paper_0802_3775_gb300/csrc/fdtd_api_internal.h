@@ -1,0 +1,85 @@
+// Host-side grid object behind the opaque fdtd_grid handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/fdtd.h"
+
+namespace fdtd {
+
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* where);
+extern thread_local std::string g_last_error;
+
+// Device allocations of one owner, released together.
+struct DeviceMemory {
+  fdtd_allocator alloc{nullptr, nullptr, nullptr};
+  void* stream = nullptr;
+  std::vector<std::pair<void*, size_t>> blocks;
+  void* get(size_t bytes);
+  void release_all();
+  size_t total() const;
+};
+
+// Precision-independent interface of a grid; GridImpl<T> implements it.
+struct GridBase {
+  fdtd_grid_desc desc{};
+  cudaStream_t stream = nullptr;
+  DeviceMemory mem;
+  long long ncell = 0;
+  long long steps = 0;
+  double S = 0, dx = 0, dt = 0;
+  bool material_set = false;
+  bool finalized = false;
+  int bx = 32, by = 8, zdepth = 0, grid_blocks = 0;
+  uint8_t* d_mat = nullptr;
+
+  virtual ~GridBase() { mem.release_all(); }
+  virtual int precision() const = 0;
+  virtual size_t word() const = 0;
+  virtual int set_gain(const fdtd_gain_params& p) = 0;
+  virtual int add_source(const fdtd_source_desc& s) = 0;
+  virtual int add_probe(int i, int j, int k) = 0;
+  virtual int add_flux(int axis, int index, double sign, int u0, int u1, int v0, int v1) = 0;
+  virtual int finalize() = 0;
+  virtual int replan() = 0;
+  virtual int step(long long n) = 0;
+  virtual int read_field(int comp, double* out) = 0;
+  virtual int write_field(int comp, const double* in) = 0;
+  virtual int read_gain(int what, double* out) = 0;
+  virtual int read_probe(int id, long long t0, long long count, double* out) = 0;
+  virtual int read_flux(int id, long long t0, long long count, double* out) = 0;
+  virtual int nprobes() const = 0;
+  virtual int nfluxes() const = 0;
+  virtual long long capacity() const = 0;
+  virtual int energy(double* out) = 0;
+  virtual int error_flags(int* flags) = 0;
+  virtual void state_blobs(std::vector<std::pair<void*, size_t>>& v) = 0;
+  virtual void set_steps(long long s) = 0;
+  virtual const void* step_record() const = 0;
+  virtual const void* obs_record() const = 0;
+  virtual size_t step_record_size() const = 0;
+  virtual size_t obs_record_size() const = 0;
+  virtual int has_gain() const = 0;
+
+  int get_material(uint8_t* out) {
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "sync");
+    if ((e = cudaMemcpy(out, d_mat, (size_t)ncell, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_error(e, "read material");
+    return FDTD_OK;
+  }
+};
+
+GridBase* make_grid(const fdtd_grid_desc& d);
+int init_grid(GridBase* g);
+
+}  // namespace fdtd
+
+struct fdtd_grid {
+  fdtd::GridBase* impl;
+};

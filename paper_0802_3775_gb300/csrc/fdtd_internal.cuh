@@ -1,0 +1,132 @@
+// Internal declarations of the GB300 Maxwell-Bloch FDTD library.
+//
+// Device-side grid records and kernel launchers shared by the library's
+// translation units.  Nothing here is part of the C ABI (include/fdtd.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdtd {
+
+constexpr int kMaxSrc = 8;
+constexpr int kMaxProbes = 64;
+constexpr int kMaxFlux = 16;
+constexpr int kMaxFluxParts = 64;
+constexpr int kEnergyBlocks = 256;
+
+// Physical constants (CODATA; mu0 of the 2019 SI, hbar exact).
+constexpr double kC0 = 299792458.0;
+constexpr double kMu0 = 1.25663706212e-6;
+constexpr double kHbar = 1.054571817e-34;
+inline double eps0() { return 1.0 / (kMu0 * kC0 * kC0); }
+inline double eta0() { return kMu0 * kC0; }
+
+// One soft current source (Gaussian-modulated sine; see fdtd_add_source).
+struct SrcDev {
+  int kind;          // 0 point, 1 sheet
+  int comp;          // driven E component
+  int axis, index;   // sheet plane
+  int i, j, k;       // point node
+  int lo1, hi1, lo2, hi2;  // sheet transverse node ranges along (axis+1)%3, (axis+2)%3
+  double uc, vc;     // profile centre (node index units)
+  double inv_w2;     // 1/waist^2 (0: uniform)
+  double amp;        // amplitude (V/m per step)
+  double f0dt;       // f0 * dt
+  double tau;        // envelope width in steps
+  double t0;         // envelope centre in steps
+};
+
+// Per-grid record read by the step kernel.  Lives in device memory (a table
+// of them for a batched launch); each block copies its grid's record into
+// shared memory.
+template <typename T>
+struct StepGrid {
+  int nx, ny, nz;
+  int per;              // bit d set: axis d periodic
+  int L[6];             // slab thickness x-,x+,y-,y+,z-,z+
+  int Sd[3];            // slab extent per axis (L[2d] + L[2d+1])
+  int gain;             // gain medium present
+  int nsrc;
+  long long step;       // steps completed before this launch sequence
+  long long step_end;   // no update n >= step_end is performed
+  T* F[2][6];           // field sets (ping-pong): Ex Ey Ez Hx Hy Hz
+  const uint8_t* mat;   // material bytes
+  T* psiE[3][2];        // E-curl CPML memory per axis, slot 0 -> comp (d+1)%3, 1 -> (d+2)%3
+  T* psiH[2][3][2];     // H-curl CPML memory, ping-pong like the fields
+  const T* prof[3][2][3];  // [axis][0 E-node (integer), 1 H-node (half-integer)][1/kappa, b, c]
+  T cH;                 // S
+  T cE[3], cP[3];       // S/eps_r and 1/eps_r per material class
+  // gain medium (normalized populations N~ = N / n_total)
+  T* P[2][3];           // P~ time slots: P^n in slot n&1
+  T* dN[3];             // dN~1..3 (dN~0 = -sum)
+  T* cmp[3];            // compensation words (binary32 runs only)
+  T a1, a2, a3, n12eq, q, noise;
+  T D[3][3], w[3];
+  unsigned long long seed;
+  SrcDev src[kMaxSrc];
+};
+
+// Per-grid record read by the observation kernel (probes, flux).
+template <typename T>
+struct ObsGrid {
+  int nx, ny, nz;
+  int nprobe, nflux;
+  long long step;       // as StepGrid::step
+  long long step_end;
+  long long cap;        // recorder ring length (steps)
+  double dx2_over_eta0; // dx^2 / eta0
+  const T* F[2][6];
+  int probe[kMaxProbes][3];
+  T* probe_ring;        // [cap][nprobe][3]
+  int flux_axis[kMaxFlux], flux_index[kMaxFlux];
+  int flux_u0[kMaxFlux], flux_u1[kMaxFlux], flux_v0[kMaxFlux], flux_v1[kMaxFlux];
+  int flux_parts[kMaxFlux];
+  double flux_sign[kMaxFlux];
+  double* flux_ring;    // [cap][nflux]
+  double* partials;     // [kMaxFlux][kMaxFluxParts] scratch
+  unsigned int* counters;  // [kMaxFlux] scratch, zero between launches
+  int* err;             // bit 0: non-finite value seen
+};
+
+// Work items of the step kernel: (grid, x0, y0, z0 | z1 << 16).
+// Work items of the observation kernel: (grid, what, part, nparts) with
+// what = -1 for the probes and f >= 0 for flux plane f.
+
+template <typename T>
+cudaError_t launch_step(const StepGrid<T>* grids, const int4* items, int nitems, int offset, int bx, int by,
+                        bool gain, int grid_blocks, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_observe(const ObsGrid<T>* grids, const int4* items, int nitems, int offset, cudaStream_t st);
+
+// Shared-memory bytes of one step block.
+template <typename T>
+size_t step_smem_bytes(int bx, int by);
+
+// Advance every grid's step counters after a launch sequence of `count` steps.
+template <typename T>
+cudaError_t launch_advance(StepGrid<T>* sg, ObsGrid<T>* og, int ngrids, int count, cudaStream_t st);
+
+// Rasterization of binned spheres (see fdtd_set_eps_from_spheres).
+cudaError_t launch_rasterize(uint8_t* mat, int nx, int ny, int nz, const double* spheres, const int* bin_start,
+                             const int* bin_list, int bin, int bnx, int bny, int bnz, const double* box,
+                             cudaStream_t st);
+
+// Gain initialization: P slots zero, dN~ = init - N~eq in gain cells.
+template <typename T>
+cudaError_t launch_gain_init(const StepGrid<T>* g_host_copy, long long ncell, T d1, T d2, T d3, cudaStream_t st);
+
+// Field energy sum (eps_r E^2 + H~^2) over the cells in FP64; result in out[0].
+template <typename T>
+cudaError_t launch_energy(const T* const* F6, const uint8_t* mat, double e0, double e1, double e2,
+                          long long ncell, double* partials, unsigned int* counter, double* out, int* err,
+                          cudaStream_t st);
+
+// Convert between the run precision and double (read / write of state).
+template <typename T>
+cudaError_t launch_to_double(const T* src, double* dst, long long n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_from_double(const double* src, T* dst, long long n, cudaStream_t st);
+
+}  // namespace fdtd

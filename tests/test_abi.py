@@ -1,0 +1,74 @@
+"""The C ABI library loads and exports every function that include/fdtd.h
+declares; argument checks that need no GPU return the documented codes."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in ("fdtd.h",):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(fdtd_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0802_3775_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("fdtd_create_grid", "fdtd_set_eps_from_spheres", "fdtd_set_gain", "fdtd_add_source",
+                     "fdtd_step_n", "fdtd_read_probes"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_null_and_range_checks_without_gpu(lib):
+    from paper_0802_3775_gb300 import fdtd as F
+    L = F.load_library()
+    # null arguments are rejected before any device work
+    assert L.fdtd_create_grid(None, None, None, None) == -1
+    assert L.fdtd_step_n(None, 1) == -1
+    assert b"null" in L.fdtd_last_error()
+    d = F.GridDesc()
+    d.nx = d.ny = d.nz = 8
+    d.res, d.a, d.courant = 10.0, 480e-9, 0.5
+    d.eps[0] = d.eps[1] = d.eps[2] = 1.0
+    d.cpml_kappa_max = 1.0
+    d.record_capacity = 16
+    d.periodic[0] = 1
+    d.npml[0] = 2
+    h = ctypes.c_void_p()
+    assert L.fdtd_create_grid(ctypes.byref(d), None, None, ctypes.byref(h)) == -1  # slab on a periodic axis
+    d.periodic[0] = 0
+    d.npml[0] = 8
+    assert L.fdtd_create_grid(ctypes.byref(d), None, None, ctypes.byref(h)) == -1  # slab fills the axis
+    d.npml[0] = 2
+    d.courant = 1.5
+    assert L.fdtd_create_grid(ctypes.byref(d), None, None, ctypes.byref(h)) == -1  # unstable step
+    assert L.fdtd_destroy_grid(None) == 0
+    assert L.fdtd_version().startswith(b"fdtd-gb300")
+
+
+def test_create_without_device_fails_loudly(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_0802_3775_gb300 import fdtd as F
+    with pytest.raises(F.FdtdError) as e:
+        F.Grid((8, 8, 8), 10, allocator=None)
+    assert e.value.code == -3

@@ -1,0 +1,216 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Bars (FP32 against the oracle fed the same binary32-rounded coefficients):
+  FP64 fields: relative L2 <= 1e-12 over all six components;
+  FP32 passive fields: relative L2 <= 1e-5, flux series relative L2 <= 1e-4;
+  rasterization: bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import gpu_grid, oracle_grid, rel_l2, small_opal
+from paper_0802_3775_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0802_3775_gb300 import build
+    build.build()
+
+
+def _fields_gpu_vs_oracle(g, o):
+    return rel_l2(g.read_fields(), o.fields_memory_order())
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_rasterizer_bit_exact(seed):
+    from oracle.rasterize import rasterize
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = (37, 29, 33)
+    sph = np.column_stack([rng.uniform(-3, 40, 60), rng.uniform(-3, 32, 60), rng.uniform(-3, 36, 60),
+                           rng.uniform(0.5, 6.0, 60)])
+    # spheres whose surfaces pass through sample points exactly
+    sph = np.vstack([sph, [[10.0, 10.0, 10.0, 2.5], [20.5, 15.0, 12.0, 3.0], [5.0, 5.5, 7.0, 0.5]]])
+    lo, hi = (2, 3.5, 1), (35, 27, 31.5)
+    from paper_0802_3775_gb300.fdtd import Grid
+    g = Grid(shape, 12, precision="f32", eps=(1, 11.9, 1))
+    g.set_eps_from_spheres(sph, lo, hi)
+    assert np.array_equal(g.get_material(), rasterize(shape, sph, lo, hi))
+
+
+def test_rasterizer_opal_bit_exact():
+    from oracle.rasterize import rasterize
+    spec = inputs.opal_planewave_f32(ncell=3, res=14, npml=6, sigma=0.06, realization=2)
+    from paper_0802_3775_gb300.fdtd import Grid
+    g = Grid(spec.shape, spec.res, precision="f32", eps=spec.eps)
+    g.set_eps_from_spheres(spec.spheres, spec.box_lo, spec.box_hi)
+    assert np.array_equal(g.get_material(), rasterize(spec.shape, spec.spheres, spec.box_lo, spec.box_hi))
+
+
+def test_fp64_opal_dipole_40cubed_2000_steps():
+    """The 40^3 FP64 dipole workload in full: fields and probes after 2000 steps."""
+    spec = inputs.opal_dipole_f64(steps=2000)
+    g = gpu_grid(spec)
+    o = oracle_grid(spec)
+    g.step(spec.steps)
+    g.sync()
+    o.step(spec.steps)
+    err = _fields_gpu_vs_oracle(g, o)
+    assert err <= 1e-12, err
+    assert rel_l2(g.read_probes(), o.probe_series()) <= 1e-12
+
+
+@pytest.mark.parametrize("source", ["dipole", "sheet"])
+def test_fp64_small_opal_all_observers(source):
+    spec = small_opal(precision="f64", source=source)
+    g = gpu_grid(spec)
+    o = oracle_grid(spec)
+    g.step(400)
+    o.step(400)
+    assert _fields_gpu_vs_oracle(g, o) <= 1e-12
+    assert rel_l2(g.read_probes(), o.probe_series()) <= 1e-12
+    assert rel_l2(g.read_flux(), o.flux_series()) <= 1e-12
+    assert abs(g.field_energy() - o.energy()) <= 1e-12 * o.energy()
+
+
+@pytest.mark.parametrize("launch", [(32, 8, 0, 0), (64, 4, 7, 0), (32, 16, 3, 5), (16, 2, 0, 0)])
+def test_fp32_passive_fields_and_flux(launch):
+    spec = small_opal(precision="f32", source="sheet", sigma=0.08)
+    g = gpu_grid(spec)
+    g.set_launch(*launch)
+    o = oracle_grid(spec, coef32=True)
+    g.step(1200)
+    o.step(1200)
+    assert _fields_gpu_vs_oracle(g, o) <= 1e-5
+    assert rel_l2(g.read_flux(0), o.flux_series()[0]) <= 1e-4
+    assert rel_l2(g.read_probes(), o.probe_series()) <= 1e-5
+
+
+def test_results_do_not_depend_on_launch_shape():
+    spec = small_opal(precision="f32", source="dipole")
+    out = []
+    for launch in [(32, 8, 0, 0), (64, 4, 5, 0), (32, 4, 2, 3)]:
+        g = gpu_grid(spec)
+        g.set_launch(*launch)
+        g.step(150)
+        out.append((g.read_fields(), g.read_probes()))
+    for F, P in out[1:]:
+        assert np.array_equal(F, out[0][0])
+        assert np.array_equal(P, out[0][1])
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_periodic_plane_wave_on_gpu(precision):
+    """Discrete plane-wave eigenmode of a periodic box (Yee dispersion closed form)."""
+    shape = (16, 12, 20)
+    spec = inputs.RunSpec(shape=shape, res=12, periodic=(True, True, True), eps=(2.0, 2.0, 2.0), precision=precision)
+    from paper_0802_3775_gb300.fdtd import Grid
+    g = Grid.from_spec(spec)
+    g.set_material(np.full(shape[::-1], 0b010101, dtype=np.uint8))
+    S = 0.5 / math.sqrt(3)
+    m = (1, -2, 3)
+    k = np.array([2 * math.pi * m[d] / shape[d] for d in range(3)])
+    K = 2 * np.sin(k / 2)
+    Eh = np.cross(K, [0.2, 1.0, -0.4])
+    Eh /= np.linalg.norm(Eh)
+    Om = S * np.linalg.norm(K) / math.sqrt(2.0)
+    w = 2 * math.asin(Om / 2)
+    Hh = (S / Om) * np.cross(K, Eh)
+    NODE = [(0.5, 0, 0), (0, 0.5, 0), (0, 0, 0.5), (0, 0.5, 0.5), (0.5, 0, 0.5), (0.5, 0.5, 0)]
+
+    def field(c, t):
+        Z, Y, X = np.meshgrid(np.arange(shape[2]) + NODE[c][2], np.arange(shape[1]) + NODE[c][1],
+                              np.arange(shape[0]) + NODE[c][0], indexing="ij")
+        amp = Eh[c] if c < 3 else Hh[c - 3]
+        return amp * np.cos(k[0] * X + k[1] * Y + k[2] * Z - w * t)
+
+    g.write_fields(np.stack([field(c, 0.0 if c < 3 else -0.5) for c in range(6)]))
+    N = 500
+    g.step(N)
+    ref = np.stack([field(c, N if c < 3 else N - 0.5) for c in range(6)])
+    tol = 1e-11 if precision == "f64" else 2e-5
+    assert rel_l2(g.read_fields(), ref) <= tol
+
+
+def test_fp64_gain_with_noise_matches_oracle():
+    gain = inputs.GainSpec(n_total=1e24, fa_hat=0.8, dw_rel=0.02, tau32=100e-15, tau21=1e-9, tau10=100e-15,
+                           pump=5e11, noise_amp=1e-3, init="steady")
+    spec = small_opal(n_cells=2, res=8, npml=5, precision="f64", source="dipole", gain=gain)
+    g = gpu_grid(spec)
+    o = oracle_grid(spec)
+    g.step(300)
+    o.step(300)
+    assert _fields_gpu_vs_oracle(g, o) <= 1e-12
+    for what in range(2):
+        P = g.read_gain(what)
+        Po = (o.P if what == 0 else o.Pm).transpose(0, 3, 2, 1)
+        assert rel_l2(P, Po) <= 1e-12
+    dN = g.read_gain(3)
+    assert rel_l2(dN, o.dN[1:].transpose(0, 3, 2, 1)) <= 1e-9
+    N = g.read_gain(2)
+    assert rel_l2(N, o.populations()[1:].transpose(0, 3, 2, 1)) <= 1e-14
+
+
+def test_fp32_gain_short_run():
+    gain = inputs.GainSpec(n_total=1e24, fa_hat=0.8, dw_rel=0.02, tau32=100e-15, tau21=1e-9, tau10=100e-15,
+                           pump=5e11, noise_amp=1e-3, init="ground")
+    spec = small_opal(n_cells=2, res=8, npml=5, precision="f32", source="dipole", gain=gain)
+    g = gpu_grid(spec)
+    o = oracle_grid(spec, coef32=True)
+    g.step(300)
+    o.step(300)
+    assert _fields_gpu_vs_oracle(g, o) <= 1e-5
+    # populations relax from the ground state: deviations carried in binary32
+    # with compensated sums
+    assert rel_l2(g.read_gain(3), o.dN[1:].transpose(0, 3, 2, 1)) <= 1e-6
+
+
+def test_full_size_planewave_grid_few_steps():
+    """184^3 FP32 disordered-opal grid in its default launch shape: 4 steps from
+    seeded random fields, every cell compared with the oracle."""
+    spec = inputs.opal_planewave_f32(ncell=8, res=20, npml=12, sigma=0.06, realization=1)
+    g = gpu_grid(spec)
+    o = oracle_grid(spec, coef32=True)
+    F = inputs.random_fields(spec.shape, seed=5, scale=1.0)
+    g.write_fields(F)
+    o.set_fields_memory_order(F.astype(np.float32).astype(np.float64))
+    g.step(4)
+    o.step(4)
+    assert _fields_gpu_vs_oracle(g, o) <= 1e-6
+
+
+def test_checkpoint_restart_is_bitwise():
+    spec = small_opal(precision="f32", source="dipole")
+    a = gpu_grid(spec)
+    a.step(200)
+    ref = a.read_fields()
+    b = gpu_grid(spec)
+    b.step(120)
+    import tempfile, os
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        b.save_state(path)
+        c = gpu_grid(spec)
+        c.load_state(path)
+    c.step(80)
+    assert np.array_equal(c.read_fields(), ref)
+    assert np.array_equal(c.read_probes(t0=120, count=80), a.read_probes(t0=120, count=80))
+
+
+def test_nonfinite_values_are_reported():
+    from paper_0802_3775_gb300.fdtd import FdtdError
+    spec = small_opal(precision="f32", source="dipole")
+    spec.sources[0].amplitude = 3e38
+    g = gpu_grid(spec)
+    g.step(400)
+    with pytest.raises(FdtdError) as e:
+        g.sync()
+    assert e.value.code == -5
