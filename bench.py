@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 Maxwell-Bloch FDTD hot path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--workload NAME]
+
+One "step" is one time step n -> n+1 of every realization in the workload
+(H and E updates with CPML, sources, gain polarization / populations / noise,
+probes and flux).  Metric: Mcell-updates/s = sum over realizations of
+cells x steps / time.  Prints ONE JSON line on rank 0.
+
+Under torchrun each rank steps its own realizations (different disorder
+seeds) with no collective on the data path (weak scaling); the timed region is
+bracketed by barriers and the max over ranks is reported.
+
+--impl reference times the FP64 CPU oracle (the reference of this build) on a
+bounded sample of the same workload, on the host cores, rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0802_3775_gb300 import inputs  # noqa: E402
+
+METRIC = "Mcell-updates/s"
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- workloads
+def workload_specs(name: str, rank: int, steps: int):
+    """Run records of one rank's share of the workload."""
+    if name == "planewave":
+        # 8x8x8 unit cells at 20 cells/a + 12-cell CPML = 184^3, FP32, sigma 6 %
+        return [inputs.opal_planewave_f32(ncell=8, res=20, npml=12, sigma=0.06, realization=rank, steps=steps)]
+    if name == "lasing":
+        # 6x6x6 unit cells at 20 cells/a + 10-cell CPML = 140^3, FP32 gain
+        return [inputs.opal_lasing_f32(ncell=6, res=20, npml=10, sigma=0.05, pump=1e10, realization=rank,
+                                       steps=steps)]
+    if name == "dipole64":
+        return [inputs.opal_dipole_f64(steps=steps)]
+    if name == "planewave64":
+        return [inputs.opal_planewave_f32(ncell=8, res=20, npml=12, sigma=0.06, realization=rank, steps=steps,
+                                          precision="f64")]
+    raise SystemExit(f"unknown workload {name}")
+
+
+WORKLOAD_TEXT = {
+    "planewave": "passive disordered fcc inverted opal, 8x8x8 unit cells at 20 cells/a + 12-cell CPML (184^3), "
+                 "FP32, sigma 6%, [111] plane-wave Gaussian pulse f=0.80 bw 0.1, FP64 flux plane, 8 probes",
+    "lasing": "Maxwell-Bloch lasing opal, 6x6x6 unit cells at 20 cells/a + 10-cell CPML (140^3), FP32, four-level "
+              "gain in spheres, pump 1e10/s, noise 1e-6, 6-face flux box, 8 probes",
+    "dipole64": "passive fcc opal 2x2x2 unit cells at 12 cells/a + 8-cell CPML (40^3), FP64, Ez dipole pulse",
+    "planewave64": "as planewave but FP64 (plain single-run FP64 GPU path)",
+}
+
+
+def algorithmic_bytes(spec, gain_cells: int) -> float:
+    """Compulsory HBM bytes of one step-kernel launch: every state word read
+    once and written once, material read once (see the design notes)."""
+    w = 4 if spec.precision == "f32" else 8
+    nx, ny, nz = spec.shape
+    ncell = nx * ny * nz
+    b = ncell * (12 * w + 1)
+    n3 = (nx, ny, nz)
+    for d in range(3):
+        slab = spec.npml[2 * d] + spec.npml[2 * d + 1]
+        b += slab * (ncell // n3[d]) * 8 * w
+    if spec.gain is not None:
+        b += gain_cells * (21 if w == 4 else 15) * w
+    return float(b)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), active=parts[4], hw=parts[5], hwt=parts[6],
+                                 swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        smax = max(r["smax"] for r in rows)
+        load = [r["sm"] for r in rows if r["sm"] > 0.3 * smax] or [r["sm"] for r in rows]
+        reasons = set()
+        for r in rows:
+            if r["hw"] == "Active":
+                reasons.add("hw_slowdown")
+            if r["hwt"] == "Active":
+                reasons.add("hw_thermal_slowdown")
+            if r["swt"] == "Active":
+                reasons.add("sw_thermal_slowdown")
+            if r["pcap"] == "Active":
+                reasons.add("sw_power_cap")
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world, dist):
+    import torch
+
+    from paper_0802_3775_gb300 import build
+    from paper_0802_3775_gb300.fdtd import Grid
+
+    build.build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    specs = workload_specs(args.workload, rank, args.steps + args.warmup)
+    cap = args.steps + args.warmup + 16
+    grids = [Grid.from_spec(s, record_capacity=cap) for s in specs]
+    gain_cells = []
+    for g, s in zip(grids, specs):
+        gain_cells.append(int(np.count_nonzero(g.get_material() & 64)) if s.gain is not None else 0)
+    for g in grids:
+        g.step(args.warmup)
+    for g in grids:
+        g.sync()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # timed region: device events on the grids' stream (torch's current stream)
+    stream = torch.cuda.current_stream()
+    for g in grids:
+        g.set_timing(True)
+    clocks = ClockSampler()
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for g in grids:
+        g.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    kernel = [g.kernel_time() for g in grids]
+    for g in grids:
+        g.set_timing(False)
+        g.sync()
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    cells = sum(s.cells for s in specs)
+    value = cells * args.steps * world / (ms_max * 1e-3) / 1e6
+
+    # roofline of the step kernel (dominant): algorithmic bytes per launch / mean launch time
+    peak, peak_kind = measured_peaks()
+    kms = sum(k[0] for k in kernel)
+    klaunch = sum(k[1] for k in kernel)
+    bytes_step = sum(algorithmic_bytes(s, gc) for s, gc in zip(specs, gain_cells))
+    per_launch_ms = kms / max(klaunch, 1) * len(grids)
+    achieved = bytes_step / (per_launch_ms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            traffic = json.load(f).get("dram_bytes_per_launch")
+
+    # end to end through the public API with host inputs and host results
+    e2e = run_e2e(args, specs, rank, dist)
+
+    launches = args.steps * len(grids) * 2 + len(grids)
+    result = {
+        "metric": METRIC, "value": round(value, 1), "unit": "Mcell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if specs[0].precision == "f32" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload], "grids_per_gpu": len(specs),
+                   "cells_per_gpu": cells, "l2": "state larger than L2 (%.0f MB per GPU)" %
+                   (sum(s.cells for s in specs) * (49 if specs[0].precision == "f32" else 97) / 1e6),
+                   "parallelism": f"replicas x{world} (independent realizations)"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": "k_step", "algorithmic_bytes_per_launch": bytes_step,
+                     "mean_launch_ms": round(per_launch_ms, 5), "peak_source": f"{peak_kind} hbm_gbs"},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": ck,
+    }
+    if rank == 0:
+        result["cpu_baseline"] = cpu_baseline(args)
+        print(json.dumps(result))
+    for g in grids:
+        g.close()
+
+
+def run_e2e(args, specs, rank, dist):
+    """Same metric through the public API: host sphere lists and parameters in,
+    host probe / flux series out, all inside the timed region."""
+    import torch
+
+    from paper_0802_3775_gb300.fdtd import Grid
+
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    h2d = d2h = 0
+    t0 = time.perf_counter()
+    for s in specs:
+        g = Grid.from_spec(s, record_capacity=args.steps + 16)
+        h2d += s.spheres.nbytes if s.spheres is not None else 0
+        g.step(args.steps)
+        fl = g.read_flux()
+        pr = g.read_probes()
+        d2h += fl.nbytes // 2 + pr.nbytes // (2 if s.precision == "f32" else 1)
+        g.close()
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    if dist is not None:
+        tt = torch.tensor([t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    world = dist.get_world_size() if dist is not None else 1
+    cells = sum(s.cells for s in specs)
+    return {"value": round(cells * args.steps * world / t / 1e6, 1), "unit": "Mcell-updates/s",
+            "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": round(d2h / args.steps, 1),
+            "includes": "grid creation, device rasterization, set-up, steps, series read-back"}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def _oracle_sample(spec, seconds: float):
+    """Time the FP64 oracle on `spec` for about `seconds`; returns (Mcell/s, steps, cells)."""
+    from oracle import Oracle
+    o = Oracle.from_spec(spec)
+    o.step(1)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        o.step(1)
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    t = time.perf_counter() - t0
+    return spec.cells * n / t / 1e6, n, spec.cells
+
+
+def cpu_baseline(args, seconds: float = 12.0):
+    spec = workload_specs(args.workload, 0, 1)[0]
+    v, n, cells = _oracle_sample(spec, seconds)
+    return {"value": round(v, 3), "unit": "Mcell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} steps of one {spec.shape[0]}x{spec.shape[1]}x{spec.shape[2]} realization of the "
+                      f"workload (numpy FP64, single thread)"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    spec = workload_specs(args.workload, 0, 1)[0]
+    budget = 150.0
+    per_step = budget / max(1, args.steps + args.warmup)
+    # shrink the sample grid until one oracle step fits the per-step budget
+    sample = spec
+    from oracle import Oracle
+    probe = Oracle.from_spec(sample)
+    t0 = time.perf_counter()
+    probe.step(1)
+    t1 = time.perf_counter() - t0
+    note = "full realization"
+    if t1 > per_step:
+        shrink = max(0.2, (per_step / t1) ** (1 / 3))
+        if sample.gain is not None:
+            ncell = max(2, int(round(6 * shrink)))
+            sample = inputs.opal_lasing_f32(ncell=ncell, res=20, npml=10, sigma=0.05, pump=1e10)
+        else:
+            ncell = max(2, int(round(8 * shrink)))
+            sample = inputs.opal_planewave_f32(ncell=ncell, res=20, npml=12, sigma=0.06,
+                                               precision=spec.precision)
+        note = f"{ncell}^3 unit cells ({sample.shape[0]}^3 grid) of the same workload"
+        probe = Oracle.from_spec(sample)
+    for _ in range(args.warmup):
+        probe.step(1)
+    t0 = time.perf_counter()
+    probe.step(args.steps)
+    t = time.perf_counter() - t0
+    value = sample.cells * args.steps / t / 1e6
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "Mcell-updates/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload]},
+        "cpu_baseline": {"value": round(value, 3), "unit": "Mcell-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": note + ", numpy FP64 oracle, single thread"},
+        "e2e": {"value": round(value, 3), "unit": "Mcell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="planewave")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        td.init_process_group("nccl")
+        dist = td
+    run_gpu(args, rank, world, dist)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

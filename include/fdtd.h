@@ -193,6 +193,13 @@ int fdtd_step_n(fdtd_grid* g, int64_t n);
  * depend on the shape.  Needs bx, by >= 2, bx*by a multiple of 32, <= 512. */
 int fdtd_set_launch(fdtd_grid* g, int32_t bx, int32_t by, int32_t zdepth, int32_t grid_blocks);
 
+/* Per-launch timing of the step kernel: while on, every step-kernel launch
+ * is bracketed by a pair of CUDA events on the grid's stream.
+ * fdtd_kernel_time synchronizes and returns the summed duration (ms) and the
+ * number of step-kernel launches since timing was switched on. */
+int fdtd_set_timing(fdtd_grid* g, int32_t on);
+int fdtd_kernel_time(fdtd_grid* g, double* ms, int64_t* launches);
+
 /* Wait for the grid's stream; returns E_NONFINITE if the device raised the
  * non-finite flag (checked on probes, flux and energy). */
 int fdtd_sync(fdtd_grid* g);

@@ -306,6 +306,32 @@ int fdtd_step_n(fdtd_grid* g, int64_t n) {
   });
 }
 
+int fdtd_set_timing(fdtd_grid* g, int32_t on) {
+  return guarded([&]() -> int {
+    CHECK_GRID(g);
+    cudaError_t e = cudaStreamSynchronize(G->stream);
+    if (e != cudaSuccess) return fdtd::cuda_error(e, "sync");
+    G->timer.collect();
+    G->timer.on = on != 0;
+    G->timer.ms = 0.0;
+    G->timer.launches = 0;
+    return FDTD_OK;
+  });
+}
+
+int fdtd_kernel_time(fdtd_grid* g, double* ms, int64_t* launches) {
+  return guarded([&]() -> int {
+    CHECK_GRID(g);
+    if (!ms || !launches) return set_error(FDTD_E_INVAL, "null output");
+    cudaError_t e = cudaStreamSynchronize(G->stream);
+    if (e != cudaSuccess) return fdtd::cuda_error(e, "sync");
+    G->timer.collect();
+    *ms = G->timer.ms;
+    *launches = G->timer.launches;
+    return FDTD_OK;
+  });
+}
+
 int fdtd_sync(fdtd_grid* g) {
   return guarded([&]() -> int {
     CHECK_GRID(g);

@@ -447,8 +447,15 @@ struct GridImpl final : GridBase {
     while (done < n) {
       const int chunk = (int)std::min<long long>(n - done, 1 << 20);
       for (int s = 0; s < chunk; ++s) {
+        const auto ev = timer.next();
+        if (ev.first) cudaEventRecord(ev.first, stream);
         if ((e = launch_step<T>(d_sg, d_items, (int)items.size(), s, bx, by, sg.gain != 0, grid_blocks, stream)) != cudaSuccess)
           return cuda_error(e, "step kernel");
+        if (ev.second) cudaEventRecord(ev.second, stream);
+        if (timer.used >= 4096) {
+          if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "sync");
+          timer.collect();
+        }
         if (!oitems.empty() && (e = launch_observe<T>(d_og, d_oitems, (int)oitems.size(), s, stream)) != cudaSuccess)
           return cuda_error(e, "observe kernel");
       }

@@ -26,6 +26,46 @@ struct DeviceMemory {
   size_t total() const;
 };
 
+// Event pairs bracketing kernel launches (optional per-launch timing).
+struct LaunchTimer {
+  bool on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
+  size_t used = 0;
+  double ms = 0.0;
+  long long launches = 0;
+  ~LaunchTimer() {
+    for (auto& e : pool) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+  }
+  // events for the next launch (nullptr pair when off)
+  std::pair<cudaEvent_t, cudaEvent_t> next() {
+    if (!on) return {nullptr, nullptr};
+    if (used == pool.size()) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess) return {nullptr, nullptr};
+      if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return {nullptr, nullptr};
+      }
+      pool.push_back({a, b});
+    }
+    return pool[used++];
+  }
+  // fold the recorded pairs into the totals (caller synchronized the stream)
+  void collect() {
+    for (size_t q = 0; q < used; ++q) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, pool[q].first, pool[q].second) == cudaSuccess) {
+        ms += t;
+        launches++;
+      }
+    }
+    used = 0;
+  }
+};
+
 // Precision-independent interface of a grid; GridImpl<T> implements it.
 struct GridBase {
   fdtd_grid_desc desc{};
@@ -38,6 +78,7 @@ struct GridBase {
   bool finalized = false;
   int bx = 32, by = 8, zdepth = 0, grid_blocks = 0;
   uint8_t* d_mat = nullptr;
+  LaunchTimer timer;
 
   virtual ~GridBase() { mem.release_all(); }
   virtual int precision() const = 0;

@@ -81,6 +81,8 @@ SIGNATURES = {
     "fdtd_write_fields": [_P, C.c_int32, _D],
     "fdtd_read_gain": [_P, C.c_int32, _D],
     "fdtd_field_energy": [_P, _D],
+    "fdtd_set_timing": [_P, C.c_int32],
+    "fdtd_kernel_time": [_P, _D, C.POINTER(C.c_int64)],
     "fdtd_save_state": [_P, C.c_char_p],
     "fdtd_load_state": [_P, C.c_char_p],
 }
@@ -266,6 +268,16 @@ class Grid:
         n = C.c_int64()
         check(self._lib.fdtd_steps_done(self.h, C.byref(n)))
         return n.value
+
+    def set_timing(self, on=True):
+        check(self._lib.fdtd_set_timing(self.h, int(bool(on))))
+
+    def kernel_time(self):
+        """(summed step-kernel milliseconds, launches) since timing was switched on."""
+        ms = C.c_double()
+        n = C.c_int64()
+        check(self._lib.fdtd_kernel_time(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
 
     # -- read-backs
     def read_probes(self, pid=None, t0=0, count=None):
