@@ -57,6 +57,9 @@ def workload_specs(name: str, rank: int, steps: int):
                                        steps=steps)]
     if name == "dipole64":
         return [inputs.opal_dipole_f64(steps=steps)]
+    if name == "batch":
+        # 64 mixed-size realizations, half passive, half lasing (one launch per step)
+        return inputs.mixed_batch(64, seed=4000 + 1000 * rank, steps=steps)
     if name == "planewave64":
         return [inputs.opal_planewave_f32(ncell=8, res=20, npml=12, sigma=0.06, realization=rank, steps=steps,
                                           precision="f64")]
@@ -70,6 +73,9 @@ WORKLOAD_TEXT = {
               "gain in spheres, pump 1e10/s, noise 1e-6, 6-face flux box, 8 probes",
     "dipole64": "passive fcc opal 2x2x2 unit cells at 12 cells/a + 8-cell CPML (40^3), FP64, Ez dipole pulse",
     "planewave64": "as planewave but FP64 (plain single-run FP64 GPU path)",
+    "batch": "64 disorder realizations of mixed size (4^3..8^3 unit cells at 16..20 cells/a + 12-cell CPML, "
+             "sigma U(0,10%)), even ones passive [111] plane-wave runs, odd ones four-level lasing runs, FP32, "
+             "all stepped together by one step-kernel launch per time step",
 }
 
 
@@ -159,19 +165,23 @@ def run_gpu(args, rank, world, dist):
     gain_cells = []
     for g, s in zip(grids, specs):
         gain_cells.append(int(np.count_nonzero(g.get_material() & 64)) if s.gain is not None else 0)
-    for g in grids:
-        g.step(args.warmup)
-    for g in grids:
-        g.sync()
+    batch = None
+    if len(grids) > 1:
+        from paper_0802_3775_gb300.fdtd import Batch
+        batch = Batch(grids)
+        stepper = batch
+    else:
+        stepper = grids[0]
+    stepper.step(args.warmup)
+    stepper.sync()
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    # timed region: device events on the grids' stream (torch's current stream)
+    # timed region: device events on the stream the kernels run on (torch's current stream)
     stream = torch.cuda.current_stream()
-    for g in grids:
-        g.set_timing(True)
+    stepper.set_timing(True)
     clocks = ClockSampler()
     clocks.start()
     time.sleep(0.3)
@@ -180,17 +190,15 @@ def run_gpu(args, rank, world, dist):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for g in grids:
-        g.step(args.steps)
+    stepper.step(args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    kernel = [g.kernel_time() for g in grids]
-    for g in grids:
-        g.set_timing(False)
-        g.sync()
+    kernel = [stepper.kernel_time()]
+    stepper.set_timing(False)
+    stepper.sync()
     ms_max = ms
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
@@ -204,7 +212,7 @@ def run_gpu(args, rank, world, dist):
     kms = sum(k[0] for k in kernel)
     klaunch = sum(k[1] for k in kernel)
     bytes_step = sum(algorithmic_bytes(s, gc) for s, gc in zip(specs, gain_cells))
-    per_launch_ms = kms / max(klaunch, 1) * len(grids)
+    per_launch_ms = kms / max(klaunch, 1)
     achieved = bytes_step / (per_launch_ms * 1e-3) / 1e9
     traffic = None
     prof = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
@@ -215,7 +223,7 @@ def run_gpu(args, rank, world, dist):
     # end to end through the public API with host inputs and host results
     e2e = run_e2e(args, specs, rank, dist)
 
-    launches = args.steps * len(grids) * 2 + len(grids)
+    launches = args.steps * 2 + 1
     result = {
         "metric": METRIC, "value": round(value, 1), "unit": "Mcell-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5),
@@ -224,10 +232,11 @@ def run_gpu(args, rank, world, dist):
         "config": {"workload": WORKLOAD_TEXT[args.workload], "grids_per_gpu": len(specs),
                    "cells_per_gpu": cells, "l2": "state larger than L2 (%.0f MB per GPU)" %
                    (sum(s.cells for s in specs) * (49 if specs[0].precision == "f32" else 97) / 1e6),
-                   "parallelism": f"replicas x{world} (independent realizations)"},
+                   "parallelism": f"replicas x{world} (independent realizations)",
+                   "launch": "direct launches with per-launch events in the timed region"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "k_step", "algorithmic_bytes_per_launch": bytes_step,
+                     "kernel": "k_step_tma", "algorithmic_bytes_per_launch": bytes_step,
                      "mean_launch_ms": round(per_launch_ms, 5), "peak_source": f"{peak_kind} hbm_gbs"},
         "e2e": e2e,
         "gpu_launches": launches,
@@ -236,6 +245,8 @@ def run_gpu(args, rank, world, dist):
     if rank == 0:
         result["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(result))
+    if batch is not None:
+        batch.close()
     for g in grids:
         g.close()
 
@@ -252,13 +263,24 @@ def run_e2e(args, specs, rank, dist):
     torch.cuda.synchronize()
     h2d = d2h = 0
     t0 = time.perf_counter()
+    gs = []
     for s in specs:
         g = Grid.from_spec(s, record_capacity=args.steps + 16)
         h2d += s.spheres.nbytes if s.spheres is not None else 0
-        g.step(args.steps)
+        gs.append(g)
+    if len(gs) > 1:
+        from paper_0802_3775_gb300.fdtd import Batch
+        b = Batch(gs)
+        b.set_graph(min(50, args.steps))
+        b.step(args.steps)
+        b.sync()
+        b.close()
+    else:
+        gs[0].step(args.steps)
+    for s, g in zip(specs, gs):
         fl = g.read_flux()
         pr = g.read_probes()
-        d2h += fl.nbytes // 2 + pr.nbytes // (2 if s.precision == "f32" else 1)
+        d2h += fl.nbytes + pr.nbytes // (2 if s.precision == "f32" else 1)
         g.close()
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
@@ -270,7 +292,8 @@ def run_e2e(args, specs, rank, dist):
     cells = sum(s.cells for s in specs)
     return {"value": round(cells * args.steps * world / t / 1e6, 1), "unit": "Mcell-updates/s",
             "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": round(d2h / args.steps, 1),
-            "includes": "grid creation, device rasterization, set-up, steps, series read-back"}
+            "includes": "grid creation from host sphere lists, device rasterization, set-up, steps "
+                        "(CUDA-graph replays for batches), probe and flux series read back to the host"}
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -291,7 +314,8 @@ def _oracle_sample(spec, seconds: float):
 
 
 def cpu_baseline(args, seconds: float = 12.0):
-    spec = workload_specs(args.workload, 0, 1)[0]
+    specs = workload_specs(args.workload, 0, 1)
+    spec = specs[1] if len(specs) > 1 and specs[1].gain is not None else specs[0]
     v, n, cells = _oracle_sample(spec, seconds)
     return {"value": round(v, 3), "unit": "Mcell-updates/s", "cores": 1, "kind": "oracle",
             "sample": f"{n} steps of one {spec.shape[0]}x{spec.shape[1]}x{spec.shape[2]} realization of the "

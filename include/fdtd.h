@@ -193,6 +193,13 @@ int fdtd_step_n(fdtd_grid* g, int64_t n);
  * depend on the shape.  Needs bx, by >= 2, bx*by a multiple of 32, <= 512. */
 int fdtd_set_launch(fdtd_grid* g, int32_t bx, int32_t by, int32_t zdepth, int32_t grid_blocks);
 
+/* Step-kernel variant: 0 = automatic (the TMA-staged kernel when no axis is
+ * periodic, else the plain-load kernel), 1 = plain-load kernel (blocks of
+ * bx x by threads own (bx-1) x (by-1) columns), 2 = TMA-staged kernel (blocks
+ * of 32 x by threads own 32 x by columns; E_INVAL on periodic grids).  Both
+ * perform the same arithmetic per node and give identical results. */
+int fdtd_set_kernel(fdtd_grid* g, int32_t kind);
+
 /* Per-launch timing of the step kernel: while on, every step-kernel launch
  * is bracketed by a pair of CUDA events on the grid's stream.
  * fdtd_kernel_time synchronizes and returns the summed duration (ms) and the
@@ -231,6 +238,35 @@ int fdtd_read_gain(fdtd_grid* g, int32_t what, double* out);
  * current time level (E^n, H~^{n-1/2}), reduced on the device in FP64 in a
  * fixed order (bitwise reproducible for a given grid size). */
 int fdtd_field_energy(fdtd_grid* g, double* out);
+
+/* Stop a grid at update `limit`: steps n >= limit are not performed (by
+ * fdtd_step_n or a batch).  Default: no limit. */
+int fdtd_set_step_limit(fdtd_grid* g, int64_t limit);
+
+/* ---------------------------------------------------------------- batches
+ * Many grids of mixed size stepped together (the disorder realizations of the
+ * paper, Sec. "Wide-band excitation and gap filling", are independent runs):
+ * one step-kernel launch per time step covers the work items of every member,
+ * followed by one observation launch.  Members keep their own counters and
+ * step limits; reads go through the member grids as usual.  All members must
+ * have the same precision; the batch does not own them (destroy the batch
+ * first).  Set-up of the members must be complete (their first step freezes
+ * it).  Work is enqueued on the batch's stream; member streams are made to
+ * wait for it. */
+typedef struct fdtd_batch fdtd_batch;
+int fdtd_batch_create(fdtd_grid* const* grids, int32_t n, void* stream, fdtd_batch** out);
+int fdtd_batch_destroy(fdtd_batch* b);
+/* kernel: as fdtd_set_kernel; by: rows of the tile; zdepth: planes per work
+ * item (0: whole z); grid_blocks > 0: persistent launch with that many blocks. */
+int fdtd_batch_set_launch(fdtd_batch* b, int32_t kernel, int32_t by, int32_t zdepth, int32_t grid_blocks);
+/* Capture `steps_per_graph` steps (step + observation launches and the
+ * counter update) into a CUDA graph replayed by fdtd_batch_step_n; 0 = off.
+ * Per-launch timing (fdtd_batch_set_timing) uses direct launches. */
+int fdtd_batch_set_graph(fdtd_batch* b, int32_t steps_per_graph);
+int fdtd_batch_step_n(fdtd_batch* b, int64_t n);
+int fdtd_batch_sync(fdtd_batch* b);
+int fdtd_batch_set_timing(fdtd_batch* b, int32_t on);
+int fdtd_batch_kernel_time(fdtd_batch* b, double* ms, int64_t* launches);
 
 /* Checkpoint: write / read every state array (fields, CPML slabs, gain state,
  * step count, recorders) to / from a file.  load requires a grid created

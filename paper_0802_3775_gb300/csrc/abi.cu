@@ -11,6 +11,7 @@
 
 #include "../../include/fdtd.h"
 #include "fdtd_api_internal.h"
+#include "fdtd_batch_internal.h"
 #include "fdtd_internal.cuh"
 
 using fdtd::GridBase;
@@ -176,7 +177,8 @@ int fdtd_set_eps_from_spheres(fdtd_grid* g, const double* spheres, int64_t n, co
       e = cudaMemcpyAsync(dlist, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, G->stream);
     const double box[6] = {box_lo[0], box_lo[1], box_lo[2], box_hi[0], box_hi[1], box_hi[2]};
     if (e == cudaSuccess)
-      e = fdtd::launch_rasterize(G->d_mat, d.nx, d.ny, d.nz, dsph, dstart, dlist, B, bn[0], bn[1], bn[2], box, G->stream);
+      e = fdtd::launch_rasterize(G->d_mat, d.nx, d.ny, d.nz, G->px, dsph, dstart, dlist, B, bn[0], bn[1], bn[2], box,
+                                 G->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(G->stream);
     tmp.release_all();
     if (e != cudaSuccess) return fdtd::cuda_error(e, "rasterize");
@@ -190,9 +192,8 @@ int fdtd_set_material(fdtd_grid* g, const uint8_t* mat) {
     CHECK_GRID(g);
     BEFORE_FIRST_STEP(G, "fdtd_set_material");
     if (!mat) return set_error(FDTD_E_INVAL, "null material");
-    cudaError_t e = cudaMemcpyAsync(G->d_mat, mat, (size_t)G->ncell, cudaMemcpyHostToDevice, G->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(G->stream);
-    if (e != cudaSuccess) return fdtd::cuda_error(e, "set material");
+    const int r = G->set_material(mat);
+    if (r != FDTD_OK) return r;
     G->material_set = true;
     return FDTD_OK;
   });
@@ -294,6 +295,23 @@ int fdtd_set_launch(fdtd_grid* g, int32_t bx, int32_t by, int32_t zdepth, int32_
   });
 }
 
+int fdtd_set_kernel(fdtd_grid* g, int32_t kind) {
+  return guarded([&]() -> int {
+    CHECK_GRID(g);
+    if (kind < 0 || kind > 2) return set_error(FDTD_E_INVAL, "kernel kind must be 0 (auto), 1 (plain) or 2 (TMA)");
+    const fdtd_grid_desc& d = G->desc;
+    if (kind == 2 && (d.periodic[0] || d.periodic[1] || d.periodic[2]))
+      return set_error(FDTD_E_INVAL, "the TMA step kernel does not handle periodic axes");
+    G->kernel_kind = kind;
+    if (G->finalized) {
+      cudaError_t e = cudaStreamSynchronize(G->stream);
+      if (e != cudaSuccess) return fdtd::cuda_error(e, "sync");
+      return G->replan();
+    }
+    return FDTD_OK;
+  });
+}
+
 int fdtd_step_n(fdtd_grid* g, int64_t n) {
   return guarded([&]() -> int {
     CHECK_GRID(g);
@@ -339,6 +357,7 @@ int fdtd_sync(fdtd_grid* g) {
     const int r = G->error_flags(&flags);
     if (r != FDTD_OK) return r;
     if (flags & 1) return set_error(FDTD_E_NONFINITE, "a probe, flux or energy value is not finite");
+    if (flags & 2) return set_error(FDTD_E_TIMEOUT, "a bounded wait of the step kernel ran out");
     return FDTD_OK;
   });
 }
@@ -413,6 +432,131 @@ int fdtd_field_energy(fdtd_grid* g, double* out) {
     CHECK_GRID(g);
     if (!out) return set_error(FDTD_E_INVAL, "null output");
     return G->energy(out);
+  });
+}
+
+int fdtd_set_step_limit(fdtd_grid* g, int64_t limit) {
+  return guarded([&]() -> int {
+    CHECK_GRID(g);
+    if (limit < 0) return set_error(FDTD_E_INVAL, "negative step limit");
+    G->step_limit = limit;
+    G->tables_dirty = true;
+    return FDTD_OK;
+  });
+}
+
+#define CHECK_BATCH(b)                                                  \
+  if (!(b) || !(b)->impl) return set_error(FDTD_E_INVAL, "null batch"); \
+  fdtd::BatchBase* B = (b)->impl
+
+int fdtd_batch_create(fdtd_grid* const* grids, int32_t n, void* stream, fdtd_batch** out) {
+  return guarded([&]() -> int {
+    if (!grids || !out || n < 1) return set_error(FDTD_E_INVAL, "need at least one grid and an output");
+    *out = nullptr;
+    int prec = -1;
+    for (int q = 0; q < n; ++q) {
+      if (!grids[q] || !grids[q]->impl) return set_error(FDTD_E_INVAL, "null member %d", q);
+      GridBase* G = grids[q]->impl;
+      if (!G->material_set) return set_error(FDTD_E_STATE, "member %d has no permittivity map", q);
+      if (prec >= 0 && G->precision() != prec) return set_error(FDTD_E_INVAL, "members differ in precision");
+      prec = G->precision();
+      for (int r = 0; r < q; ++r)
+        if (grids[r] == grids[q]) return set_error(FDTD_E_INVAL, "member %d listed twice", q);
+    }
+    fdtd::BatchBase* B = fdtd::make_batch(prec);
+    if (!B) return set_error(FDTD_E_NOMEM, "host allocation failed");
+    for (int q = 0; q < n; ++q) B->grids.push_back(grids[q]->impl);
+    B->stream = (cudaStream_t)stream;
+    B->mem.stream = stream;
+    *out = new fdtd_batch{B};
+    return FDTD_OK;
+  });
+}
+
+int fdtd_batch_destroy(fdtd_batch* b) {
+  return guarded([&]() -> int {
+    if (!b) return FDTD_OK;
+    if (b->impl) {
+      cudaStreamSynchronize(b->impl->stream);
+      delete b->impl;
+    }
+    delete b;
+    return FDTD_OK;
+  });
+}
+
+int fdtd_batch_set_launch(fdtd_batch* b, int32_t kernel, int32_t by, int32_t zdepth, int32_t grid_blocks) {
+  return guarded([&]() -> int {
+    CHECK_BATCH(b);
+    if (kernel < 0 || kernel > 2 || by < 2 || by > 16 || zdepth < 0 || grid_blocks < 0)
+      return set_error(FDTD_E_INVAL, "batch launch shape");
+    B->kernel_kind = kernel;
+    B->bx = 32;
+    B->by = by;
+    B->zdepth = zdepth;
+    B->grid_blocks = grid_blocks;
+    B->dirty = true;
+    return FDTD_OK;
+  });
+}
+
+int fdtd_batch_set_graph(fdtd_batch* b, int32_t steps_per_graph) {
+  return guarded([&]() -> int {
+    CHECK_BATCH(b);
+    if (steps_per_graph < 0 || steps_per_graph > 100000) return set_error(FDTD_E_INVAL, "steps per graph");
+    B->graph_steps = steps_per_graph;
+    return FDTD_OK;
+  });
+}
+
+int fdtd_batch_step_n(fdtd_batch* b, int64_t n) {
+  return guarded([&]() -> int {
+    CHECK_BATCH(b);
+    if (n < 0) return set_error(FDTD_E_INVAL, "negative step count");
+    if (n == 0) return FDTD_OK;
+    return B->step(n);
+  });
+}
+
+int fdtd_batch_sync(fdtd_batch* b) {
+  return guarded([&]() -> int {
+    CHECK_BATCH(b);
+    cudaError_t e = cudaStreamSynchronize(B->stream);
+    if (e != cudaSuccess) return fdtd::cuda_error(e, "sync");
+    for (GridBase* G : B->grids) {
+      int flags = 0;
+      const int r = G->error_flags(&flags);
+      if (r != FDTD_OK) return r;
+      if (flags & 1) return set_error(FDTD_E_NONFINITE, "a member produced a non-finite value");
+      if (flags & 2) return set_error(FDTD_E_TIMEOUT, "a bounded wait of the step kernel ran out");
+    }
+    return FDTD_OK;
+  });
+}
+
+int fdtd_batch_set_timing(fdtd_batch* b, int32_t on) {
+  return guarded([&]() -> int {
+    CHECK_BATCH(b);
+    cudaError_t e = cudaStreamSynchronize(B->stream);
+    if (e != cudaSuccess) return fdtd::cuda_error(e, "sync");
+    B->timer.collect();
+    B->timer.on = on != 0;
+    B->timer.ms = 0.0;
+    B->timer.launches = 0;
+    return FDTD_OK;
+  });
+}
+
+int fdtd_batch_kernel_time(fdtd_batch* b, double* ms, int64_t* launches) {
+  return guarded([&]() -> int {
+    CHECK_BATCH(b);
+    if (!ms || !launches) return set_error(FDTD_E_INVAL, "null output");
+    cudaError_t e = cudaStreamSynchronize(B->stream);
+    if (e != cudaSuccess) return fdtd::cuda_error(e, "sync");
+    B->timer.collect();
+    *ms = B->timer.ms;
+    *launches = B->timer.launches;
+    return FDTD_OK;
   });
 }
 

@@ -5,6 +5,8 @@
 // host computes the grid's constant tables once (CPML grading profiles,
 // material-class coefficients, the 4x4 Crank-Nicolson matrices of the gain
 // model) and plans the launches.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -128,6 +130,23 @@ static void solve4(const double Lin[4][4], double B[4][5], int ncol) {
   }
 }
 
+// cuTensorMapEncodeTiled from the driver, resolved once through the runtime.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
 // ------------------------------------------------------------------ grid
 template <typename T>
 struct GridImpl final : GridBase {
@@ -148,6 +167,8 @@ struct GridImpl final : GridBase {
   T* d_psi = nullptr;
   size_t psi_words = 0;
   T* d_prof = nullptr;
+  TmaGrid* d_tma = nullptr;
+  bool use_tma = false;
   double n_total = 0.0, neq[4] = {0, 0, 0, 0};
 
   int precision() const override { return sizeof(T) == 4 ? FDTD_FP32 : FDTD_FP64; }
@@ -155,19 +176,25 @@ struct GridImpl final : GridBase {
 
   int init() {
     const long long nc = ncell;
-    d_F = (T*)mem.get(sizeof(T) * 12 * (size_t)nc);
-    uint8_t* mat = (uint8_t*)mem.get((size_t)nc);
+    px = (desc.nx + 15) / 16 * 16;
+    nstore = (long long)px * desc.ny * desc.nz;
+    d_F = (T*)mem.get(sizeof(T) * 12 * (size_t)nstore);
+    uint8_t* mat = (uint8_t*)mem.get((size_t)nstore);
+    d_tma = (TmaGrid*)mem.get(sizeof(TmaGrid));
     d_err = (int*)mem.get(sizeof(int) * 4);
     d_energy = (double*)mem.get(sizeof(double) * 4);
     d_epart = (double*)mem.get(sizeof(double) * kEnergyBlocks);
     d_ecount = (unsigned int*)mem.get(sizeof(unsigned int) * 4);
     d_sg = (StepGrid<T>*)mem.get(sizeof(StepGrid<T>));
     d_og = (ObsGrid<T>*)mem.get(sizeof(ObsGrid<T>));
-    if (!d_F || !mat || !d_err || !d_energy || !d_epart || !d_ecount || !d_sg || !d_og)
+    if (!d_F || !mat || !d_tma || !d_err || !d_energy || !d_epart || !d_ecount || !d_sg || !d_og)
       return set_error(FDTD_E_NOMEM, "device allocation failed (%lld cells)", nc);
     cudaError_t e;
-    if ((e = cudaMemsetAsync(d_F, 0, sizeof(T) * 12 * (size_t)nc, stream)) != cudaSuccess) return cuda_error(e, "memset fields");
-    if ((e = cudaMemsetAsync(mat, 0x15, (size_t)nc, stream)) != cudaSuccess) return cuda_error(e, "memset material");
+    if ((e = cudaMemsetAsync(d_F, 0, sizeof(T) * 12 * (size_t)nstore, stream)) != cudaSuccess) return cuda_error(e, "memset fields");
+    // background class in every E node of the grid; the pitch padding stays 0
+    if ((e = cudaMemsetAsync(mat, 0, (size_t)nstore, stream)) != cudaSuccess) return cuda_error(e, "memset material");
+    if ((e = cudaMemset2DAsync(mat, px, 0x15, desc.nx, (size_t)desc.ny * desc.nz, stream)) != cudaSuccess)
+      return cuda_error(e, "memset material");
     if ((e = cudaMemsetAsync(d_err, 0, sizeof(int) * 4, stream)) != cudaSuccess) return cuda_error(e, "memset err");
     if ((e = cudaMemsetAsync(d_ecount, 0, sizeof(unsigned) * 4, stream)) != cudaSuccess) return cuda_error(e, "memset");
     d_mat = mat;
@@ -175,11 +202,13 @@ struct GridImpl final : GridBase {
     sg.nx = og.nx = desc.nx;
     sg.ny = og.ny = desc.ny;
     sg.nz = og.nz = desc.nz;
+    sg.px = og.px = px;
+    sg.err = d_err;
     sg.per = (desc.periodic[0] ? 1 : 0) | (desc.periodic[1] ? 2 : 0) | (desc.periodic[2] ? 4 : 0);
     for (int q = 0; q < 6; ++q) sg.L[q] = desc.npml[q];
     for (int s = 0; s < 2; ++s)
       for (int c = 0; c < 6; ++c) {
-        sg.F[s][c] = d_F + (size_t)(s * 6 + c) * nc;
+        sg.F[s][c] = d_F + (size_t)(s * 6 + c) * nstore;
         og.F[s][c] = sg.F[s][c];
       }
     sg.mat = mat;
@@ -288,14 +317,14 @@ struct GridImpl final : GridBase {
     // state: P (2 slots x 3), dN (3), compensation (3, binary32 only)
     const size_t nw = (sizeof(T) == 4 ? 12 : 9);
     if (!d_gain) {
-      gain_words = nw * (size_t)ncell;
+      gain_words = nw * (size_t)nstore;
       d_gain = (T*)mem.get(sizeof(T) * gain_words);
       if (!d_gain) return set_error(FDTD_E_NOMEM, "device allocation failed (gain state)");
     }
     for (int s = 0; s < 2; ++s)
-      for (int c = 0; c < 3; ++c) sg.P[s][c] = d_gain + (size_t)(s * 3 + c) * ncell;
-    for (int c = 0; c < 3; ++c) sg.dN[c] = d_gain + (size_t)(6 + c) * ncell;
-    for (int c = 0; c < 3; ++c) sg.cmp[c] = sizeof(T) == 4 ? d_gain + (size_t)(9 + c) * ncell : nullptr;
+      for (int c = 0; c < 3; ++c) sg.P[s][c] = d_gain + (size_t)(s * 3 + c) * nstore;
+    for (int c = 0; c < 3; ++c) sg.dN[c] = d_gain + (size_t)(6 + c) * nstore;
+    for (int c = 0; c < 3; ++c) sg.cmp[c] = sizeof(T) == 4 ? d_gain + (size_t)(9 + c) * nstore : nullptr;
     sg.gain = 1;
     T d1 = 0, d2 = 0, d3 = 0;
     if (p.init == FDTD_INIT_GROUND) {
@@ -303,7 +332,7 @@ struct GridImpl final : GridBase {
       d2 = (T)(-neq[2] / p.n_total);
       d3 = (T)(-neq[3] / p.n_total);
     }
-    cudaError_t e = launch_gain_init<T>(&sg, ncell, d1, d2, d3, stream);
+    cudaError_t e = launch_gain_init<T>(&sg, nstore, d1, d2, d3, stream);
     if (e != cudaSuccess) return cuda_error(e, "gain init");
     return FDTD_OK;
   }
@@ -363,17 +392,41 @@ struct GridImpl final : GridBase {
     return FDTD_OK;
   }
 
-  // Work items of one time step for a tile of (bx-1) x (by-1) owned columns
-  // and z-ranges of `zdepth` planes.
+  // Work items of one time step.  TMA kernel: tiles of 32 x by owned columns;
+  // plain kernel: tiles of (bx-1) x (by-1) owned columns.  Each tile marches
+  // z-ranges of `zdepth` planes (0: chosen so the items fill whole waves).
   void plan_items() {
     items.clear();
-    const int ox = bx - 1, oy = by - 1;
+    const bool periodic = desc.periodic[0] || desc.periodic[1] || desc.periodic[2];
+    use_tma = (kernel_kind == 2 || (kernel_kind == 0 && !periodic)) && !periodic && kTmaOX * by <= 256 &&
+              tensor_map_encoder() != nullptr;
+    const int ox = use_tma ? kTmaOX : bx - 1;
+    const int oy = use_tma ? by : by - 1;
     const int tnx = (desc.nx + ox - 1) / ox, tny = (desc.ny + oy - 1) / oy;
+    const int tiles = tnx * tny;
     int depth = zdepth;
     if (depth <= 0) {
-      const int target = 4 * 152;
-      const int chunks = std::max(1, (target + tnx * tny - 1) / (tnx * tny));
-      depth = std::max(8, (desc.nz + chunks - 1) / chunks);
+      // z-ranges chosen so that the items fill whole waves of resident blocks
+      int dev = 0, sms = 152;
+      if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaGetLastError();
+      const int wave = sms * step_blocks_per_sm<T>(use_tma, sg.gain != 0, bx, by);
+      double best = -1.0;
+      int best_chunks = 1;
+      for (int chunks = 1; chunks <= 64; ++chunks) {
+        const int d = (desc.nz + chunks - 1) / chunks;
+        if (d < 8 && chunks > 1) break;
+        const int real_chunks = (desc.nz + d - 1) / d;
+        const double waves = (double)tiles * real_chunks / wave;
+        const double eff = waves / std::ceil(waves);
+        // prefer full waves, then fewer (longer) z-ranges
+        if (eff > best + 1e-9) {
+          best = eff;
+          best_chunks = chunks;
+        }
+        if (waves > 4.0) break;
+      }
+      depth = (desc.nz + best_chunks - 1) / best_chunks;
     }
     depth = std::min(depth, desc.nz);
     for (int z0 = 0; z0 < desc.nz; z0 += depth) {
@@ -385,6 +438,34 @@ struct GridImpl final : GridBase {
     if (og.nprobe) oitems.push_back(make_int4(0, -1, 0, 1));
     for (int f = 0; f < og.nflux; ++f)
       for (int p = 0; p < og.flux_parts[f]; ++p) oitems.push_back(make_int4(0, f, p, og.flux_parts[f]));
+  }
+
+  // TMA descriptors of the fields (4D: x, y, z, array) and the material (3D).
+  int encode_tma() {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return set_error(FDTD_E_CUDA, "cuTensorMapEncodeTiled unavailable");
+    TmaGrid h;
+    std::memset(&h, 0, sizeof(h));
+    const int AX = 16 / (int)sizeof(T);
+    const cuuint64_t fdim[4] = {(cuuint64_t)desc.nx, (cuuint64_t)desc.ny, (cuuint64_t)desc.nz, 12};
+    const cuuint64_t fstr[3] = {(cuuint64_t)px * sizeof(T), (cuuint64_t)px * desc.ny * sizeof(T),
+                                (cuuint64_t)nstore * sizeof(T)};
+    const cuuint32_t fbox[4] = {(cuuint32_t)(kTmaOX + 2 * AX), (cuuint32_t)(by + 2), 1, 6};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    CUresult r = enc(&h.fields, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                     (void*)d_F, fdim, fstr, fbox, one, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(FDTD_E_CUDA, "tensor map (fields) encode failed: %d", (int)r);
+    const cuuint64_t mdim[3] = {(cuuint64_t)desc.nx, (cuuint64_t)desc.ny, (cuuint64_t)desc.nz};
+    const cuuint64_t mstr[2] = {(cuuint64_t)px, (cuuint64_t)px * desc.ny};
+    const cuuint32_t mbox[3] = {(cuuint32_t)kTmaOX, (cuuint32_t)by, 1};
+    r = enc(&h.mat, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, (void*)d_mat, mdim, mstr, mbox, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(FDTD_E_CUDA, "tensor map (material) encode failed: %d", (int)r);
+    cudaError_t e = cudaMemcpyAsync(d_tma, &h, sizeof(h), cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_error(e, "upload tensor maps");
+    return FDTD_OK;
   }
 
   int finalize() override {
@@ -413,6 +494,10 @@ struct GridImpl final : GridBase {
   int replan() override {
     cudaError_t e;
     plan_items();
+    if (use_tma) {
+      const int r = encode_tma();
+      if (r != FDTD_OK) return r;
+    }
     if (items.size() > items_cap) {
       d_items = (int4*)mem.get(sizeof(int4) * items.size());
       items_cap = items.size();
@@ -435,6 +520,8 @@ struct GridImpl final : GridBase {
   int upload_tables() {
     cudaError_t e;
     sg.step = og.step = steps;
+    sg.step_end = og.step_end = step_limit;
+    tables_dirty = false;
     if ((e = cudaMemcpyAsync(d_sg, &sg, sizeof(sg), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return cuda_error(e, "upload grid");
     if ((e = cudaMemcpyAsync(d_og, &og, sizeof(og), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return cuda_error(e, "upload grid");
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "upload grid");
@@ -443,14 +530,22 @@ struct GridImpl final : GridBase {
 
   int step(long long n) override {
     cudaError_t e;
+    if (tables_dirty) {
+      const int r = upload_tables();
+      if (r != FDTD_OK) return r;
+    }
+    n = std::min(n, std::max(0LL, step_limit - steps));
     long long done = 0;
     while (done < n) {
       const int chunk = (int)std::min<long long>(n - done, 1 << 20);
       for (int s = 0; s < chunk; ++s) {
         const auto ev = timer.next();
         if (ev.first) cudaEventRecord(ev.first, stream);
-        if ((e = launch_step<T>(d_sg, d_items, (int)items.size(), s, bx, by, sg.gain != 0, grid_blocks, stream)) != cudaSuccess)
-          return cuda_error(e, "step kernel");
+        if (use_tma)
+          e = launch_step_tma<T>(d_sg, d_tma, d_items, (int)items.size(), s, by, sg.gain != 0, grid_blocks, stream);
+        else
+          e = launch_step<T>(d_sg, d_items, (int)items.size(), s, bx, by, sg.gain != 0, grid_blocks, stream);
+        if (e != cudaSuccess) return cuda_error(e, "step kernel");
         if (ev.second) cudaEventRecord(ev.second, stream);
         if (timer.used >= 4096) {
           if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "sync");
@@ -469,15 +564,18 @@ struct GridImpl final : GridBase {
 
   int read_field(int comp, double* out) override {
     const int sel = (int)(steps & 1);
-    return copy_out(sg.F[sel][comp], ncell, out);
+    return copy_out(sg.F[sel][comp], out);
   }
 
-  int copy_out(const T* src, long long count, double* out) {
+  // device array in the pitched layout -> double[nz][ny][nx] on the host
+  int copy_out(const T* src, double* out) {
     cudaError_t e;
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "sync");
-    std::vector<T> h((size_t)count);
-    if ((e = cudaMemcpy(h.data(), src, sizeof(T) * count, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_error(e, "read");
-    for (long long q = 0; q < count; ++q) out[q] = (double)h[q];
+    std::vector<T> h((size_t)ncell);
+    if ((e = cudaMemcpy2D(h.data(), sizeof(T) * desc.nx, src, sizeof(T) * px, sizeof(T) * desc.nx,
+                          (size_t)desc.ny * desc.nz, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_error(e, "read");
+    for (long long q = 0; q < ncell; ++q) out[q] = (double)h[q];
     return FDTD_OK;
   }
 
@@ -485,7 +583,9 @@ struct GridImpl final : GridBase {
     std::vector<T> h((size_t)ncell);
     for (long long q = 0; q < ncell; ++q) h[q] = (T)in[q];
     cudaError_t e;
-    if ((e = cudaMemcpy(sg.F[0][comp], h.data(), sizeof(T) * ncell, cudaMemcpyHostToDevice)) != cudaSuccess) return cuda_error(e, "write");
+    if ((e = cudaMemcpy2D(sg.F[0][comp], sizeof(T) * px, h.data(), sizeof(T) * desc.nx, sizeof(T) * desc.nx,
+                          (size_t)desc.ny * desc.nz, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_error(e, "write");
     return FDTD_OK;
   }
 
@@ -495,13 +595,13 @@ struct GridImpl final : GridBase {
     if (what == 0 || what == 1) {
       const int slot = (int)((steps + (what == 1 ? 1 : 0)) & 1);
       for (int c = 0; c < 3; ++c)
-        if ((r = copy_out(sg.P[slot][c], ncell, out + (size_t)c * ncell)) != FDTD_OK) return r;
+        if ((r = copy_out(sg.P[slot][c], out + (size_t)c * ncell)) != FDTD_OK) return r;
       return FDTD_OK;
     }
     std::vector<uint8_t> m((size_t)ncell);
     if ((r = get_material(m.data())) != FDTD_OK) return r;
     for (int c = 0; c < 3; ++c) {
-      if ((r = copy_out(sg.dN[c], ncell, out + (size_t)c * ncell)) != FDTD_OK) return r;
+      if ((r = copy_out(sg.dN[c], out + (size_t)c * ncell)) != FDTD_OK) return r;
       for (long long q = 0; q < ncell; ++q) {
         double& v = out[(size_t)c * ncell + q];
         if (!((m[q] >> 6) & 1)) v = 0.0;
@@ -543,7 +643,7 @@ struct GridImpl final : GridBase {
     const int sel = (int)(steps & 1);
     const T* F6[6];
     for (int c = 0; c < 6; ++c) F6[c] = sg.F[sel][c];
-    cudaError_t e = launch_energy<T>(F6, d_mat, desc.eps[0], desc.eps[1], desc.eps[2], ncell, d_epart, d_ecount,
+    cudaError_t e = launch_energy<T>(F6, d_mat, desc.eps[0], desc.eps[1], desc.eps[2], nstore, d_epart, d_ecount,
                                      d_energy, d_err, stream);
     if (e != cudaSuccess) return cuda_error(e, "energy kernel");
     double v = 0;
@@ -563,8 +663,8 @@ struct GridImpl final : GridBase {
   // state blobs for checkpointing: (device pointer, bytes)
   void state_blobs(std::vector<std::pair<void*, size_t>>& v) override {
     v.clear();
-    v.push_back({d_F, sizeof(T) * 12 * (size_t)ncell});
-    v.push_back({(void*)d_mat, (size_t)ncell});
+    v.push_back({d_F, sizeof(T) * 12 * (size_t)nstore});
+    v.push_back({(void*)d_mat, (size_t)nstore});
     if (d_psi) v.push_back({d_psi, sizeof(T) * psi_words});
     if (d_gain) v.push_back({d_gain, sizeof(T) * gain_words});
     if (og.probe_ring) v.push_back({og.probe_ring, sizeof(T) * (size_t)og.cap * og.nprobe * 3});
@@ -582,6 +682,12 @@ struct GridImpl final : GridBase {
   size_t step_record_size() const override { return sizeof(sg); }
   size_t obs_record_size() const override { return sizeof(og); }
   int has_gain() const override { return sg.gain; }
+  const void* tma_device() const override { return d_tma; }
+  bool uses_tma() const override { return use_tma; }
+  void work_items(std::vector<int4>& si, std::vector<int4>& oi) const override {
+    si = items;
+    oi = oitems;
+  }
 };
 
 GridBase* make_grid(const fdtd_grid_desc& d) {

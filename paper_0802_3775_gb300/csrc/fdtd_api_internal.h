@@ -71,7 +71,10 @@ struct GridBase {
   fdtd_grid_desc desc{};
   cudaStream_t stream = nullptr;
   DeviceMemory mem;
-  long long ncell = 0;
+  long long ncell = 0;   // nx * ny * nz
+  int px = 0;            // x pitch of the device arrays (nx rounded up to 16)
+  long long nstore = 0;  // px * ny * nz
+  int kernel_kind = 0;   // 0 auto (TMA when no axis is periodic), 1 plain loads, 2 TMA
   long long steps = 0;
   double S = 0, dx = 0, dt = 0;
   bool material_set = false;
@@ -79,6 +82,8 @@ struct GridBase {
   int bx = 32, by = 8, zdepth = 0, grid_blocks = 0;
   uint8_t* d_mat = nullptr;
   LaunchTimer timer;
+  long long step_limit = 0x7fffffffffffffffLL;  // no update n >= step_limit
+  bool tables_dirty = false;                     // device records stale (stepped by a batch)
 
   virtual ~GridBase() { mem.release_all(); }
   virtual int precision() const = 0;
@@ -107,11 +112,23 @@ struct GridBase {
   virtual size_t step_record_size() const = 0;
   virtual size_t obs_record_size() const = 0;
   virtual int has_gain() const = 0;
+  // batch support: device TMA descriptors, kernel path, work items (grid index 0)
+  virtual const void* tma_device() const = 0;
+  virtual bool uses_tma() const = 0;
+  virtual void work_items(std::vector<int4>& step_items, std::vector<int4>& obs_items) const = 0;
 
   int get_material(uint8_t* out) {
     cudaError_t e;
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "sync");
-    if ((e = cudaMemcpy(out, d_mat, (size_t)ncell, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_error(e, "read material");
+    if ((e = cudaMemcpy2D(out, desc.nx, d_mat, px, desc.nx, (size_t)desc.ny * desc.nz, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_error(e, "read material");
+    return FDTD_OK;
+  }
+  int set_material(const uint8_t* in) {
+    cudaError_t e = cudaMemcpy2DAsync(d_mat, px, in, desc.nx, desc.nx, (size_t)desc.ny * desc.nz,
+                                      cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_error(e, "set material");
     return FDTD_OK;
   }
 };

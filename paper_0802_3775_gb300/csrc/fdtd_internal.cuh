@@ -4,6 +4,7 @@
 // translation units.  Nothing here is part of the C ABI (include/fdtd.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -14,6 +15,8 @@ constexpr int kMaxProbes = 64;
 constexpr int kMaxFlux = 16;
 constexpr int kMaxFluxParts = 64;
 constexpr int kEnergyBlocks = 256;
+constexpr int kTmaStages = 4;     // planes resident or in flight per block (TMA step kernel)
+constexpr int kTmaOX = 32;        // owned tile width of the TMA step kernel
 
 // Physical constants (CODATA; mu0 of the 2019 SI, hbar exact).
 constexpr double kC0 = 299792458.0;
@@ -43,6 +46,7 @@ struct SrcDev {
 template <typename T>
 struct StepGrid {
   int nx, ny, nz;
+  int px;               // x pitch of field, material and gain arrays (elements)
   int per;              // bit d set: axis d periodic
   int L[6];             // slab thickness x-,x+,y-,y+,z-,z+
   int Sd[3];            // slab extent per axis (L[2d] + L[2d+1])
@@ -64,6 +68,7 @@ struct StepGrid {
   T a1, a2, a3, n12eq, q, noise;
   T D[3][3], w[3];
   unsigned long long seed;
+  int* err;             // bit 1: a bounded wait of the step kernel ran out
   SrcDev src[kMaxSrc];
 };
 
@@ -71,6 +76,7 @@ struct StepGrid {
 template <typename T>
 struct ObsGrid {
   int nx, ny, nz;
+  int px;               // x pitch
   int nprobe, nflux;
   long long step;       // as StepGrid::step
   long long step_end;
@@ -89,6 +95,14 @@ struct ObsGrid {
   int* err;             // bit 0: non-finite value seen
 };
 
+// TMA descriptors of one grid: all twelve field arrays as one 4D tensor
+// (x, y, z, array) with a box of (32 + 2 pad) x (tile rows + 2) x 1 x 6,
+// and the material bytes as a 3D tensor with a box of 32 x rows x 1.
+struct alignas(128) TmaGrid {
+  CUtensorMap fields;
+  CUtensorMap mat;
+};
+
 // Work items of the step kernel: (grid, x0, y0, z0 | z1 << 16).
 // Work items of the observation kernel: (grid, what, part, nparts) with
 // what = -1 for the probes and f >= 0 for flux plane f.
@@ -96,6 +110,17 @@ struct ObsGrid {
 template <typename T>
 cudaError_t launch_step(const StepGrid<T>* grids, const int4* items, int nitems, int offset, int bx, int by,
                         bool gain, int grid_blocks, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_step_tma(const StepGrid<T>* grids, const TmaGrid* maps, const int4* items, int nitems, int offset,
+                            int oy, bool gain, int grid_blocks, cudaStream_t st);
+
+template <typename T>
+size_t step_tma_smem_bytes(int oy);
+
+// Resident blocks per SM of the step kernel for a launch shape.
+template <typename T>
+int step_blocks_per_sm(bool tma, bool gain, int bx, int by);
 
 template <typename T>
 cudaError_t launch_observe(const ObsGrid<T>* grids, const int4* items, int nitems, int offset, cudaStream_t st);
@@ -109,13 +134,13 @@ template <typename T>
 cudaError_t launch_advance(StepGrid<T>* sg, ObsGrid<T>* og, int ngrids, int count, cudaStream_t st);
 
 // Rasterization of binned spheres (see fdtd_set_eps_from_spheres).
-cudaError_t launch_rasterize(uint8_t* mat, int nx, int ny, int nz, const double* spheres, const int* bin_start,
+cudaError_t launch_rasterize(uint8_t* mat, int nx, int ny, int nz, int px, const double* spheres, const int* bin_start,
                              const int* bin_list, int bin, int bnx, int bny, int bnz, const double* box,
                              cudaStream_t st);
 
 // Gain initialization: P slots zero, dN~ = init - N~eq in gain cells.
 template <typename T>
-cudaError_t launch_gain_init(const StepGrid<T>* g_host_copy, long long ncell, T d1, T d2, T d3, cudaStream_t st);
+cudaError_t launch_gain_init(const StepGrid<T>* g_host_copy, long long nstore, T d1, T d2, T d3, cudaStream_t st);
 
 // Field energy sum (eps_r E^2 + H~^2) over the cells in FP64; result in out[0].
 template <typename T>

@@ -1,14 +1,18 @@
 // Device kernels of the GB300 Maxwell-Bloch FDTD library (sm_103a).
 //
-// k_step      one time step n -> n+1 of a set of work items (x-y tile x
-//             z-range of some grid): H half step with CPML, polarization,
-//             E step with CPML, source and gain current, populations, noise.
-//             The tile marches in z with the E planes of the tile (plus a
-//             one-node halo) staged in shared memory; H on the -x / -y halo is
-//             recomputed so that no block needs a neighbour's output of the
-//             same step.  Fields and H-side CPML memory are double-buffered
-//             (read set n&1, write set (n+1)&1); E-side CPML memory and the
-//             gain state are updated in place by the owning thread.
+// k_step_tma  one time step n -> n+1 of a list of work items (32-column x
+//             OY-row tile x z-range of some grid), non-periodic grids.  The
+//             tile marches in z; each plane of all six fields (tile plus a
+//             one-node halo, x padded to 16-byte alignment) and the tile's
+//             material bytes arrive in shared memory by two TMA bulk-tensor
+//             copies into a 4-stage mbarrier pipeline, so three planes are in
+//             flight while one is computed.  H on the -x / -y halo is
+//             recomputed so no block needs a neighbour's output of the same
+//             step; fields and H-side CPML memory are double-buffered (read
+//             set n&1, write set (n+1)&1); E-side CPML memory and gain state
+//             are updated in place by the owning thread.
+// k_step      the same step with plain loads and register prefetch of the
+//             next plane; any boundary, including periodic axes.
 // k_observe   probes (E^{n+1}) and Poynting flux T^n per plane with a
 //             fixed-order FP64 reduction (bitwise reproducible).
 // k_energy    field energy in FP64, fixed-order reduction.
@@ -20,76 +24,10 @@
 // "Wide-band excitation", "Dynamical diffusion").
 #include <math.h>
 
+#include "cell.cuh"
 #include "fdtd_internal.cuh"
 
 namespace fdtd {
-
-__device__ __forceinline__ long long lidx(int i, int j, int k, int nx, int ny) {
-  return ((long long)k * ny + j) * nx + i;
-}
-
-// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
-// multiplications with a Weyl key schedule.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r) {
-      k.x += 0x9E3779B9u;
-      k.y += 0xBB67AE85u;
-    }
-    const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-  }
-  return c;
-}
-
-// Three N(0,1) deviates for (seed, cell, step): Box-Muller on the uniforms
-// u = ((x >> 9) + 0.5) 2^-23 (exact in binary32).
-__device__ __forceinline__ void gain_normals(unsigned long long seed, long long cell, long long step, float& a,
-                                             float& b, float& c) {
-  const uint4 x = philox4x32_10(
-      make_uint4((unsigned)cell, (unsigned)((unsigned long long)cell >> 32), (unsigned)step,
-                 (unsigned)((unsigned long long)step >> 32)),
-      make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
-  const float u0 = ((float)(x.x >> 9) + 0.5f) * 0x1p-23f;
-  const float u1 = ((float)(x.y >> 9) + 0.5f) * 0x1p-23f;
-  const float u2 = ((float)(x.z >> 9) + 0.5f) * 0x1p-23f;
-  const float u3 = ((float)(x.w >> 9) + 0.5f) * 0x1p-23f;
-  const float rho = sqrtf(-2.0f * logf(u0));
-  float s, co;
-  sincospif(2.0f * u1, &s, &co);
-  a = rho * co;
-  b = rho * s;
-  c = sqrtf(-2.0f * logf(u2)) * cospif(2.0f * u3);
-}
-
-__device__ __forceinline__ void gain_normals(unsigned long long seed, long long cell, long long step, double& a,
-                                             double& b, double& c) {
-  const uint4 x = philox4x32_10(
-      make_uint4((unsigned)cell, (unsigned)((unsigned long long)cell >> 32), (unsigned)step,
-                 (unsigned)((unsigned long long)step >> 32)),
-      make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
-  const double u0 = ((double)(x.x >> 9) + 0.5) * 0x1p-23;
-  const double u1 = ((double)(x.y >> 9) + 0.5) * 0x1p-23;
-  const double u2 = ((double)(x.z >> 9) + 0.5) * 0x1p-23;
-  const double u3 = ((double)(x.w >> 9) + 0.5) * 0x1p-23;
-  const double rho = sqrt(-2.0 * log(u0));
-  double s, co;
-  sincospi(2.0 * u1, &s, &co);
-  a = rho * co;
-  b = rho * s;
-  c = sqrt(-2.0 * log(u2)) * cospi(2.0 * u3);
-}
-
-// CPML-modified difference: D / kappa + psi with psi <- b psi + c D.
-template <typename T>
-__device__ __forceinline__ T pml_term(T D, const T* const* pr, int pos, const T* psi_in, T* psi_out,
-                                      long long pidx) {
-  const T p = pr[1][pos] * psi_in[pidx] + pr[2][pos] * D;
-  if (psi_out) psi_out[pidx] = p;
-  return pr[0][pos] * D + p;
-}
 
 // Index along an axis of length n: wrapped when periodic, otherwise flagged
 // invalid (v = false, reads as zero) outside [0, n).
@@ -112,9 +50,22 @@ __device__ __forceinline__ T ldz(const T* __restrict__ a, bool v, long long idx)
   return v ? __ldg(a + idx) : T(0);
 }
 
+__host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
+
+// Copy a grid record into shared memory (all threads of the block).
+template <typename T>
+__device__ __forceinline__ void load_record(const StepGrid<T>* g, unsigned char* dst_raw, int tid, int nthreads) {
+  const int* src = reinterpret_cast<const int*>(g);
+  int* dst = reinterpret_cast<int*>(dst_raw);
+  for (int w = tid; w < (int)(sizeof(StepGrid<T>) / 4); w += nthreads) dst[w] = src[w];
+}
+
+// =====================================================================
+// Plain-load step kernel (any boundary)
+// =====================================================================
 template <typename T>
 size_t step_smem_bytes(int bx, int by) {
-  const size_t gs = (sizeof(StepGrid<T>) + 15) & ~size_t(15);
+  const size_t gs = align128(sizeof(StepGrid<T>));
   const size_t planes = (size_t)3 * (bx + 1) * (by + 1) + (size_t)3 * bx * by;
   return gs + kMaxSrc * sizeof(double) + planes * sizeof(T);
 }
@@ -122,9 +73,9 @@ size_t step_smem_bytes(int bx, int by) {
 template <typename T, bool GAIN>
 __global__ void __launch_bounds__(512) k_step(const StepGrid<T>* __restrict__ grids, const int4* __restrict__ items,
                                               int nitems, int offset) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   StepGrid<T>& G = *reinterpret_cast<StepGrid<T>*>(smem);
-  constexpr size_t GS = (sizeof(StepGrid<T>) + 15) & ~size_t(15);
+  constexpr size_t GS = align128(sizeof(StepGrid<T>));
   double* sg = reinterpret_cast<double*>(smem + GS);
   T* sbase = reinterpret_cast<T*>(smem + GS + kMaxSrc * sizeof(double));
   const int bx = blockDim.x, by = blockDim.y;
@@ -146,34 +97,28 @@ __global__ void __launch_bounds__(512) k_step(const StepGrid<T>* __restrict__ gr
     const int4 item = items[it];
     __syncthreads();
     if (item.x != cur) {
-      const int* src = reinterpret_cast<const int*>(grids + item.x);
-      int* dst = reinterpret_cast<int*>(smem);
-      for (int w = tid; w < (int)(sizeof(StepGrid<T>) / 4); w += bx * by) dst[w] = src[w];
+      load_record(grids + item.x, smem, tid, bx * by);
       cur = item.x;
     }
     __syncthreads();
     const long long n = G.step + offset;
     if (n >= G.step_end) continue;
-    if (tid < G.nsrc) {
-      const SrcDev& s = G.src[tid];
-      const double t = (double)n + 0.5 - s.t0;
-      sg[tid] = exp(-t * t / (2.0 * s.tau * s.tau)) * sin(2.0 * 3.14159265358979323846 * s.f0dt * t);
-    }
+    source_waveforms(G, n, tid, sg);
     __syncthreads();
 
-    const int nx = G.nx, ny = G.ny, nz = G.nz;
-    const bool px = G.per & 1, py = G.per & 2, pz = G.per & 4;
+    const int nx = G.nx, ny = G.ny, nz = G.nz, px = G.px;
+    const bool perx = G.per & 1, pery = G.per & 2, perz = G.per & 4;
     const int x0 = item.y, y0 = item.z, z0 = item.w & 0xffff, z1 = (item.w >> 16) & 0xffff;
     const int i = x0 - 1 + tx, j = y0 - 1 + ty;
     bool vx, vy, vxp, vyp;
-    const int iw = wrap_index(i, nx, px, vx);
-    const int jw = wrap_index(j, ny, py, vy);
+    const int iw = wrap_index(i, nx, perx, vx);
+    const int jw = wrap_index(j, ny, pery, vy);
     const bool valid = vx && vy;
     const bool xcol = (tx == bx - 1), yrow = (ty == by - 1);
-    const int ip = wrap_index(i + 1, nx, px, vxp);
-    const int jp = wrap_index(j + 1, ny, py, vyp);
-    const bool vcol = xcol && vxp && vy;   // extra column node (i+1, j) exists
-    const bool vrow = yrow && vx && vyp;   // extra row node (i, j+1) exists
+    const int ip = wrap_index(i + 1, nx, perx, vxp);
+    const int jp = wrap_index(j + 1, ny, pery, vyp);
+    const bool vcol = xcol && vxp && vy;  // extra column node (i+1, j) exists
+    const bool vrow = yrow && vx && vyp;  // extra row node (i, j+1) exists
     const bool owner = tx > 0 && ty > 0 && i < nx && j < ny;
 
     const int sel = (int)(n & 1);
@@ -184,32 +129,21 @@ __global__ void __launch_bounds__(512) k_step(const StepGrid<T>* __restrict__ gr
     const T* __restrict__ Hy = G.F[sel][4];
     const T* __restrict__ Hz = G.F[sel][5];
 
-    // CPML slab coordinates of this column
-    int sx = -1, sy = -1;
-    if (valid && G.Sd[0]) {
-      if (iw < G.L[0]) sx = iw;
-      else if (iw >= nx - G.L[1]) sx = G.L[0] + iw - (nx - G.L[1]);
-    }
-    if (valid && G.Sd[1]) {
-      if (jw < G.L[2]) sy = jw;
-      else if (jw >= ny - G.L[3]) sy = G.L[2] + jw - (ny - G.L[3]);
-    }
+    auto kwrap = [&](int k, bool& v) { return wrap_index(k, nz, perz, v); };
 
-    auto kwrap = [&](int k, bool& v) { return wrap_index(k, nz, pz, v); };
-
-    const int kstart = (z0 > 0 || pz) ? z0 - 1 : z0;
+    const int kstart = (z0 > 0 || perz) ? z0 - 1 : z0;
     bool vk0, vk1;
     const int kw0 = kwrap(kstart, vk0);
     const int kw1 = kwrap(kstart + 1, vk1);
-    const long long c0 = lidx(iw, jw, kw0, nx, ny);
-    const long long c1 = lidx(iw, jw, kw1, nx, ny);
+    const long long c0 = pidx3(iw, jw, kw0, px, ny);
+    const long long c1 = pidx3(iw, jw, kw1, px, ny);
     T eCx = ldz(Ex, valid && vk0, c0), eCy = ldz(Ey, valid && vk0, c0), eCz = ldz(Ez, valid && vk0, c0);
     T eNx = ldz(Ex, valid && vk1, c1), eNy = ldz(Ey, valid && vk1, c1), eNz = ldz(Ez, valid && vk1, c1);
     T hOx = ldz(Hx, valid && vk0, c0), hOy = ldz(Hy, valid && vk0, c0), hOz = ldz(Hz, valid && vk0, c0);
-    T xCy = T(0), xCz = T(0), yCx = T(0), yCz = T(0);
+    T xCy, xCz, yCx, yCz;
     {
-      const long long cc = lidx(ip, jw, kw0, nx, ny);
-      const long long cr = lidx(iw, jp, kw0, nx, ny);
+      const long long cc = pidx3(ip, jw, kw0, px, ny);
+      const long long cr = pidx3(iw, jp, kw0, px, ny);
       xCy = ldz(Ey, vcol && vk0, cc);
       xCz = ldz(Ez, vcol && vk0, cc);
       yCx = ldz(Ex, vrow && vk0, cr);
@@ -228,23 +162,22 @@ __global__ void __launch_bounds__(512) k_step(const StepGrid<T>* __restrict__ gr
         bool va, vb;
         const int ka = kwrap(k + 1, va);
         const int kb = kwrap(k + 2, vb);
-        const long long ca = lidx(iw, jw, ka, nx, ny);
-        const long long cb = lidx(iw, jw, kb, nx, ny);
+        const long long ca = pidx3(iw, jw, ka, px, ny);
+        const long long cb = pidx3(iw, jw, kb, px, ny);
         eNNx = ldz(Ex, valid && vb, cb);
         eNNy = ldz(Ey, valid && vb, cb);
         eNNz = ldz(Ez, valid && vb, cb);
         hONx = ldz(Hx, valid && va, ca);
         hONy = ldz(Hy, valid && va, ca);
         hONz = ldz(Hz, valid && va, ca);
-        const long long cc = lidx(ip, jw, ka, nx, ny);
-        const long long cr = lidx(iw, jp, ka, nx, ny);
+        const long long cc = pidx3(ip, jw, ka, px, ny);
+        const long long cr = pidx3(iw, jp, ka, px, ny);
         xNy = ldz(Ey, vcol && va, cc);
         xNz = ldz(Ez, vcol && va, cc);
         yNx = ldz(Ex, vrow && va, cr);
         yNz = ldz(Ez, vrow && va, cr);
       }
-      // owner loads for the E update of this plane
-      const long long cidx = lidx(iw, jw, kw, nx, ny);
+      const long long cidx = pidx3(iw, jw, kw, px, ny);
       unsigned m = 0;
       if (owner && active) m = __ldg(G.mat + cidx);
 
@@ -262,39 +195,10 @@ __global__ void __launch_bounds__(512) k_step(const StepGrid<T>* __restrict__ gr
       }
       __syncthreads();
 
-      // H^{n+1/2} at this node
       T hx = T(0), hy = T(0), hz = T(0);
       if (valid && vk) {
-        T dyEz = sEz[se + EW] - eCz;
-        T dzEy = eNy - eCy;
-        T dzEx = eNx - eCx;
-        T dxEz = sEz[se + 1] - eCz;
-        T dxEy = sEy[se + 1] - eCy;
-        T dyEx = sEx[se + EW] - eCx;
-        const bool wr = owner && active;
-        if (sx >= 0) {
-          const long long pi = ((long long)kw * ny + jw) * G.Sd[0] + sx;
-          dxEz = pml_term(dxEz, G.prof[0][1], iw, G.psiH[sel][0][0], wr ? G.psiH[sel ^ 1][0][0] : (T*)nullptr, pi);
-          dxEy = pml_term(dxEy, G.prof[0][1], iw, G.psiH[sel][0][1], wr ? G.psiH[sel ^ 1][0][1] : (T*)nullptr, pi);
-        }
-        if (sy >= 0) {
-          const long long pi = ((long long)kw * G.Sd[1] + sy) * nx + iw;
-          dyEx = pml_term(dyEx, G.prof[1][1], jw, G.psiH[sel][1][0], wr ? G.psiH[sel ^ 1][1][0] : (T*)nullptr, pi);
-          dyEz = pml_term(dyEz, G.prof[1][1], jw, G.psiH[sel][1][1], wr ? G.psiH[sel ^ 1][1][1] : (T*)nullptr, pi);
-        }
-        if (G.Sd[2]) {
-          int sz = -1;
-          if (kw < G.L[4]) sz = kw;
-          else if (kw >= nz - G.L[5]) sz = G.L[4] + kw - (nz - G.L[5]);
-          if (sz >= 0) {
-            const long long pi = ((long long)sz * ny + jw) * nx + iw;
-            dzEy = pml_term(dzEy, G.prof[2][1], kw, G.psiH[sel][2][0], wr ? G.psiH[sel ^ 1][2][0] : (T*)nullptr, pi);
-            dzEx = pml_term(dzEx, G.prof[2][1], kw, G.psiH[sel][2][1], wr ? G.psiH[sel ^ 1][2][1] : (T*)nullptr, pi);
-          }
-        }
-        hx = hOx - G.cH * (dyEz - dzEy);
-        hy = hOy - G.cH * (dzEx - dxEz);
-        hz = hOz - G.cH * (dxEy - dyEx);
+        h_node(G, sel, owner && active, iw, jw, kw, sEz[se + EW] - eCz, eNy - eCy, eNx - eCx, sEz[se + 1] - eCz,
+               sEy[se + 1] - eCy, sEx[se + EW] - eCx, hOx, hOy, hOz, hx, hy, hz);
       }
       sHx[tid] = hx;
       sHy[tid] = hy;
@@ -302,134 +206,12 @@ __global__ void __launch_bounds__(512) k_step(const StepGrid<T>* __restrict__ gr
       __syncthreads();
 
       if (owner && active) {
-        T dyHz = hz - sHz[tid - bx];
-        T dzHy = hy - hPy;
-        T dzHx = hx - hPx;
-        T dxHz = hz - sHz[tid - 1];
-        T dxHy = hy - sHy[tid - 1];
-        T dyHx = hx - sHx[tid - bx];
-        if (sx >= 0) {
-          const long long pi = ((long long)kw * ny + jw) * G.Sd[0] + sx;
-          dxHz = pml_term(dxHz, G.prof[0][0], iw, G.psiE[0][0], G.psiE[0][0], pi);
-          dxHy = pml_term(dxHy, G.prof[0][0], iw, G.psiE[0][1], G.psiE[0][1], pi);
-        }
-        if (sy >= 0) {
-          const long long pi = ((long long)kw * G.Sd[1] + sy) * nx + iw;
-          dyHx = pml_term(dyHx, G.prof[1][0], jw, G.psiE[1][0], G.psiE[1][0], pi);
-          dyHz = pml_term(dyHz, G.prof[1][0], jw, G.psiE[1][1], G.psiE[1][1], pi);
-        }
-        if (G.Sd[2]) {
-          int sz = -1;
-          if (kw < G.L[4]) sz = kw;
-          else if (kw >= nz - G.L[5]) sz = G.L[4] + kw - (nz - G.L[5]);
-          if (sz >= 0) {
-            const long long pi = ((long long)sz * ny + jw) * nx + iw;
-            dzHy = pml_term(dzHy, G.prof[2][0], kw, G.psiE[2][0], G.psiE[2][0], pi);
-            dzHx = pml_term(dzHx, G.prof[2][0], kw, G.psiE[2][1], G.psiE[2][1], pi);
-          }
-        }
-        const T curlx = dyHz - dzHy;
-        const T curly = dzHx - dxHz;
-        const T curlz = dxHy - dyHx;
-        const int clx = m & 3, cly = (m >> 2) & 3, clz = (m >> 4) & 3;
-
-        // soft sources
-        T sx_ = T(0), sy_ = T(0), sz_ = T(0);
-        for (int s = 0; s < G.nsrc; ++s) {
-          const SrcDev& S = G.src[s];
-          double w = 0.0;
-          if (S.kind == 0) {
-            if (iw == S.i && jw == S.j && kw == S.k) w = S.amp;
-          } else {
-            const int crd[3] = {iw, jw, kw};
-            if (crd[S.axis] == S.index) {
-              const int u = crd[(S.axis + 1) % 3], v = crd[(S.axis + 2) % 3];
-              if (u >= S.lo1 && u < S.hi1 && v >= S.lo2 && v < S.hi2) {
-                if (S.inv_w2 > 0.0) {
-                  const double du = u - S.uc, dv = v - S.vc;
-                  w = S.amp * exp(-(du * du + dv * dv) * S.inv_w2);
-                } else {
-                  w = S.amp;
-                }
-              }
-            }
-          }
-          if (w != 0.0) {
-            const T val = (T)(w * sg[s]);
-            if (S.comp == 0) sx_ += val;
-            else if (S.comp == 1) sy_ += val;
-            else sz_ += val;
-          }
-        }
-
-        T dPx = T(0), dPy = T(0), dPz = T(0);
-        T Pnx = T(0), Pny = T(0), Pnz = T(0);
-        bool gcell = false;
-        if (GAIN) gcell = G.gain && ((m >> 6) & 1);
-        T d1 = T(0), d2 = T(0), d3 = T(0);
-        if (GAIN && gcell) {
-          const T* __restrict__ P0x = G.P[sel][0];
-          const T* __restrict__ P0y = G.P[sel][1];
-          const T* __restrict__ P0z = G.P[sel][2];
-          T* __restrict__ P1x = G.P[sel ^ 1][0];
-          T* __restrict__ P1y = G.P[sel ^ 1][1];
-          T* __restrict__ P1z = G.P[sel ^ 1][2];
-          const T pnx = P0x[cidx], pny = P0y[cidx], pnz = P0z[cidx];
-          const T pmx = P1x[cidx], pmy = P1y[cidx], pmz = P1z[cidx];
-          d1 = G.dN[0][cidx];
-          d2 = G.dN[1][cidx];
-          d3 = G.dN[2][cidx];
-          const T dn12 = G.n12eq + (d1 - d2);
-          const T drive = G.a3 * dn12;
-          Pnx = G.a1 * pnx - G.a2 * pmx + drive * eCx;
-          Pny = G.a1 * pny - G.a2 * pmy + drive * eCy;
-          Pnz = G.a1 * pnz - G.a2 * pmz + drive * eCz;
-          if (G.noise != T(0)) {
-            T xa, xb, xc;
-            gain_normals(G.seed, cidx, n, xa, xb, xc);
-            Pnx += G.noise * xa;
-            Pny += G.noise * xb;
-            Pnz += G.noise * xc;
-          }
-          dPx = Pnx - pnx;
-          dPy = Pny - pny;
-          dPz = Pnz - pnz;
-          P1x[cidx] = Pnx;
-          P1y[cidx] = Pny;
-          P1z[cidx] = Pnz;
-        }
-
-        T enx = eCx + G.cE[clx] * curlx - G.cP[clx] * (dPx + sx_);
-        T eny = eCy + G.cE[cly] * curly - G.cP[cly] * (dPy + sy_);
-        T enz = eCz + G.cE[clz] * curlz - G.cP[clz] * (dPz + sz_);
-        // tangential E held at zero on the index-0 plane of non-periodic axes
-        if ((jw == 0 && !py) || (kw == 0 && !pz)) enx = T(0);
-        if ((iw == 0 && !px) || (kw == 0 && !pz)) eny = T(0);
-        if ((iw == 0 && !px) || (jw == 0 && !py)) enz = T(0);
-
-        if (GAIN && gcell) {
-          const T r = G.q * (T(0.5) * (enx + eCx) * dPx + T(0.5) * (eny + eCy) * dPy + T(0.5) * (enz + eCz) * dPz);
-          const T inc1 = G.D[0][0] * d1 + G.D[0][1] * d2 + G.D[0][2] * d3 + G.w[0] * r;
-          const T inc2 = G.D[1][0] * d1 + G.D[1][1] * d2 + G.D[1][2] * d3 + G.w[1] * r;
-          const T inc3 = G.D[2][0] * d1 + G.D[2][1] * d2 + G.D[2][2] * d3 + G.w[2] * r;
-          if (sizeof(T) == 4) {
-            // compensated (Kahan) accumulation of the population deviations
-            T c1 = G.cmp[0][cidx], c2 = G.cmp[1][cidx], c3 = G.cmp[2][cidx];
-            const T y1 = inc1 - c1, y2 = inc2 - c2, y3 = inc3 - c3;
-            const T t1 = d1 + y1, t2 = d2 + y2, t3 = d3 + y3;
-            G.cmp[0][cidx] = (t1 - d1) - y1;
-            G.cmp[1][cidx] = (t2 - d2) - y2;
-            G.cmp[2][cidx] = (t3 - d3) - y3;
-            G.dN[0][cidx] = t1;
-            G.dN[1][cidx] = t2;
-            G.dN[2][cidx] = t3;
-          } else {
-            G.dN[0][cidx] = d1 + inc1;
-            G.dN[1][cidx] = d2 + inc2;
-            G.dN[2][cidx] = d3 + inc3;
-          }
-        }
-
+        const bool gcell = GAIN && G.gain && ((m >> 6) & 1);
+        GainState<T> gs{};
+        if (GAIN && gcell) load_gain(G, sel, cidx, gs);
+        T enx, eny, enz;
+        e_node<T, GAIN>(G, sg, sel, n, iw, jw, kw, cidx, m, gcell, gs, hz - sHz[tid - bx], hy - hPy, hx - hPx,
+                        hz - sHz[tid - 1], hy - sHy[tid - 1], hx - sHx[tid - bx], eCx, eCy, eCz, enx, eny, enz);
         G.F[sel ^ 1][0][cidx] = enx;
         G.F[sel ^ 1][1][cidx] = eny;
         G.F[sel ^ 1][2][cidx] = enz;
@@ -465,7 +247,306 @@ cudaError_t launch_step(const StepGrid<T>* grids, const int4* items, int nitems,
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- observers
+// =====================================================================
+// TMA-staged step kernel (non-periodic grids)
+// =====================================================================
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of an mbarrier, giving up after about 2 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    for (int r = 0; r < 64; ++r)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > 2000000000ull) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Byte layout of the TMA kernel's shared memory (host and device agree).
+template <typename T>
+struct TmaLayout {
+  static constexpr int AX = 16 / (int)sizeof(T);       // x pad: one 16-byte unit each side
+  static constexpr int BXT = kTmaOX + 2 * AX;          // box width (elements)
+  size_t grid_off, sg_off, bar_off, stage_off, field_bytes, mat_bytes, stage_bytes, h_off, total;
+  __host__ __device__ explicit TmaLayout(int oy) {
+    const int byt = oy + 2;
+    grid_off = 0;
+    sg_off = align128(sizeof(StepGrid<T>));
+    bar_off = sg_off + align128(kMaxSrc * sizeof(double));
+    stage_off = bar_off + 128;
+    field_bytes = align128((size_t)6 * BXT * byt * sizeof(T));
+    mat_bytes = align128((size_t)kTmaOX * oy);
+    stage_bytes = field_bytes + mat_bytes;
+    h_off = stage_off + (size_t)kTmaStages * stage_bytes;
+    total = h_off + (size_t)3 * (oy + 1) * (kTmaOX + 1) * sizeof(T) + 128;  // + base alignment slack
+  }
+};
+
+template <typename T>
+size_t step_tma_smem_bytes(int oy) {
+  return TmaLayout<T>(oy).total;
+}
+
+template <typename T, bool GAIN>
+__global__ void __launch_bounds__(256) k_step_tma(const StepGrid<T>* __restrict__ grids,
+                                                  const TmaGrid* __restrict__ maps, const int4* __restrict__ items,
+                                                  int nitems, int offset) {
+  constexpr int OX = kTmaOX;
+  constexpr int S = kTmaStages;
+  constexpr int AX = TmaLayout<T>::AX;
+  constexpr int BXT = TmaLayout<T>::BXT;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // TMA destinations need 128-byte alignment: align the dynamic base explicitly
+  unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  const int OY = blockDim.y;
+  const int BYT = OY + 2;
+  const int PL = BYT * BXT;      // elements of one component plane in a stage
+  const int HW = OX + 1;         // row length of the H plane buffer
+  const int HPL = (OY + 1) * HW;
+  const TmaLayout<T> lay(OY);
+  StepGrid<T>& G = *reinterpret_cast<StepGrid<T>*>(smem + lay.grid_off);
+  double* sg = reinterpret_cast<double*>(smem + lay.sg_off);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + lay.bar_off);
+  unsigned char* stages = smem + lay.stage_off;
+  T* sHx = reinterpret_cast<T*>(smem + lay.h_off);
+  T* sHy = sHx + HPL;
+  T* sHz = sHy + HPL;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * OX + tx;
+  const unsigned tx_bytes = (unsigned)(6 * PL * sizeof(T) + OX * OY);
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  unsigned ld = 0;  // plane loads issued by this block so far (same value in every thread)
+  int cur = -1;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int4 item = items[it];
+    __syncthreads();
+    if (item.x != cur) {
+      load_record(grids + item.x, smem + lay.grid_off, tid, OX * OY);
+      cur = item.x;
+    }
+    __syncthreads();
+    const long long n = G.step + offset;
+    if (n >= G.step_end) continue;
+    source_waveforms(G, n, tid, sg);
+
+    const int nx = G.nx, ny = G.ny, px = G.px;
+    const int x0 = item.y, y0 = item.z, z0 = item.w & 0xffff, z1 = (item.w >> 16) & 0xffff;
+    const int kstart = z0 > 0 ? z0 - 1 : z0;
+    const int NP = z1 - kstart + 1;  // planes kstart .. z1 (E of plane z1 feeds H of plane z1-1)
+    const int sel = (int)(n & 1);
+    const CUtensorMap* fmap = &maps[item.x].fields;
+    const CUtensorMap* mmap = &maps[item.x].mat;
+    const unsigned q0 = ld;
+
+    auto issue = [&](unsigned q, int plane) {
+      const int s = (int)(q % S);
+      unsigned char* dst = stages + (size_t)s * lay.stage_bytes;
+      mbar_arrive_expect_tx(&full[s], tx_bytes);
+      tma_load_4d(dst, fmap, x0 - AX, y0 - 1, plane, sel * 6, &full[s]);
+      tma_load_3d(dst + lay.field_bytes, mmap, x0, y0, plane, &full[s]);
+    };
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      for (int p = 0; p < S && p < NP; ++p) issue(q0 + p, kstart + p);
+    }
+    ld = q0 + (unsigned)(NP < S ? NP : S);
+    __syncthreads();
+
+    const int i = x0 + tx, j = y0 + ty;
+    const bool own = i < nx && j < ny;
+    const int xo = tx + AX, yo = ty + 1;  // own node in the staged box
+    T hPx = T(0), hPy = T(0);
+    bool ok = true;
+
+    for (int p = 0; p < NP - 1; ++p) {
+      const int k = kstart + p;
+      const unsigned q = q0 + p;
+      if (p == 0) ok = ok && mbar_wait(&full[q % S], (q / S) & 1);
+      ok = ok && mbar_wait(&full[(q + 1) % S], ((q + 1) / S) & 1);
+      const T* Fk = reinterpret_cast<const T*>(stages + (size_t)(q % S) * lay.stage_bytes);
+      const T* Fn = reinterpret_cast<const T*>(stages + (size_t)((q + 1) % S) * lay.stage_bytes);
+      const uint8_t* Mk = stages + (size_t)(q % S) * lay.stage_bytes + lay.field_bytes;
+      const bool active = k >= z0;
+      const long long cidx = pidx3(i, j, k, px, ny);
+
+      // own node: material, gain state (issued before the H work)
+      unsigned m = 0;
+      bool gcell = false;
+      GainState<T> gs{};
+      if (ok && own && active) {
+        m = Mk[ty * OX + tx];
+        gcell = GAIN && G.gain && ((m >> 6) & 1);
+        if (GAIN && gcell) load_gain(G, sel, cidx, gs);
+      }
+
+      // H^{n+1/2} of plane k at a staged node (xx, yy) = node (x0 - AX + xx, y0 - 1 + yy)
+      auto h_at = [&](int xx, int yy, int ii, int jj, bool wr, T& hx, T& hy, T& hz) {
+        const T* Ex = Fk;
+        const T* Ey = Fk + PL;
+        const T* Ez = Fk + 2 * PL;
+        const int o = yy * BXT + xx;
+        const T ex = Ex[o], ey = Ey[o], ez = Ez[o];
+        h_node(G, sel, wr, ii, jj, k, Ez[o + BXT] - ez, Fn[PL + o] - ey, Fn[o] - ex, Ez[o + 1] - ez, Ey[o + 1] - ey,
+               Ex[o + BXT] - ex, Fk[3 * PL + o], Fk[4 * PL + o], Fk[5 * PL + o], hx, hy, hz);
+      };
+
+      T hx = T(0), hy = T(0), hz = T(0);
+      if (ok && own) h_at(xo, yo, i, j, active, hx, hy, hz);
+      sHx[yo * HW + tx + 1] = hx;
+      sHy[yo * HW + tx + 1] = hy;
+      sHz[yo * HW + tx + 1] = hz;
+      if (ty == 0) {  // -y halo row: node (i, y0-1)
+        T a = T(0), b = T(0), c = T(0);
+        if (ok && y0 > 0 && i < nx) h_at(xo, 0, i, y0 - 1, false, a, b, c);
+        sHx[tx + 1] = a;
+        sHy[tx + 1] = b;
+        sHz[tx + 1] = c;
+      } else if (ty == 1 && tx < OY) {  // -x halo column: node (x0-1, y0+tx)
+        T a = T(0), b = T(0), c = T(0);
+        if (ok && x0 > 0 && y0 + tx < ny) h_at(AX - 1, tx + 1, x0 - 1, y0 + tx, false, a, b, c);
+        sHx[(tx + 1) * HW] = a;
+        sHy[(tx + 1) * HW] = b;
+        sHz[(tx + 1) * HW] = c;
+      }
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(G.err, 2);
+        return;
+      }
+
+      if (own && active) {
+        const int oh = yo * HW + tx + 1;
+        const int oe = yo * BXT + xo;
+        T enx, eny, enz;
+        e_node<T, GAIN>(G, sg, sel, n, i, j, k, cidx, m, gcell, gs, hz - sHz[oh - HW], hy - hPy, hx - hPx,
+                        hz - sHz[oh - 1], hy - sHy[oh - 1], hx - sHx[oh - HW], Fk[oe], Fk[PL + oe], Fk[2 * PL + oe],
+                        enx, eny, enz);
+        G.F[sel ^ 1][0][cidx] = enx;
+        G.F[sel ^ 1][1][cidx] = eny;
+        G.F[sel ^ 1][2][cidx] = enz;
+        G.F[sel ^ 1][3][cidx] = hx;
+        G.F[sel ^ 1][4][cidx] = hy;
+        G.F[sel ^ 1][5][cidx] = hz;
+      }
+      hPx = hx;
+      hPy = hy;
+      __syncthreads();
+      // stage of plane p is free: refill it with plane p + S
+      if (tid == 0 && p + S < NP) {
+        fence_proxy_async_smem();
+        issue(q + S, kstart + p + S);
+      }
+    }
+    ld = q0 + (unsigned)NP;
+  }
+}
+
+template <typename T>
+int step_blocks_per_sm(bool tma, bool gain, int bx, int by) {
+  int nb = 0;
+  cudaError_t e;
+  if (tma) {
+    const size_t smem = step_tma_smem_bytes<T>(by);
+    if (gain) {
+      cudaFuncSetAttribute(k_step_tma<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_tma<T, true>, kTmaOX * by, smem);
+    } else {
+      cudaFuncSetAttribute(k_step_tma<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_tma<T, false>, kTmaOX * by, smem);
+    }
+  } else {
+    const size_t smem = step_smem_bytes<T>(bx, by);
+    if (gain) {
+      if (smem > 48 * 1024) cudaFuncSetAttribute(k_step<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<T, true>, bx * by, smem);
+    } else {
+      if (smem > 48 * 1024) cudaFuncSetAttribute(k_step<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step<T, false>, bx * by, smem);
+    }
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
+
+template <typename T>
+cudaError_t launch_step_tma(const StepGrid<T>* grids, const TmaGrid* maps, const int4* items, int nitems, int offset,
+                            int oy, bool gain, int grid_blocks, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  const size_t smem = step_tma_smem_bytes<T>(oy);
+  const int blocks = (grid_blocks > 0 && grid_blocks < nitems) ? grid_blocks : nitems;
+  dim3 blk(kTmaOX, oy);
+  cudaError_t e;
+  if (gain) {
+    e = cudaFuncSetAttribute(k_step_tma<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_step_tma<T, true><<<blocks, blk, smem, st>>>(grids, maps, items, nitems, offset);
+  } else {
+    e = cudaFuncSetAttribute(k_step_tma<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_step_tma<T, false><<<blocks, blk, smem, st>>>(grids, maps, items, nitems, offset);
+  }
+  return cudaGetLastError();
+}
+
+// =====================================================================
+// Observers
+// =====================================================================
 __device__ __forceinline__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -489,12 +570,12 @@ __global__ void __launch_bounds__(256) k_observe(const ObsGrid<T>* __restrict__ 
   const long long n = G.step + offset;
   if (n >= G.step_end) return;
   const int sel = (int)(n & 1);
-  const int nx = G.nx, ny = G.ny;
+  const int px = G.px, ny = G.ny;
   const long long slot = n % G.cap;
   if (it.y < 0) {
     for (int q = threadIdx.x; q < G.nprobe * 3; q += blockDim.x) {
       const int p = q / 3, c = q % 3;
-      const T v = G.F[sel ^ 1][c][lidx(G.probe[p][0], G.probe[p][1], G.probe[p][2], nx, ny)];
+      const T v = G.F[sel ^ 1][c][pidx3(G.probe[p][0], G.probe[p][1], G.probe[p][2], px, ny)];
       G.probe_ring[(slot * G.nprobe + p) * 3 + c] = v;
       if (!isfinite((double)v)) atomicOr(G.err, 1);
     }
@@ -521,7 +602,7 @@ __global__ void __launch_bounds__(256) k_observe(const ObsGrid<T>* __restrict__ 
       c[d] = pp;
       c[d1] = uu;
       c[d2] = vv;
-      return lidx(c[0], c[1], c[2], nx, ny);
+      return pidx3(c[0], c[1], c[2], px, ny);
     };
     const long long a = at(p, u, v), av = at(p, u, v + 1), au = at(p, u + 1, v);
     const long long b = at(p - 1, u, v), bv = at(p - 1, u, v + 1), bu = at(p - 1, u + 1, v);
@@ -577,7 +658,9 @@ cudaError_t launch_advance(StepGrid<T>* sg, ObsGrid<T>* og, int ngrids, int coun
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- energy
+// =====================================================================
+// Energy
+// =====================================================================
 template <typename T>
 __global__ void __launch_bounds__(256) k_energy(const T* __restrict__ ex, const T* __restrict__ ey,
                                                 const T* __restrict__ ez, const T* __restrict__ hx,
@@ -624,10 +707,12 @@ cudaError_t launch_energy(const T* const* F6, const uint8_t* mat, double e0, dou
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- rasterizer
-__global__ void k_rasterize(uint8_t* __restrict__ mat, int nx, int ny, int nz, const double* __restrict__ sph,
+// =====================================================================
+// Rasterizer
+// =====================================================================
+__global__ void k_rasterize(uint8_t* __restrict__ mat, int nx, int ny, int nz, int px, const double* __restrict__ sph,
                             const int* __restrict__ bstart, const int* __restrict__ blist, int bin, int bnx, int bny,
-                            int bnz, double lo0, double lo1, double lo2, double hi0, double hi1, double hi2) {
+                            double lo0, double lo1, double lo2, double hi0, double hi1, double hi2) {
   const long long ncell = (long long)nx * ny * nz;
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncell) return;
@@ -635,9 +720,9 @@ __global__ void k_rasterize(uint8_t* __restrict__ mat, int nx, int ny, int nz, c
   const int j = (int)((c / nx) % ny);
   const int k = (int)(c / ((long long)nx * ny));
   const int b = ((k / bin) * bny + (j / bin)) * bnx + (i / bin);
-  const double px[4] = {i + 0.5, (double)i, (double)i, i + 0.5};
-  const double py[4] = {(double)j, j + 0.5, (double)j, j + 0.5};
-  const double pz[4] = {(double)k, (double)k, k + 0.5, k + 0.5};
+  const double pxs[4] = {i + 0.5, (double)i, (double)i, i + 0.5};
+  const double pys[4] = {(double)j, j + 0.5, (double)j, j + 0.5};
+  const double pzs[4] = {(double)k, (double)k, k + 0.5, k + 0.5};
   bool ins[4] = {false, false, false, false};
   for (int q = bstart[b]; q < bstart[b + 1]; ++q) {
     const int s = blist[q];
@@ -645,7 +730,7 @@ __global__ void k_rasterize(uint8_t* __restrict__ mat, int nx, int ny, int nz, c
     const double rr = __dmul_rn(r, r);
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      const double dx = __dsub_rn(px[t], cx), dy = __dsub_rn(py[t], cy), dz = __dsub_rn(pz[t], cz);
+      const double dx = __dsub_rn(pxs[t], cx), dy = __dsub_rn(pys[t], cy), dz = __dsub_rn(pzs[t], cz);
       const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
       ins[t] = ins[t] || (d2 < rr);
     }
@@ -653,30 +738,32 @@ __global__ void k_rasterize(uint8_t* __restrict__ mat, int nx, int ny, int nz, c
   unsigned byte = 0;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
-    const bool inbox = px[t] >= lo0 && px[t] < hi0 && py[t] >= lo1 && py[t] < hi1 && pz[t] >= lo2 && pz[t] < hi2;
+    const bool inbox = pxs[t] >= lo0 && pxs[t] < hi0 && pys[t] >= lo1 && pys[t] < hi1 && pzs[t] >= lo2 && pzs[t] < hi2;
     if (t < 3) byte |= (inbox ? (ins[t] ? 2u : 1u) : 0u) << (2 * t);
     else if (inbox && ins[t]) byte |= 64u;
   }
-  mat[c] = (uint8_t)byte;
-  (void)bnz;
+  mat[pidx3(i, j, k, px, ny)] = (uint8_t)byte;
 }
 
-cudaError_t launch_rasterize(uint8_t* mat, int nx, int ny, int nz, const double* spheres, const int* bin_start,
+cudaError_t launch_rasterize(uint8_t* mat, int nx, int ny, int nz, int px, const double* spheres, const int* bin_start,
                              const int* bin_list, int bin, int bnx, int bny, int bnz, const double* box,
                              cudaStream_t st) {
+  (void)bnz;
   const long long ncell = (long long)nx * ny * nz;
   const int threads = 256;
   const long long blocks = (ncell + threads - 1) / threads;
-  k_rasterize<<<(unsigned)blocks, threads, 0, st>>>(mat, nx, ny, nz, spheres, bin_start, bin_list, bin, bnx, bny,
-                                                     bnz, box[0], box[1], box[2], box[3], box[4], box[5]);
+  k_rasterize<<<(unsigned)blocks, threads, 0, st>>>(mat, nx, ny, nz, px, spheres, bin_start, bin_list, bin, bnx, bny,
+                                                     box[0], box[1], box[2], box[3], box[4], box[5]);
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- gain init
+// =====================================================================
+// Gain initialization and conversions
+// =====================================================================
 template <typename T>
-__global__ void k_gain_init(StepGrid<T> G, long long ncell, T d1, T d2, T d3) {
+__global__ void k_gain_init(StepGrid<T> G, long long nstore, T d1, T d2, T d3) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
+  if (c >= nstore) return;
   const bool g = (G.mat[c] >> 6) & 1;
   for (int s = 0; s < 2; ++s)
     for (int q = 0; q < 3; ++q) G.P[s][q][c] = T(0);
@@ -691,12 +778,11 @@ __global__ void k_gain_init(StepGrid<T> G, long long ncell, T d1, T d2, T d3) {
 }
 
 template <typename T>
-cudaError_t launch_gain_init(const StepGrid<T>* g, long long ncell, T d1, T d2, T d3, cudaStream_t st) {
-  k_gain_init<T><<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(*g, ncell, d1, d2, d3);
+cudaError_t launch_gain_init(const StepGrid<T>* g, long long nstore, T d1, T d2, T d3, cudaStream_t st) {
+  k_gain_init<T><<<(unsigned)((nstore + 255) / 256), 256, 0, st>>>(*g, nstore, d1, d2, d3);
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- conversions
 template <typename T>
 __global__ void k_to_double(const T* __restrict__ s, double* __restrict__ d, long long n) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -720,17 +806,23 @@ cudaError_t launch_from_double(const double* src, T* dst, long long n, cudaStrea
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- instantiations
-#define FDTD_INST(T)                                                                                          \
-  template size_t step_smem_bytes<T>(int, int);                                                               \
-  template cudaError_t launch_step<T>(const StepGrid<T>*, const int4*, int, int, int, int, bool, int,        \
-                                      cudaStream_t);                                                          \
-  template cudaError_t launch_observe<T>(const ObsGrid<T>*, const int4*, int, int, cudaStream_t);            \
-  template cudaError_t launch_advance<T>(StepGrid<T>*, ObsGrid<T>*, int, int, cudaStream_t);                 \
-  template cudaError_t launch_gain_init<T>(const StepGrid<T>*, long long, T, T, T, cudaStream_t);            \
-  template cudaError_t launch_energy<T>(const T* const*, const uint8_t*, double, double, double, long long,  \
-                                        double*, unsigned int*, double*, int*, cudaStream_t);                \
-  template cudaError_t launch_to_double<T>(const T*, double*, long long, cudaStream_t);                      \
+// =====================================================================
+// Instantiations
+// =====================================================================
+#define FDTD_INST(T)                                                                                           \
+  template size_t step_smem_bytes<T>(int, int);                                                                \
+  template size_t step_tma_smem_bytes<T>(int);                                                                 \
+  template int step_blocks_per_sm<T>(bool, bool, int, int);                                                    \
+  template cudaError_t launch_step<T>(const StepGrid<T>*, const int4*, int, int, int, int, bool, int,         \
+                                      cudaStream_t);                                                           \
+  template cudaError_t launch_step_tma<T>(const StepGrid<T>*, const TmaGrid*, const int4*, int, int, int, bool, \
+                                          int, cudaStream_t);                                                  \
+  template cudaError_t launch_observe<T>(const ObsGrid<T>*, const int4*, int, int, cudaStream_t);             \
+  template cudaError_t launch_advance<T>(StepGrid<T>*, ObsGrid<T>*, int, int, cudaStream_t);                  \
+  template cudaError_t launch_gain_init<T>(const StepGrid<T>*, long long, T, T, T, cudaStream_t);             \
+  template cudaError_t launch_energy<T>(const T* const*, const uint8_t*, double, double, double, long long,   \
+                                        double*, unsigned int*, double*, int*, cudaStream_t);                 \
+  template cudaError_t launch_to_double<T>(const T*, double*, long long, cudaStream_t);                       \
   template cudaError_t launch_from_double<T>(const double*, T*, long long, cudaStream_t);
 
 FDTD_INST(float)

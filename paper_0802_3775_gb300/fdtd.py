@@ -72,6 +72,7 @@ SIGNATURES = {
     "fdtd_add_flux_plane": [_P, C.c_int32, C.c_int32, C.c_double, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                             C.POINTER(C.c_int32)],
     "fdtd_set_launch": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
+    "fdtd_set_kernel": [_P, C.c_int32],
     "fdtd_step_n": [_P, C.c_int64],
     "fdtd_sync": [_P],
     "fdtd_steps_done": [_P, C.POINTER(C.c_int64)],
@@ -83,6 +84,15 @@ SIGNATURES = {
     "fdtd_field_energy": [_P, _D],
     "fdtd_set_timing": [_P, C.c_int32],
     "fdtd_kernel_time": [_P, _D, C.POINTER(C.c_int64)],
+    "fdtd_set_step_limit": [_P, C.c_int64],
+    "fdtd_batch_create": [C.POINTER(_P), C.c_int32, _P, C.POINTER(_P)],
+    "fdtd_batch_destroy": [_P],
+    "fdtd_batch_set_launch": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
+    "fdtd_batch_set_graph": [_P, C.c_int32],
+    "fdtd_batch_step_n": [_P, C.c_int64],
+    "fdtd_batch_sync": [_P],
+    "fdtd_batch_set_timing": [_P, C.c_int32],
+    "fdtd_batch_kernel_time": [_P, _D, C.POINTER(C.c_int64)],
     "fdtd_save_state": [_P, C.c_char_p],
     "fdtd_load_state": [_P, C.c_char_p],
 }
@@ -256,6 +266,14 @@ class Grid:
     def set_launch(self, bx=32, by=8, zdepth=0, grid_blocks=0):
         check(self._lib.fdtd_set_launch(self.h, int(bx), int(by), int(zdepth), int(grid_blocks)))
 
+    def set_kernel(self, kind):
+        """0 automatic, 1 plain-load step kernel, 2 TMA-staged step kernel."""
+        kinds = {"auto": 0, "plain": 1, "tma": 2}
+        check(self._lib.fdtd_set_kernel(self.h, int(kinds.get(kind, kind))))
+
+    def set_step_limit(self, limit):
+        check(self._lib.fdtd_set_step_limit(self.h, int(limit)))
+
     # -- stepping
     def step(self, n=1):
         check(self._lib.fdtd_step_n(self.h, int(n)))
@@ -351,3 +369,55 @@ class Grid:
 
     def __exit__(self, *a):
         self.close()
+
+
+KERNELS = {"auto": 0, "plain": 1, "tma": 2}
+
+
+class Batch:
+    """Many grids stepped together: one step-kernel launch per time step over
+    the work items of every member (see fdtd_batch_* in include/fdtd.h)."""
+
+    def __init__(self, grids, stream=None):
+        self._lib = load_library()
+        self.grids = list(grids)
+        if stream is None:
+            stream = self.grids[0].stream_ptr
+        st = int(getattr(stream, "cuda_stream", stream)) if stream else None
+        arr = (_P * len(self.grids))(*[g.h.value for g in self.grids])
+        h = C.c_void_p()
+        check(self._lib.fdtd_batch_create(arr, len(self.grids), C.c_void_p(st) if st else None, C.byref(h)))
+        self.h = h
+
+    def set_launch(self, kernel="auto", by=8, zdepth=0, grid_blocks=0):
+        check(self._lib.fdtd_batch_set_launch(self.h, int(KERNELS.get(kernel, kernel)), int(by), int(zdepth),
+                                              int(grid_blocks)))
+
+    def set_graph(self, steps_per_graph):
+        check(self._lib.fdtd_batch_set_graph(self.h, int(steps_per_graph)))
+
+    def step(self, n=1):
+        check(self._lib.fdtd_batch_step_n(self.h, int(n)))
+
+    def sync(self):
+        check(self._lib.fdtd_batch_sync(self.h))
+
+    def set_timing(self, on=True):
+        check(self._lib.fdtd_batch_set_timing(self.h, int(bool(on))))
+
+    def kernel_time(self):
+        ms = C.c_double()
+        n = C.c_int64()
+        check(self._lib.fdtd_batch_kernel_time(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.fdtd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -81,10 +81,15 @@ def test_fp64_small_opal_all_observers(source):
     assert abs(g.field_energy() - o.energy()) <= 1e-12 * o.energy()
 
 
-@pytest.mark.parametrize("launch", [(32, 8, 0, 0), (64, 4, 7, 0), (32, 16, 3, 5), (16, 2, 0, 0)])
-def test_fp32_passive_fields_and_flux(launch):
+LAUNCHES = [("tma", (32, 8, 0, 0)), ("tma", (32, 4, 7, 0)), ("tma", (32, 2, 3, 5)), ("plain", (32, 8, 0, 0)),
+            ("plain", (64, 4, 7, 0)), ("plain", (32, 16, 3, 5)), ("plain", (16, 2, 0, 0))]
+
+
+@pytest.mark.parametrize("kernel,launch", LAUNCHES)
+def test_fp32_passive_fields_and_flux(kernel, launch):
     spec = small_opal(precision="f32", source="sheet", sigma=0.08)
     g = gpu_grid(spec)
+    g.set_kernel(kernel)
     g.set_launch(*launch)
     o = oracle_grid(spec, coef32=True)
     g.step(1200)
@@ -94,17 +99,38 @@ def test_fp32_passive_fields_and_flux(launch):
     assert rel_l2(g.read_probes(), o.probe_series()) <= 1e-5
 
 
+@pytest.mark.parametrize("kernel", ["tma", "plain"])
+def test_fp64_both_kernels_match_oracle(kernel):
+    gain = inputs.GainSpec(pump=5e11, noise_amp=1e-3, init="ground")
+    spec = small_opal(n_cells=2, res=8, npml=5, precision="f64", source="sheet", gain=gain)
+    g = gpu_grid(spec)
+    g.set_kernel(kernel)
+    o = oracle_grid(spec)
+    g.step(250)
+    o.step(250)
+    assert _fields_gpu_vs_oracle(g, o) <= 1e-12
+    assert rel_l2(g.read_gain(3), o.dN[1:].transpose(0, 3, 2, 1)) <= 1e-9
+    assert rel_l2(g.read_flux(), o.flux_series()) <= 1e-12
+
+
 def test_results_do_not_depend_on_launch_shape():
-    spec = small_opal(precision="f32", source="dipole")
-    out = []
-    for launch in [(32, 8, 0, 0), (64, 4, 5, 0), (32, 4, 2, 3)]:
+    gain = inputs.GainSpec(pump=5e11, noise_amp=1e-3, init="ground")
+    spec = small_opal(precision="f32", source="dipole", gain=gain)
+    out = {}
+    for kernel, launch in LAUNCHES:
         g = gpu_grid(spec)
+        g.set_kernel(kernel)
         g.set_launch(*launch)
         g.step(150)
-        out.append((g.read_fields(), g.read_probes()))
-    for F, P in out[1:]:
-        assert np.array_equal(F, out[0][0])
-        assert np.array_equal(P, out[0][1])
+        out.setdefault(kernel, []).append((g.read_fields(), g.read_probes(), g.read_gain(3), g.read_flux()))
+    for kernel, runs in out.items():
+        for F, P, N, T in runs[1:]:
+            assert np.array_equal(F, runs[0][0])
+            assert np.array_equal(P, runs[0][1])
+            assert np.array_equal(N, runs[0][2])
+            assert np.array_equal(T, runs[0][3])
+    # the two kernels share the per-node arithmetic
+    assert rel_l2(out["tma"][0][0], out["plain"][0][0]) <= 1e-6
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])
