@@ -268,6 +268,77 @@ int fdtd_batch_sync(fdtd_batch* b);
 int fdtd_batch_set_timing(fdtd_batch* b, int32_t on);
 int fdtd_batch_kernel_time(fdtd_batch* b, double* ms, int64_t* launches);
 
+/* ---------------------------------------------------------------- serving
+ * A request server keeps runs (disorder realizations, pulse or lasing runs of
+ * any grid size) resident on the device and steps them together: requests
+ * arriving while others run are admitted at chunk boundaries as slots and
+ * memory free up (first in, first out), their work shares the step launches,
+ * and each run stops exactly at its own step count, so its results do not
+ * depend on the other runs.  Device memory comes from the stream-ordered
+ * pool; admission keeps the estimated bytes of resident runs within the
+ * budget.  A worker thread does all device work. */
+typedef struct fdtd_server fdtd_server;
+
+typedef struct fdtd_server_desc {
+  int64_t hbm_budget_bytes;  /* device bytes resident runs may hold */
+  int32_t max_slots;         /* resident runs at most */
+  int32_t steps_per_chunk;   /* steps between admission / retirement points */
+  int32_t precision;         /* FDTD_FP32 or FDTD_FP64 (all requests) */
+  int32_t graph;             /* 1: replay chunks as CUDA graphs */
+} fdtd_server_desc;
+
+typedef struct fdtd_flux_desc {
+  int32_t axis, index, u0, u1, v0, v1;
+  double sign;
+} fdtd_flux_desc;
+
+/* One run.  All arrays are caller-owned and copied by fdtd_submit. */
+typedef struct fdtd_request {
+  fdtd_grid_desc grid;              /* record_capacity is set to `steps` */
+  const double* spheres;            /* n_spheres x (cx, cy, cz, r), grid units */
+  int64_t n_spheres;
+  double box_lo[3], box_hi[3];
+  const fdtd_gain_params* gain;     /* NULL: passive */
+  const fdtd_source_desc* sources;
+  int32_t n_sources;
+  const int32_t* probes;            /* n_probes x (i, j, k) */
+  int32_t n_probes;
+  const fdtd_flux_desc* fluxes;
+  int32_t n_fluxes;
+  int64_t steps;
+} fdtd_request;
+
+typedef struct fdtd_result {
+  int32_t status;         /* FDTD_OK, FDTD_E_BUSY (pending) or the run's error */
+  int64_t steps;
+  double submit_s, admit_s, done_s;  /* seconds since the server started */
+  double field_energy;    /* joules after the last step */
+  int32_t n_probes, n_fluxes;
+} fdtd_result;
+
+typedef struct fdtd_server_stats {
+  int64_t submitted, admitted, completed, failed, chunks;
+  int64_t cell_updates;   /* of completed runs */
+  int32_t resident, queued;
+  int64_t used_bytes;
+} fdtd_server_stats;
+
+int fdtd_server_create(const fdtd_server_desc* desc, void* stream, fdtd_server** out);
+/* Fails queued requests, finishes resident runs, joins the worker. */
+int fdtd_server_destroy(fdtd_server* s);
+/* E_BUDGET if the run alone exceeds the budget; E_INVAL on bad arrays. */
+int fdtd_submit(fdtd_server* s, const fdtd_request* req, uint64_t* ticket);
+/* timeout_ms 0: returns FDTD_E_BUSY while pending; > 0: waits up to that long
+ * and returns FDTD_E_TIMEOUT if still pending.  Fills `out` in every case. */
+int fdtd_poll(fdtd_server* s, uint64_t ticket, fdtd_result* out, int32_t timeout_ms);
+/* Results of a completed run: probes as double[steps][n_probes][3], flux as
+ * double[n_fluxes][steps] (caller-owned host buffers). */
+int fdtd_result_probes(fdtd_server* s, uint64_t ticket, double* out);
+int fdtd_result_flux(fdtd_server* s, uint64_t ticket, double* out);
+/* Forget a finished run's results. */
+int fdtd_result_release(fdtd_server* s, uint64_t ticket);
+int fdtd_server_get_stats(fdtd_server* s, fdtd_server_stats* out);
+
 /* Checkpoint: write / read every state array (fields, CPML slabs, gain state,
  * step count, recorders) to / from a file.  load requires a grid created
  * with the same description. */

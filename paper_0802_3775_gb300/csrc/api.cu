@@ -411,20 +411,20 @@ struct GridImpl final : GridBase {
       if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       cudaGetLastError();
       const int wave = sms * step_blocks_per_sm<T>(use_tma, sg.gain != 0, bx, by);
-      double best = -1.0;
+      // fewest z-ranges whose items fill at least 85 % of the last wave
       int best_chunks = 1;
+      double best = -1.0;
       for (int chunks = 1; chunks <= 64; ++chunks) {
         const int d = (desc.nz + chunks - 1) / chunks;
         if (d < 8 && chunks > 1) break;
         const int real_chunks = (desc.nz + d - 1) / d;
         const double waves = (double)tiles * real_chunks / wave;
         const double eff = waves / std::ceil(waves);
-        // prefer full waves, then fewer (longer) z-ranges
         if (eff > best + 1e-9) {
           best = eff;
           best_chunks = chunks;
         }
-        if (waves > 4.0) break;
+        if (eff >= 0.85) break;
       }
       depth = (desc.nz + best_chunks - 1) / best_chunks;
     }

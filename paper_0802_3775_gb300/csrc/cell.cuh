@@ -1,5 +1,6 @@
 // Per-node update arithmetic shared by the step kernels (identical results
-// whichever kernel stages the data).
+// whichever kernel stages the data: every multiply-add is written as an
+// explicit fma so the compiler cannot contract differently per kernel).
 //
 // Paper: Yee leapfrog (Sec. "Sample and numerical approach"), absorbing layer
 // (same section; CPML reading), four-level gain with the polarization at the
@@ -16,6 +17,9 @@ namespace fdtd {
 __device__ __forceinline__ long long pidx3(int i, int j, int k, int px, int ny) {
   return ((long long)k * ny + j) * px + i;
 }
+
+__device__ __forceinline__ float fmad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmad(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
 // multiplications with a Weyl key schedule.
@@ -73,11 +77,10 @@ __device__ __forceinline__ void gain_normals(unsigned long long seed, long long 
 
 // CPML-modified difference: D / kappa + psi with psi <- b psi + c D.
 template <typename T>
-__device__ __forceinline__ T pml_term(T D, const T* const* pr, int pos, const T* psi_in, T* psi_out,
-                                      long long pi) {
-  const T p = pr[1][pos] * psi_in[pi] + pr[2][pos] * D;
+__device__ __forceinline__ T pml_term(T D, const T* const* pr, int pos, const T* psi_in, T* psi_out, int pi) {
+  const T p = fmad(pr[1][pos], psi_in[pi], pr[2][pos] * D);
   if (psi_out) psi_out[pi] = p;
-  return pr[0][pos] * D + p;
+  return fmad(pr[0][pos], D, p);
 }
 
 // Slab coordinate of node index q on an axis of length n with slabs L0, L1 (-1 outside).
@@ -97,41 +100,94 @@ __device__ __forceinline__ void source_waveforms(const StepGrid<T>& G, long long
   }
 }
 
-// H~^{n+1/2} at node (iw, jw, kw) from the six forward differences of E^n.
+// Everything about a node column (i, j) that stays fixed while a tile
+// marches in z: CPML slab coordinates and memory offsets, the sources that
+// can touch the column, the PEC holds of its x and y faces.
+struct Column {
+  int i, j;
+  int sx, sy;         // slab coordinates, -1 outside the x / y slabs
+  int px0, py0, pz0;  // psi offsets of plane 0 (x slab, y slab) and the column offset in a z slab
+  unsigned src;       // bit s: source s can touch this column
+  bool pecx, pecy;    // i == 0 on a non-periodic x axis, j == 0 on a non-periodic y axis
+};
+
+template <typename T>
+__device__ __forceinline__ void make_column(const StepGrid<T>& G, int i, int j, Column& c, bool with_sources = true) {
+  c.i = i;
+  c.j = j;
+  c.sx = G.Sd[0] ? slab_index(i, G.nx, G.L[0], G.L[1]) : -1;
+  c.sy = G.Sd[1] ? slab_index(j, G.ny, G.L[2], G.L[3]) : -1;
+  c.px0 = j * G.Sd[0] + c.sx;
+  c.py0 = c.sy * G.nx + i;
+  c.pz0 = j * G.nx + i;
+  c.pecx = (i == 0) && !(G.per & 1);
+  c.pecy = (j == 0) && !(G.per & 2);
+  unsigned m = 0;
+  for (int s = 0; with_sources && s < G.nsrc; ++s) {
+    const SrcDev& S = G.src[s];
+    bool hit;
+    if (S.kind == 0) {
+      hit = (i == S.i && j == S.j);
+    } else if (S.axis == 2) {
+      hit = (i >= S.lo1 && i < S.hi1 && j >= S.lo2 && j < S.hi2);
+    } else if (S.axis == 0) {
+      hit = (i == S.index && j >= S.lo1 && j < S.hi1);
+    } else {
+      hit = (j == S.index && i >= S.lo2 && i < S.hi2);
+    }
+    if (hit) m |= 1u << s;
+  }
+  c.src = m;
+}
+
+// Per-plane facts shared by all nodes of plane k.
+struct Plane {
+  int k;
+  int sz;        // z slab coordinate, -1 outside
+  int pz_plane;  // psi offset of the plane in a z slab
+  int px_plane;  // k * ny * Sd0
+  int py_plane;  // k * Sd1 * nx
+  bool pecz;     // k == 0 on a non-periodic z axis
+};
+
+template <typename T>
+__device__ __forceinline__ Plane make_plane(const StepGrid<T>& G, int k) {
+  Plane p;
+  p.k = k;
+  p.sz = G.Sd[2] ? slab_index(k, G.nz, G.L[4], G.L[5]) : -1;
+  p.pz_plane = p.sz * G.ny * G.nx;
+  p.px_plane = k * G.ny * G.Sd[0];
+  p.py_plane = k * G.Sd[1] * G.nx;
+  p.pecz = (k == 0) && !(G.per & 4);
+  return p;
+}
+
+// H~^{n+1/2} at node (c.i, c.j, p.k) from the six forward differences of E^n.
 // Inside a slab the difference becomes D/kappa + psi; psi^{n-1/2} is read from
 // set `sel`, psi^{n+1/2} written to set sel^1 when `wr` (owner of the node).
 template <typename T>
-__device__ __forceinline__ void h_node(const StepGrid<T>& G, int sel, bool wr, int iw, int jw, int kw, T dyEz,
-                                       T dzEy, T dzEx, T dxEz, T dxEy, T dyEx, T hOx, T hOy, T hOz, T& hx, T& hy,
-                                       T& hz) {
-  const int nx = G.nx, ny = G.ny, nz = G.nz;
-  if (G.Sd[0]) {
-    const int s = slab_index(iw, nx, G.L[0], G.L[1]);
-    if (s >= 0) {
-      const long long pi = ((long long)kw * ny + jw) * G.Sd[0] + s;
-      dxEz = pml_term(dxEz, G.prof[0][1], iw, G.psiH[sel][0][0], wr ? G.psiH[sel ^ 1][0][0] : (T*)nullptr, pi);
-      dxEy = pml_term(dxEy, G.prof[0][1], iw, G.psiH[sel][0][1], wr ? G.psiH[sel ^ 1][0][1] : (T*)nullptr, pi);
-    }
+__device__ __forceinline__ void h_node(const StepGrid<T>& G, const Column& c, const Plane& p, int sel, bool wr,
+                                       T dyEz, T dzEy, T dzEx, T dxEz, T dxEy, T dyEx, T hOx, T hOy, T hOz, T& hx,
+                                       T& hy, T& hz) {
+  if (c.sx >= 0) {
+    const int pi = p.px_plane + c.px0;
+    dxEz = pml_term(dxEz, G.prof[0][1], c.i, G.psiH[sel][0][0], wr ? G.psiH[sel ^ 1][0][0] : (T*)nullptr, pi);
+    dxEy = pml_term(dxEy, G.prof[0][1], c.i, G.psiH[sel][0][1], wr ? G.psiH[sel ^ 1][0][1] : (T*)nullptr, pi);
   }
-  if (G.Sd[1]) {
-    const int s = slab_index(jw, ny, G.L[2], G.L[3]);
-    if (s >= 0) {
-      const long long pi = ((long long)kw * G.Sd[1] + s) * nx + iw;
-      dyEx = pml_term(dyEx, G.prof[1][1], jw, G.psiH[sel][1][0], wr ? G.psiH[sel ^ 1][1][0] : (T*)nullptr, pi);
-      dyEz = pml_term(dyEz, G.prof[1][1], jw, G.psiH[sel][1][1], wr ? G.psiH[sel ^ 1][1][1] : (T*)nullptr, pi);
-    }
+  if (c.sy >= 0) {
+    const int pi = p.py_plane + c.py0;
+    dyEx = pml_term(dyEx, G.prof[1][1], c.j, G.psiH[sel][1][0], wr ? G.psiH[sel ^ 1][1][0] : (T*)nullptr, pi);
+    dyEz = pml_term(dyEz, G.prof[1][1], c.j, G.psiH[sel][1][1], wr ? G.psiH[sel ^ 1][1][1] : (T*)nullptr, pi);
   }
-  if (G.Sd[2]) {
-    const int s = slab_index(kw, nz, G.L[4], G.L[5]);
-    if (s >= 0) {
-      const long long pi = ((long long)s * ny + jw) * nx + iw;
-      dzEy = pml_term(dzEy, G.prof[2][1], kw, G.psiH[sel][2][0], wr ? G.psiH[sel ^ 1][2][0] : (T*)nullptr, pi);
-      dzEx = pml_term(dzEx, G.prof[2][1], kw, G.psiH[sel][2][1], wr ? G.psiH[sel ^ 1][2][1] : (T*)nullptr, pi);
-    }
+  if (p.sz >= 0) {
+    const int pi = p.pz_plane + c.pz0;
+    dzEy = pml_term(dzEy, G.prof[2][1], p.k, G.psiH[sel][2][0], wr ? G.psiH[sel ^ 1][2][0] : (T*)nullptr, pi);
+    dzEx = pml_term(dzEx, G.prof[2][1], p.k, G.psiH[sel][2][1], wr ? G.psiH[sel ^ 1][2][1] : (T*)nullptr, pi);
   }
-  hx = hOx - G.cH * (dyEz - dzEy);
-  hy = hOy - G.cH * (dzEx - dxEz);
-  hz = hOz - G.cH * (dxEy - dyEx);
+  const T cH = G.cH;
+  hx = fmad(-cH, dyEz - dzEy, hOx);
+  hy = fmad(-cH, dzEx - dxEz, hOy);
+  hz = fmad(-cH, dxEy - dyEx, hOz);
 }
 
 // Gain state of one node, loaded ahead of its update.
@@ -160,90 +216,99 @@ __device__ __forceinline__ void load_gain(const StepGrid<T>& G, int sel, long lo
   }
 }
 
-// E^{n+1} at node (iw, jw, kw) from the six backward differences of H~^{n+1/2},
-// with the CPML (E-side memory updated in place), the soft sources, the gain
-// polarization current and populations (state `gs` of a gain cell), and the
-// PEC hold of tangential E on the index-0 planes of non-periodic axes.
+// Soft-source drive of the node's three E components at plane p.k.
+template <typename T>
+__device__ __forceinline__ void source_drive(const StepGrid<T>& G, const double* sg, const Column& c, const Plane& p,
+                                             T& sx, T& sy, T& sz) {
+  unsigned m = c.src;
+  while (m) {
+    const int s = __ffs(m) - 1;
+    m &= m - 1;
+    const SrcDev& S = G.src[s];
+    double w = 0.0;
+    if (S.kind == 0) {
+      if (p.k == S.k) w = S.amp;
+    } else {
+      int u, v;
+      bool on;
+      if (S.axis == 2) {
+        on = p.k == S.index;
+        u = c.i;
+        v = c.j;
+      } else if (S.axis == 0) {
+        on = p.k >= S.lo2 && p.k < S.hi2;
+        u = c.j;
+        v = p.k;
+      } else {
+        on = p.k >= S.lo1 && p.k < S.hi1;
+        u = p.k;
+        v = c.i;
+      }
+      if (on) {
+        if (S.inv_w2 > 0.0) {
+          const double du = u - S.uc, dv = v - S.vc;
+          w = S.amp * exp(-(du * du + dv * dv) * S.inv_w2);
+        } else {
+          w = S.amp;
+        }
+      }
+    }
+    if (w != 0.0) {
+      const T val = (T)(w * sg[s]);
+      if (S.comp == 0) sx += val;
+      else if (S.comp == 1) sy += val;
+      else sz += val;
+    }
+  }
+}
+
+// E^{n+1} at node (c.i, c.j, p.k) from the six backward differences of
+// H~^{n+1/2}, with the CPML (E-side memory updated in place), the soft
+// sources, the gain polarization current and populations (state `gs` of a
+// gain cell), and the PEC hold of tangential E on index-0 planes.
 template <typename T, bool GAIN>
-__device__ __forceinline__ void e_node(const StepGrid<T>& G, const double* sg, int sel, long long n, int iw, int jw,
-                                       int kw, long long cidx, unsigned m, bool gcell, const GainState<T>& gs,
-                                       T dyHz, T dzHy, T dzHx, T dxHz, T dxHy, T dyHx, T eCx, T eCy, T eCz, T& enx,
-                                       T& eny, T& enz) {
-  const int nx = G.nx, ny = G.ny, nz = G.nz;
-  if (G.Sd[0]) {
-    const int s = slab_index(iw, nx, G.L[0], G.L[1]);
-    if (s >= 0) {
-      const long long pi = ((long long)kw * ny + jw) * G.Sd[0] + s;
-      dxHz = pml_term(dxHz, G.prof[0][0], iw, G.psiE[0][0], G.psiE[0][0], pi);
-      dxHy = pml_term(dxHy, G.prof[0][0], iw, G.psiE[0][1], G.psiE[0][1], pi);
-    }
+__device__ __forceinline__ void e_node(const StepGrid<T>& G, const double* sg, const Column& c, const Plane& p,
+                                       int sel, long long n, long long cidx, unsigned m, bool gcell,
+                                       const GainState<T>& gs, T dyHz, T dzHy, T dzHx, T dxHz, T dxHy, T dyHx, T eCx,
+                                       T eCy, T eCz, T& enx, T& eny, T& enz) {
+  if (c.sx >= 0) {
+    const int pi = p.px_plane + c.px0;
+    dxHz = pml_term(dxHz, G.prof[0][0], c.i, G.psiE[0][0], G.psiE[0][0], pi);
+    dxHy = pml_term(dxHy, G.prof[0][0], c.i, G.psiE[0][1], G.psiE[0][1], pi);
   }
-  if (G.Sd[1]) {
-    const int s = slab_index(jw, ny, G.L[2], G.L[3]);
-    if (s >= 0) {
-      const long long pi = ((long long)kw * G.Sd[1] + s) * nx + iw;
-      dyHx = pml_term(dyHx, G.prof[1][0], jw, G.psiE[1][0], G.psiE[1][0], pi);
-      dyHz = pml_term(dyHz, G.prof[1][0], jw, G.psiE[1][1], G.psiE[1][1], pi);
-    }
+  if (c.sy >= 0) {
+    const int pi = p.py_plane + c.py0;
+    dyHx = pml_term(dyHx, G.prof[1][0], c.j, G.psiE[1][0], G.psiE[1][0], pi);
+    dyHz = pml_term(dyHz, G.prof[1][0], c.j, G.psiE[1][1], G.psiE[1][1], pi);
   }
-  if (G.Sd[2]) {
-    const int s = slab_index(kw, nz, G.L[4], G.L[5]);
-    if (s >= 0) {
-      const long long pi = ((long long)s * ny + jw) * nx + iw;
-      dzHy = pml_term(dzHy, G.prof[2][0], kw, G.psiE[2][0], G.psiE[2][0], pi);
-      dzHx = pml_term(dzHx, G.prof[2][0], kw, G.psiE[2][1], G.psiE[2][1], pi);
-    }
+  if (p.sz >= 0) {
+    const int pi = p.pz_plane + c.pz0;
+    dzHy = pml_term(dzHy, G.prof[2][0], p.k, G.psiE[2][0], G.psiE[2][0], pi);
+    dzHx = pml_term(dzHx, G.prof[2][0], p.k, G.psiE[2][1], G.psiE[2][1], pi);
   }
   const T curlx = dyHz - dzHy;
   const T curly = dzHx - dxHz;
   const T curlz = dxHy - dyHx;
   const int clx = m & 3, cly = (m >> 2) & 3, clz = (m >> 4) & 3;
 
-  // soft sources
   T srcx = T(0), srcy = T(0), srcz = T(0);
-  for (int s = 0; s < G.nsrc; ++s) {
-    const SrcDev& S = G.src[s];
-    double w = 0.0;
-    if (S.kind == 0) {
-      if (iw == S.i && jw == S.j && kw == S.k) w = S.amp;
-    } else {
-      const int a = S.axis;
-      const int along = a == 0 ? iw : a == 1 ? jw : kw;
-      if (along == S.index) {
-        const int u = a == 0 ? jw : a == 1 ? kw : iw;
-        const int v = a == 0 ? kw : a == 1 ? iw : jw;
-        if (u >= S.lo1 && u < S.hi1 && v >= S.lo2 && v < S.hi2) {
-          if (S.inv_w2 > 0.0) {
-            const double du = u - S.uc, dv = v - S.vc;
-            w = S.amp * exp(-(du * du + dv * dv) * S.inv_w2);
-          } else {
-            w = S.amp;
-          }
-        }
-      }
-    }
-    if (w != 0.0) {
-      const T val = (T)(w * sg[s]);
-      if (S.comp == 0) srcx += val;
-      else if (S.comp == 1) srcy += val;
-      else srcz += val;
-    }
-  }
+  if (c.src) source_drive(G, sg, c, p, srcx, srcy, srcz);
 
   T dPx = T(0), dPy = T(0), dPz = T(0);
   if (GAIN && gcell) {
     const T dn12 = G.n12eq + (gs.d1 - gs.d2);
     const T drive = G.a3 * dn12;
-    T Pnx = G.a1 * gs.pnx - G.a2 * gs.pmx + drive * eCx;
-    T Pny = G.a1 * gs.pny - G.a2 * gs.pmy + drive * eCy;
-    T Pnz = G.a1 * gs.pnz - G.a2 * gs.pmz + drive * eCz;
+    const T a1 = G.a1, a2 = G.a2;
+    T Pnx = fmad(drive, eCx, fmad(a1, gs.pnx, -(a2 * gs.pmx)));
+    T Pny = fmad(drive, eCy, fmad(a1, gs.pny, -(a2 * gs.pmy)));
+    T Pnz = fmad(drive, eCz, fmad(a1, gs.pnz, -(a2 * gs.pmz)));
     if (G.noise != T(0)) {
       T xa, xb, xc;
-      const long long lcell = ((long long)kw * ny + jw) * nx + iw;
+      const long long lcell = ((long long)p.k * G.ny + c.j) * G.nx + c.i;
       gain_normals(G.seed, lcell, n, xa, xb, xc);
-      Pnx += G.noise * xa;
-      Pny += G.noise * xb;
-      Pnz += G.noise * xc;
+      Pnx = fmad(G.noise, xa, Pnx);
+      Pny = fmad(G.noise, xb, Pny);
+      Pnz = fmad(G.noise, xc, Pnz);
     }
     dPx = Pnx - gs.pnx;
     dPy = Pny - gs.pny;
@@ -253,19 +318,19 @@ __device__ __forceinline__ void e_node(const StepGrid<T>& G, const double* sg, i
     G.P[sel ^ 1][2][cidx] = Pnz;
   }
 
-  enx = eCx + G.cE[clx] * curlx - G.cP[clx] * (dPx + srcx);
-  eny = eCy + G.cE[cly] * curly - G.cP[cly] * (dPy + srcy);
-  enz = eCz + G.cE[clz] * curlz - G.cP[clz] * (dPz + srcz);
-  const bool px = G.per & 1, py = G.per & 2, pz = G.per & 4;
-  if ((jw == 0 && !py) || (kw == 0 && !pz)) enx = T(0);
-  if ((iw == 0 && !px) || (kw == 0 && !pz)) eny = T(0);
-  if ((iw == 0 && !px) || (jw == 0 && !py)) enz = T(0);
+  enx = fmad(-G.cP[clx], dPx + srcx, fmad(G.cE[clx], curlx, eCx));
+  eny = fmad(-G.cP[cly], dPy + srcy, fmad(G.cE[cly], curly, eCy));
+  enz = fmad(-G.cP[clz], dPz + srcz, fmad(G.cE[clz], curlz, eCz));
+  if (c.pecy || p.pecz) enx = T(0);
+  if (c.pecx || p.pecz) eny = T(0);
+  if (c.pecx || c.pecy) enz = T(0);
 
   if (GAIN && gcell) {
-    const T r = G.q * (T(0.5) * (enx + eCx) * dPx + T(0.5) * (eny + eCy) * dPy + T(0.5) * (enz + eCz) * dPz);
-    const T inc1 = G.D[0][0] * gs.d1 + G.D[0][1] * gs.d2 + G.D[0][2] * gs.d3 + G.w[0] * r;
-    const T inc2 = G.D[1][0] * gs.d1 + G.D[1][1] * gs.d2 + G.D[1][2] * gs.d3 + G.w[1] * r;
-    const T inc3 = G.D[2][0] * gs.d1 + G.D[2][1] * gs.d2 + G.D[2][2] * gs.d3 + G.w[2] * r;
+    const T hx_ = T(0.5) * (enx + eCx), hy_ = T(0.5) * (eny + eCy), hz_ = T(0.5) * (enz + eCz);
+    const T r = G.q * fmad(hz_, dPz, fmad(hy_, dPy, hx_ * dPx));
+    const T inc1 = fmad(G.w[0], r, fmad(G.D[0][2], gs.d3, fmad(G.D[0][1], gs.d2, G.D[0][0] * gs.d1)));
+    const T inc2 = fmad(G.w[1], r, fmad(G.D[1][2], gs.d3, fmad(G.D[1][1], gs.d2, G.D[1][0] * gs.d1)));
+    const T inc3 = fmad(G.w[2], r, fmad(G.D[2][2], gs.d3, fmad(G.D[2][1], gs.d2, G.D[2][0] * gs.d1)));
     if (sizeof(T) == 4) {
       // compensated (Kahan) accumulation of the population deviations
       const T y1 = inc1 - gs.c1, y2 = inc2 - gs.c2, y3 = inc3 - gs.c3;

@@ -150,11 +150,14 @@ __global__ void __launch_bounds__(512) k_step(const StepGrid<T>* __restrict__ gr
       yCz = ldz(Ez, vrow && vk0, cr);
     }
     T hPx = T(0), hPy = T(0);
+    Column col;
+    make_column(G, iw, jw, col, owner);
 
     for (int k = kstart; k < z1; ++k) {
       bool vk;
       const int kw = kwrap(k, vk);
       const bool active = k >= z0;
+      const Plane pl = make_plane(G, kw);
       // prefetch the next plane
       T eNNx = T(0), eNNy = T(0), eNNz = T(0), hONx = T(0), hONy = T(0), hONz = T(0);
       T xNy = T(0), xNz = T(0), yNx = T(0), yNz = T(0);
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(512) k_step(const StepGrid<T>* __restrict__ gr
 
       T hx = T(0), hy = T(0), hz = T(0);
       if (valid && vk) {
-        h_node(G, sel, owner && active, iw, jw, kw, sEz[se + EW] - eCz, eNy - eCy, eNx - eCx, sEz[se + 1] - eCz,
+        h_node(G, col, pl, sel, owner && active, sEz[se + EW] - eCz, eNy - eCy, eNx - eCx, sEz[se + 1] - eCz,
                sEy[se + 1] - eCy, sEx[se + EW] - eCx, hOx, hOy, hOz, hx, hy, hz);
       }
       sHx[tid] = hx;
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(512) k_step(const StepGrid<T>* __restrict__ gr
         GainState<T> gs{};
         if (GAIN && gcell) load_gain(G, sel, cidx, gs);
         T enx, eny, enz;
-        e_node<T, GAIN>(G, sg, sel, n, iw, jw, kw, cidx, m, gcell, gs, hz - sHz[tid - bx], hy - hPy, hx - hPx,
+        e_node<T, GAIN>(G, sg, col, pl, sel, n, cidx, m, gcell, gs, hz - sHz[tid - bx], hy - hPy, hx - hPx,
                         hz - sHz[tid - 1], hy - sHy[tid - 1], hx - sHx[tid - bx], eCx, eCy, eCz, enx, eny, enz);
         G.F[sel ^ 1][0][cidx] = enx;
         G.F[sel ^ 1][1][cidx] = eny;
@@ -335,8 +338,12 @@ size_t step_tma_smem_bytes(int oy) {
   return TmaLayout<T>(oy).total;
 }
 
+#ifndef FDTD_TMA_MIN_BLOCKS
+#define FDTD_TMA_MIN_BLOCKS 1
+#endif
+
 template <typename T, bool GAIN>
-__global__ void __launch_bounds__(256) k_step_tma(const StepGrid<T>* __restrict__ grids,
+__global__ void __launch_bounds__(256, FDTD_TMA_MIN_BLOCKS) k_step_tma(const StepGrid<T>* __restrict__ grids,
                                                   const TmaGrid* __restrict__ maps, const int4* __restrict__ items,
                                                   int nitems, int offset) {
   constexpr int OX = kTmaOX;
@@ -409,6 +416,16 @@ __global__ void __launch_bounds__(256) k_step_tma(const StepGrid<T>* __restrict_
     const int i = x0 + tx, j = y0 + ty;
     const bool own = i < nx && j < ny;
     const int xo = tx + AX, yo = ty + 1;  // own node in the staged box
+    Column col;
+    make_column(G, own ? i : 0, own ? j : 0, col, true);
+    const long long pstride = (long long)px * ny;
+    const long long cbase = (long long)j * px + i;
+    // halo node of this thread, if any: -y row (ty == 0) or -x column (ty == 1, tx < OY)
+    const bool hrow = (ty == 0) && y0 > 0 && i < nx;
+    const bool hcolm = (ty == 1) && tx < OY && x0 > 0 && y0 + tx < ny;
+    Column hcol;
+    make_column(G, hrow ? i : (hcolm ? x0 - 1 : 0), hrow ? y0 - 1 : (hcolm ? y0 + tx : 0), hcol, false);
+    const int hxo = hrow ? xo : AX - 1, hyo = hrow ? 0 : tx + 1;
     T hPx = T(0), hPy = T(0);
     bool ok = true;
 
@@ -421,7 +438,8 @@ __global__ void __launch_bounds__(256) k_step_tma(const StepGrid<T>* __restrict_
       const T* Fn = reinterpret_cast<const T*>(stages + (size_t)((q + 1) % S) * lay.stage_bytes);
       const uint8_t* Mk = stages + (size_t)(q % S) * lay.stage_bytes + lay.field_bytes;
       const bool active = k >= z0;
-      const long long cidx = pidx3(i, j, k, px, ny);
+      const Plane pl = make_plane(G, k);
+      const long long cidx = cbase + (long long)k * pstride;
 
       // own node: material, gain state (issued before the H work)
       unsigned m = 0;
@@ -433,34 +451,26 @@ __global__ void __launch_bounds__(256) k_step_tma(const StepGrid<T>* __restrict_
         if (GAIN && gcell) load_gain(G, sel, cidx, gs);
       }
 
-      // H^{n+1/2} of plane k at a staged node (xx, yy) = node (x0 - AX + xx, y0 - 1 + yy)
-      auto h_at = [&](int xx, int yy, int ii, int jj, bool wr, T& hx, T& hy, T& hz) {
-        const T* Ex = Fk;
-        const T* Ey = Fk + PL;
-        const T* Ez = Fk + 2 * PL;
+      // H^{n+1/2} of plane k at staged node (xx, yy)
+      auto h_at = [&](const Column& c, int xx, int yy, bool wr, T& hx, T& hy, T& hz) {
         const int o = yy * BXT + xx;
-        const T ex = Ex[o], ey = Ey[o], ez = Ez[o];
-        h_node(G, sel, wr, ii, jj, k, Ez[o + BXT] - ez, Fn[PL + o] - ey, Fn[o] - ex, Ez[o + 1] - ez, Ey[o + 1] - ey,
-               Ex[o + BXT] - ex, Fk[3 * PL + o], Fk[4 * PL + o], Fk[5 * PL + o], hx, hy, hz);
+        const T ex = Fk[o], ey = Fk[PL + o], ez = Fk[2 * PL + o];
+        h_node(G, c, pl, sel, wr, Fk[2 * PL + o + BXT] - ez, Fn[PL + o] - ey, Fn[o] - ex, Fk[2 * PL + o + 1] - ez,
+               Fk[PL + o + 1] - ey, Fk[o + BXT] - ex, Fk[3 * PL + o], Fk[4 * PL + o], Fk[5 * PL + o], hx, hy, hz);
       };
 
       T hx = T(0), hy = T(0), hz = T(0);
-      if (ok && own) h_at(xo, yo, i, j, active, hx, hy, hz);
+      if (ok && own) h_at(col, xo, yo, active, hx, hy, hz);
       sHx[yo * HW + tx + 1] = hx;
       sHy[yo * HW + tx + 1] = hy;
       sHz[yo * HW + tx + 1] = hz;
-      if (ty == 0) {  // -y halo row: node (i, y0-1)
+      if (ty == 0 || (ty == 1 && tx < OY)) {
         T a = T(0), b = T(0), c = T(0);
-        if (ok && y0 > 0 && i < nx) h_at(xo, 0, i, y0 - 1, false, a, b, c);
-        sHx[tx + 1] = a;
-        sHy[tx + 1] = b;
-        sHz[tx + 1] = c;
-      } else if (ty == 1 && tx < OY) {  // -x halo column: node (x0-1, y0+tx)
-        T a = T(0), b = T(0), c = T(0);
-        if (ok && x0 > 0 && y0 + tx < ny) h_at(AX - 1, tx + 1, x0 - 1, y0 + tx, false, a, b, c);
-        sHx[(tx + 1) * HW] = a;
-        sHy[(tx + 1) * HW] = b;
-        sHz[(tx + 1) * HW] = c;
+        if (ok && (hrow || hcolm)) h_at(hcol, hxo, hyo, false, a, b, c);
+        const int slot = ty == 0 ? tx + 1 : (tx + 1) * HW;
+        sHx[slot] = a;
+        sHy[slot] = b;
+        sHz[slot] = c;
       }
       if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicOr(G.err, 2);
@@ -471,7 +481,7 @@ __global__ void __launch_bounds__(256) k_step_tma(const StepGrid<T>* __restrict_
         const int oh = yo * HW + tx + 1;
         const int oe = yo * BXT + xo;
         T enx, eny, enz;
-        e_node<T, GAIN>(G, sg, sel, n, i, j, k, cidx, m, gcell, gs, hz - sHz[oh - HW], hy - hPy, hx - hPx,
+        e_node<T, GAIN>(G, sg, col, pl, sel, n, cidx, m, gcell, gs, hz - sHz[oh - HW], hy - hPy, hx - hPx,
                         hz - sHz[oh - 1], hy - sHy[oh - 1], hx - sHx[oh - HW], Fk[oe], Fk[PL + oe], Fk[2 * PL + oe],
                         enx, eny, enz);
         G.F[sel ^ 1][0][cidx] = enx;
