@@ -339,6 +339,26 @@ int fdtd_result_flux(fdtd_server* s, uint64_t ticket, double* out);
 int fdtd_result_release(fdtd_server* s, uint64_t ticket);
 int fdtd_server_get_stats(fdtd_server* s, fdtd_server_stats* out);
 
+/* Field energy 1/2 eps0 dx^3 (sum eps_r E^2 + sum H~^2) in joules of
+ * caller-owned DEVICE arrays, computed without allocating any memory.
+ * The paper has no counterpart: this is for callers that cannot allocate
+ * device memory where they need the number (another framework owns the
+ * allocator, a real-time loop must not enter it, a tool inspects fields in
+ * place).  fields: six device pointers Ex, Ey, Ez, H~x, H~y, H~z, each
+ * [nz][ny][pitch] elements of the given precision with x fastest; mat: device
+ * material bytes in the same layout (eps[class] per E node, as in
+ * fdtd_set_eps_from_spheres); dx: cell size in metres; stream: cudaStream_t
+ * or NULL; out: HOST double.  The reduction scratch is a fixed file-scope
+ * device array holding 2048 partial sums: at most 134,217,728 cells (2048 x
+ * 65536); larger inputs return E_INVAL.  The call synchronizes `stream`.
+ * Every call shares that scratch and leaves the last call's contents there;
+ * calls that overlap on the GPU race, so serialize them.  The scratch's
+ * device address is looked up on the first call made on each device, so make
+ * that first call before capturing a stream into a CUDA graph. */
+int fdtd_field_energy_noalloc(const void* const fields[6], const uint8_t* mat, int32_t nx, int32_t ny, int32_t nz,
+                              int32_t pitch, int32_t precision, const double eps[3], double dx, void* stream,
+                              double* out);
+
 /* Checkpoint: write / read every state array (fields, CPML slabs, gain state,
  * step count, recorders) to / from a file.  load requires a grid created
  * with the same description. */
