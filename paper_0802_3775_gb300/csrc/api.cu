@@ -387,7 +387,7 @@ struct GridImpl final : GridBase {
     og.flux_v0[f] = v0;
     og.flux_v1[f] = v1;
     const long long faces = (long long)(u1 - u0) * (v1 - v0);
-    int parts = (int)((faces + 2047) / 2048);
+    int parts = (int)((faces + 1023) / 1024);
     og.flux_parts[f] = std::max(1, std::min(kMaxFluxParts, parts));
     return FDTD_OK;
   }
@@ -398,7 +398,7 @@ struct GridImpl final : GridBase {
   void plan_items() {
     items.clear();
     const bool periodic = desc.periodic[0] || desc.periodic[1] || desc.periodic[2];
-    use_tma = (kernel_kind == 2 || (kernel_kind == 0 && !periodic)) && !periodic && kTmaOX * by <= 256 &&
+    use_tma = (kernel_kind == 2 || (kernel_kind == 0 && !periodic)) && !periodic && (by == 4 || by == 8) &&
               tensor_map_encoder() != nullptr;
     const int ox = use_tma ? kTmaOX : bx - 1;
     const int oy = use_tma ? by : by - 1;
@@ -406,27 +406,14 @@ struct GridImpl final : GridBase {
     const int tiles = tnx * tny;
     int depth = zdepth;
     if (depth <= 0) {
-      // z-ranges chosen so that the items fill whole waves of resident blocks
+      // short z-ranges (about 10 planes) balance the slower absorbing-slab
+      // tiles across SMs; small grids go shorter so the items fill two waves
       int dev = 0, sms = 152;
       if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       cudaGetLastError();
       const int wave = sms * step_blocks_per_sm<T>(use_tma, sg.gain != 0, bx, by);
-      // fewest z-ranges whose items fill at least 85 % of the last wave
-      int best_chunks = 1;
-      double best = -1.0;
-      for (int chunks = 1; chunks <= 64; ++chunks) {
-        const int d = (desc.nz + chunks - 1) / chunks;
-        if (d < 8 && chunks > 1) break;
-        const int real_chunks = (desc.nz + d - 1) / d;
-        const double waves = (double)tiles * real_chunks / wave;
-        const double eff = waves / std::ceil(waves);
-        if (eff > best + 1e-9) {
-          best = eff;
-          best_chunks = chunks;
-        }
-        if (eff >= 0.85) break;
-      }
-      depth = (desc.nz + best_chunks - 1) / best_chunks;
+      depth = 10;
+      while (depth > 4 && (long long)tiles * ((desc.nz + depth - 1) / depth) < 2LL * wave) depth -= 2;
     }
     depth = std::min(depth, desc.nz);
     for (int z0 = 0; z0 < desc.nz; z0 += depth) {
@@ -463,6 +450,11 @@ struct GridImpl final : GridBase {
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(FDTD_E_CUDA, "tensor map (material) encode failed: %d", (int)r);
+    const cuuint32_t sbox[4] = {(cuuint32_t)kTmaOX, (cuuint32_t)by, 1, 6};
+    r = enc(&h.store, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+            (void*)d_F, fdim, fstr, sbox, one, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(FDTD_E_CUDA, "tensor map (store) encode failed: %d", (int)r);
     cudaError_t e = cudaMemcpyAsync(d_tma, &h, sizeof(h), cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return cuda_error(e, "upload tensor maps");
     return FDTD_OK;

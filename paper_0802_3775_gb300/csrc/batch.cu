@@ -55,7 +55,7 @@ struct BatchImpl final : BatchBase {
       g->kernel_kind = kernel_kind;
       g->bx = bx;
       g->by = by;
-      g->zdepth = zdepth > 0 ? zdepth : 1 << 15;  // default: whole z per item (many items across members)
+      g->zdepth = zdepth > 0 ? zdepth : 10;  // default: short z-ranges (balance across SMs)
       g->grid_blocks = 0;
       int r = g->finalized ? g->replan() : g->finalize();
       if (r != FDTD_OK) return r;

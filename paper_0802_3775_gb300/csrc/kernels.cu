@@ -313,62 +313,71 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(map), "r"(c0),
+      "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // Byte layout of the TMA kernel's shared memory (host and device agree).
-template <typename T>
+template <typename T, int OY>
 struct TmaLayout {
-  static constexpr int AX = 16 / (int)sizeof(T);       // x pad: one 16-byte unit each side
-  static constexpr int BXT = kTmaOX + 2 * AX;          // box width (elements)
-  size_t grid_off, sg_off, bar_off, stage_off, field_bytes, mat_bytes, stage_bytes, h_off, total;
-  __host__ __device__ explicit TmaLayout(int oy) {
-    const int byt = oy + 2;
-    grid_off = 0;
-    sg_off = align128(sizeof(StepGrid<T>));
-    bar_off = sg_off + align128(kMaxSrc * sizeof(double));
-    stage_off = bar_off + 128;
-    field_bytes = align128((size_t)6 * BXT * byt * sizeof(T));
-    mat_bytes = align128((size_t)kTmaOX * oy);
-    stage_bytes = field_bytes + mat_bytes;
-    h_off = stage_off + (size_t)kTmaStages * stage_bytes;
-    total = h_off + (size_t)3 * (oy + 1) * (kTmaOX + 1) * sizeof(T) + 128;  // + base alignment slack
-  }
+  static constexpr int AX = 16 / (int)sizeof(T);  // x pad: one 16-byte unit each side
+  static constexpr int BXT = kTmaOX + 2 * AX;     // staged box width
+  static constexpr int BYT = OY + 2;              // staged box height (rows y0-1 .. y0+OY)
+  static constexpr int PL = BXT * BYT;            // elements of one component plane in a stage
+  static constexpr int HW = kTmaOX + 1;           // row length of the H plane buffer
+  static constexpr int HPL = (OY + 1) * HW;
+  static constexpr int OPL = kTmaOX * OY;         // elements of one component of the output tile
+  static constexpr size_t sg_off = align128(sizeof(StepGrid<T>));
+  static constexpr size_t bar_off = sg_off + align128(kMaxSrc * sizeof(double));
+  static constexpr size_t stage_off = bar_off + 128;
+  static constexpr size_t field_bytes = align128((size_t)6 * PL * sizeof(T));
+  static constexpr size_t mat_bytes = align128((size_t)kTmaOX * OY);
+  static constexpr size_t stage_bytes = field_bytes + mat_bytes;
+  static constexpr size_t out_off = stage_off + (size_t)kTmaStages * stage_bytes;
+  static constexpr size_t h_off = out_off + align128((size_t)6 * OPL * sizeof(T));
+  static constexpr size_t total = h_off + (size_t)3 * HPL * sizeof(T) + 128;  // + base alignment slack
 };
 
 template <typename T>
 size_t step_tma_smem_bytes(int oy) {
-  return TmaLayout<T>(oy).total;
+  return oy == 4 ? TmaLayout<T, 4>::total : TmaLayout<T, 8>::total;
 }
 
+// Four resident blocks of 256 threads per SM (64 registers a thread): the
+// sweep of launch shapes on GB300 favoured occupancy over the extra registers.
 #ifndef FDTD_TMA_MIN_BLOCKS
-#define FDTD_TMA_MIN_BLOCKS 1
+#define FDTD_TMA_MIN_BLOCKS 4
 #endif
 
-template <typename T, bool GAIN>
-__global__ void __launch_bounds__(256, FDTD_TMA_MIN_BLOCKS) k_step_tma(const StepGrid<T>* __restrict__ grids,
-                                                  const TmaGrid* __restrict__ maps, const int4* __restrict__ items,
-                                                  int nitems, int offset) {
+template <typename T, bool GAIN, int OY>
+__global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
+    k_step_tma(const StepGrid<T>* __restrict__ grids, const TmaGrid* __restrict__ maps,
+               const int4* __restrict__ items, int nitems, int offset) {
+  using L = TmaLayout<T, OY>;
   constexpr int OX = kTmaOX;
   constexpr int S = kTmaStages;
-  constexpr int AX = TmaLayout<T>::AX;
-  constexpr int BXT = TmaLayout<T>::BXT;
+  constexpr int AX = L::AX, BXT = L::BXT, PL = L::PL, HW = L::HW, HPL = L::HPL, OPL = L::OPL;
+  constexpr unsigned TX_BYTES = (unsigned)(6 * PL * sizeof(T) + OX * OY);
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  // TMA destinations need 128-byte alignment: align the dynamic base explicitly
+  // TMA sources and destinations need 128-byte alignment: align the dynamic base explicitly
   unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-  const int OY = blockDim.y;
-  const int BYT = OY + 2;
-  const int PL = BYT * BXT;      // elements of one component plane in a stage
-  const int HW = OX + 1;         // row length of the H plane buffer
-  const int HPL = (OY + 1) * HW;
-  const TmaLayout<T> lay(OY);
-  StepGrid<T>& G = *reinterpret_cast<StepGrid<T>*>(smem + lay.grid_off);
-  double* sg = reinterpret_cast<double*>(smem + lay.sg_off);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + lay.bar_off);
-  unsigned char* stages = smem + lay.stage_off;
-  T* sHx = reinterpret_cast<T*>(smem + lay.h_off);
+  StepGrid<T>& G = *reinterpret_cast<StepGrid<T>*>(smem);
+  double* sg = reinterpret_cast<double*>(smem + L::sg_off);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::bar_off);
+  unsigned char* stages = smem + L::stage_off;
+  T* out = reinterpret_cast<T*>(smem + L::out_off);
+  T* sHx = reinterpret_cast<T*>(smem + L::h_off);
   T* sHy = sHx + HPL;
   T* sHz = sHy + HPL;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * OX + tx;
-  const unsigned tx_bytes = (unsigned)(6 * PL * sizeof(T) + OX * OY);
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
@@ -382,7 +391,7 @@ __global__ void __launch_bounds__(256, FDTD_TMA_MIN_BLOCKS) k_step_tma(const Ste
     const int4 item = items[it];
     __syncthreads();
     if (item.x != cur) {
-      load_record(grids + item.x, smem + lay.grid_off, tid, OX * OY);
+      load_record(grids + item.x, smem, tid, OX * OY);
       cur = item.x;
     }
     __syncthreads();
@@ -397,14 +406,15 @@ __global__ void __launch_bounds__(256, FDTD_TMA_MIN_BLOCKS) k_step_tma(const Ste
     const int sel = (int)(n & 1);
     const CUtensorMap* fmap = &maps[item.x].fields;
     const CUtensorMap* mmap = &maps[item.x].mat;
+    const CUtensorMap* smap = &maps[item.x].store;
     const unsigned q0 = ld;
 
     auto issue = [&](unsigned q, int plane) {
       const int s = (int)(q % S);
-      unsigned char* dst = stages + (size_t)s * lay.stage_bytes;
-      mbar_arrive_expect_tx(&full[s], tx_bytes);
+      unsigned char* dst = stages + (size_t)s * L::stage_bytes;
+      mbar_arrive_expect_tx(&full[s], TX_BYTES);
       tma_load_4d(dst, fmap, x0 - AX, y0 - 1, plane, sel * 6, &full[s]);
-      tma_load_3d(dst + lay.field_bytes, mmap, x0, y0, plane, &full[s]);
+      tma_load_3d(dst + L::field_bytes, mmap, x0, y0, plane, &full[s]);
     };
     if (tid == 0) {
       fence_proxy_async_smem();
@@ -415,17 +425,16 @@ __global__ void __launch_bounds__(256, FDTD_TMA_MIN_BLOCKS) k_step_tma(const Ste
 
     const int i = x0 + tx, j = y0 + ty;
     const bool own = i < nx && j < ny;
-    const int xo = tx + AX, yo = ty + 1;  // own node in the staged box
+    constexpr int xo = AX;      // own node: staged column tx + AX, row ty + 1
+    const int oe = (ty + 1) * BXT + tx + xo;
+    const int oh = (ty + 1) * HW + tx + 1;
     Column col;
     make_column(G, own ? i : 0, own ? j : 0, col, true);
-    const long long pstride = (long long)px * ny;
     const long long cbase = (long long)j * px + i;
+    const long long pstride = (long long)px * ny;
     // halo node of this thread, if any: -y row (ty == 0) or -x column (ty == 1, tx < OY)
     const bool hrow = (ty == 0) && y0 > 0 && i < nx;
     const bool hcolm = (ty == 1) && tx < OY && x0 > 0 && y0 + tx < ny;
-    Column hcol;
-    make_column(G, hrow ? i : (hcolm ? x0 - 1 : 0), hrow ? y0 - 1 : (hcolm ? y0 + tx : 0), hcol, false);
-    const int hxo = hrow ? xo : AX - 1, hyo = hrow ? 0 : tx + 1;
     T hPx = T(0), hPy = T(0);
     bool ok = true;
 
@@ -434,9 +443,9 @@ __global__ void __launch_bounds__(256, FDTD_TMA_MIN_BLOCKS) k_step_tma(const Ste
       const unsigned q = q0 + p;
       if (p == 0) ok = ok && mbar_wait(&full[q % S], (q / S) & 1);
       ok = ok && mbar_wait(&full[(q + 1) % S], ((q + 1) / S) & 1);
-      const T* Fk = reinterpret_cast<const T*>(stages + (size_t)(q % S) * lay.stage_bytes);
-      const T* Fn = reinterpret_cast<const T*>(stages + (size_t)((q + 1) % S) * lay.stage_bytes);
-      const uint8_t* Mk = stages + (size_t)(q % S) * lay.stage_bytes + lay.field_bytes;
+      const T* Fk = reinterpret_cast<const T*>(stages + (size_t)(q % S) * L::stage_bytes);
+      const T* Fn = reinterpret_cast<const T*>(stages + (size_t)((q + 1) % S) * L::stage_bytes);
+      const uint8_t* Mk = stages + (size_t)(q % S) * L::stage_bytes + L::field_bytes;
       const bool active = k >= z0;
       const Plane pl = make_plane(G, k);
       const long long cidx = cbase + (long long)k * pstride;
@@ -446,62 +455,79 @@ __global__ void __launch_bounds__(256, FDTD_TMA_MIN_BLOCKS) k_step_tma(const Ste
       bool gcell = false;
       GainState<T> gs{};
       if (ok && own && active) {
-        m = Mk[ty * OX + tx];
+        m = Mk[tid];
         gcell = GAIN && G.gain && ((m >> 6) & 1);
         if (GAIN && gcell) load_gain(G, sel, cidx, gs);
       }
 
-      // H^{n+1/2} of plane k at staged node (xx, yy)
-      auto h_at = [&](const Column& c, int xx, int yy, bool wr, T& hx, T& hy, T& hz) {
-        const int o = yy * BXT + xx;
+      // H^{n+1/2} of plane k at the staged node with offset o
+      auto h_at = [&](const Column& c, int o, bool wr, T& hx, T& hy, T& hz) {
         const T ex = Fk[o], ey = Fk[PL + o], ez = Fk[2 * PL + o];
         h_node(G, c, pl, sel, wr, Fk[2 * PL + o + BXT] - ez, Fn[PL + o] - ey, Fn[o] - ex, Fk[2 * PL + o + 1] - ez,
                Fk[PL + o + 1] - ey, Fk[o + BXT] - ex, Fk[3 * PL + o], Fk[4 * PL + o], Fk[5 * PL + o], hx, hy, hz);
       };
 
       T hx = T(0), hy = T(0), hz = T(0);
-      if (ok && own) h_at(col, xo, yo, active, hx, hy, hz);
-      sHx[yo * HW + tx + 1] = hx;
-      sHy[yo * HW + tx + 1] = hy;
-      sHz[yo * HW + tx + 1] = hz;
+      if (ok && own) h_at(col, oe, active, hx, hy, hz);
+      sHx[oh] = hx;
+      sHy[oh] = hy;
+      sHz[oh] = hz;
       if (ty == 0 || (ty == 1 && tx < OY)) {
         T a = T(0), b = T(0), c = T(0);
-        if (ok && (hrow || hcolm)) h_at(hcol, hxo, hyo, false, a, b, c);
+        if (ok && (hrow || hcolm)) {
+          Column hc;
+          if (hrow) make_column(G, i, y0 - 1, hc, false);
+          else make_column(G, x0 - 1, y0 + tx, hc, false);
+          h_at(hc, hrow ? tx + xo : (tx + 1) * BXT + xo - 1, false, a, b, c);
+        }
         const int slot = ty == 0 ? tx + 1 : (tx + 1) * HW;
         sHx[slot] = a;
         sHy[slot] = b;
         sHz[slot] = c;
       }
+      // the output tile buffer must have been read by the previous plane's store
+      if (tid == 0) bulk_wait_read0();
       if (__syncthreads_or(!ok)) {
-        if (tid == 0) atomicOr(G.err, 2);
+        if (tid == 0) {
+          atomicOr(G.err, 2);
+          bulk_wait0();
+        }
         return;
       }
 
-      if (own && active) {
-        const int oh = yo * HW + tx + 1;
-        const int oe = yo * BXT + xo;
-        T enx, eny, enz;
-        e_node<T, GAIN>(G, sg, col, pl, sel, n, cidx, m, gcell, gs, hz - sHz[oh - HW], hy - hPy, hx - hPx,
-                        hz - sHz[oh - 1], hy - sHy[oh - 1], hx - sHx[oh - HW], Fk[oe], Fk[PL + oe], Fk[2 * PL + oe],
-                        enx, eny, enz);
-        G.F[sel ^ 1][0][cidx] = enx;
-        G.F[sel ^ 1][1][cidx] = eny;
-        G.F[sel ^ 1][2][cidx] = enz;
-        G.F[sel ^ 1][3][cidx] = hx;
-        G.F[sel ^ 1][4][cidx] = hy;
-        G.F[sel ^ 1][5][cidx] = hz;
+      if (active) {
+        T enx = T(0), eny = T(0), enz = T(0);
+        if (own)
+          e_node<T, GAIN>(G, sg, col, pl, sel, n, cidx, m, gcell, gs, hz - sHz[oh - HW], hy - hPy, hx - hPx,
+                          hz - sHz[oh - 1], hy - sHy[oh - 1], hx - sHx[oh - HW], Fk[oe], Fk[PL + oe],
+                          Fk[2 * PL + oe], enx, eny, enz);
+        out[tid] = enx;
+        out[OPL + tid] = eny;
+        out[2 * OPL + tid] = enz;
+        out[3 * OPL + tid] = hx;
+        out[4 * OPL + tid] = hy;
+        out[5 * OPL + tid] = hz;
+        fence_proxy_async_smem();
       }
       hPx = hx;
       hPy = hy;
       __syncthreads();
-      // stage of plane p is free: refill it with plane p + S
-      if (tid == 0 && p + S < NP) {
-        fence_proxy_async_smem();
-        issue(q + S, kstart + p + S);
+      if (tid == 0) {
+        if (active) {
+          // E^{n+1} and H~^{n+1/2} of the owned tile (clipped at the grid edge) to set (n+1)&1
+          tma_store_4d(smap, out, x0, y0, k, (sel ^ 1) * 6);
+          bulk_commit();
+        }
+        // stage of plane p is free: refill it with plane p + S
+        if (p + S < NP) {
+          fence_proxy_async_smem();
+          issue(q + S, kstart + p + S);
+        }
       }
     }
     ld = q0 + (unsigned)NP;
   }
+  if (tid == 0) bulk_wait0();
 }
 
 template <typename T>
@@ -510,13 +536,11 @@ int step_blocks_per_sm(bool tma, bool gain, int bx, int by) {
   cudaError_t e;
   if (tma) {
     const size_t smem = step_tma_smem_bytes<T>(by);
-    if (gain) {
-      cudaFuncSetAttribute(k_step_tma<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_tma<T, true>, kTmaOX * by, smem);
-    } else {
-      cudaFuncSetAttribute(k_step_tma<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_tma<T, false>, kTmaOX * by, smem);
-    }
+    const void* f = nullptr;
+    if (by == 4) f = gain ? (const void*)k_step_tma<T, true, 4> : (const void*)k_step_tma<T, false, 4>;
+    else f = gain ? (const void*)k_step_tma<T, true, 8> : (const void*)k_step_tma<T, false, 8>;
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kTmaOX * by, smem);
   } else {
     const size_t smem = step_smem_bytes<T>(bx, by);
     if (gain) {
@@ -534,24 +558,28 @@ int step_blocks_per_sm(bool tma, bool gain, int bx, int by) {
   return nb > 0 ? nb : 1;
 }
 
+template <typename T, bool GAIN, int OY>
+static cudaError_t launch_tma_variant(const StepGrid<T>* grids, const TmaGrid* maps, const int4* items, int nitems,
+                                      int offset, int blocks, cudaStream_t st) {
+  const size_t smem = TmaLayout<T, OY>::total;
+  cudaError_t e = cudaFuncSetAttribute(k_step_tma<T, GAIN, OY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_step_tma<T, GAIN, OY><<<blocks, dim3(kTmaOX, OY), smem, st>>>(grids, maps, items, nitems, offset);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_step_tma(const StepGrid<T>* grids, const TmaGrid* maps, const int4* items, int nitems, int offset,
                             int oy, bool gain, int grid_blocks, cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
-  const size_t smem = step_tma_smem_bytes<T>(oy);
   const int blocks = (grid_blocks > 0 && grid_blocks < nitems) ? grid_blocks : nitems;
-  dim3 blk(kTmaOX, oy);
-  cudaError_t e;
-  if (gain) {
-    e = cudaFuncSetAttribute(k_step_tma<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_step_tma<T, true><<<blocks, blk, smem, st>>>(grids, maps, items, nitems, offset);
-  } else {
-    e = cudaFuncSetAttribute(k_step_tma<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_step_tma<T, false><<<blocks, blk, smem, st>>>(grids, maps, items, nitems, offset);
-  }
-  return cudaGetLastError();
+  if (oy == 4)
+    return gain ? launch_tma_variant<T, true, 4>(grids, maps, items, nitems, offset, blocks, st)
+                : launch_tma_variant<T, false, 4>(grids, maps, items, nitems, offset, blocks, st);
+  if (oy == 8)
+    return gain ? launch_tma_variant<T, true, 8>(grids, maps, items, nitems, offset, blocks, st)
+                : launch_tma_variant<T, false, 8>(grids, maps, items, nitems, offset, blocks, st);
+  return cudaErrorInvalidValue;
 }
 
 // =====================================================================
@@ -606,7 +634,9 @@ __global__ void __launch_bounds__(256) k_observe(const ObsGrid<T>* __restrict__ 
   const T* H2b = G.F[sel ^ 1][3 + d2];
   double acc = 0.0;
   for (long long q = beg + threadIdx.x; q < end; q += blockDim.x) {
-    const int u = u0 + (int)(q / nv), v = v0 + (int)(q % nv);
+    // consecutive threads take consecutive x (the fastest memory axis) when x is transverse
+    const bool ufast = (d1 == 0);
+    const int u = u0 + (int)(ufast ? q % nu : q / nv), v = v0 + (int)(ufast ? q / nu : q % nv);
     int c[3];
     auto at = [&](int pp, int uu, int vv) {
       c[d] = pp;
