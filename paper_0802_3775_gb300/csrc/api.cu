@@ -392,6 +392,17 @@ struct GridImpl final : GridBase {
     return FDTD_OK;
   }
 
+  // Relative cost of a work item: planes (plus the recomputed plane below)
+  // times a factor for each absorbing slab the tile's columns or planes cross.
+  double item_cost(const int4& it, int ox, int oy) const {
+    const int x0 = it.y, y0 = it.z, z0 = it.w & 0xffff, z1 = (it.w >> 16) & 0xffff;
+    auto crosses = [](int a0, int a1, int n, int L0, int L1) { return (L0 > 0 && a0 < L0) || (L1 > 0 && a1 > n - L1); };
+    const bool sx = crosses(x0 - 1, x0 + ox, desc.nx, desc.npml[0], desc.npml[1]);
+    const bool sy = crosses(y0 - 1, y0 + oy, desc.ny, desc.npml[2], desc.npml[3]);
+    const bool sz = crosses(z0 - 1, z1, desc.nz, desc.npml[4], desc.npml[5]);
+    return (double)(z1 - z0 + 1) * (1.0 + 0.45 * sx + 0.25 * sy + 0.1 * sz + 0.3 * ((int)sx + sy + sz >= 2));
+  }
+
   // Work items of one time step.  TMA kernel: tiles of 32 x by owned columns;
   // plain kernel: tiles of (bx-1) x (by-1) owned columns.  Each tile marches
   // z-ranges of `zdepth` planes (0: chosen so the items fill whole waves).
@@ -406,21 +417,33 @@ struct GridImpl final : GridBase {
     const int tiles = tnx * tny;
     int depth = zdepth;
     if (depth <= 0) {
-      // short z-ranges (about 10 planes) balance the slower absorbing-slab
-      // tiles across SMs; small grids go shorter so the items fill two waves
+      // short z-ranges (16 planes) with the slab-heavy items issued first
+      // balance the load across SMs; small grids go shorter so the items fill
+      // two waves
       int dev = 0, sms = 152;
       if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       cudaGetLastError();
       const int wave = sms * step_blocks_per_sm<T>(use_tma, sg.gain != 0, bx, by);
-      depth = 10;
+      depth = 16;
       while (depth > 4 && (long long)tiles * ((desc.nz + depth - 1) / depth) < 2LL * wave) depth -= 2;
     }
     depth = std::min(depth, desc.nz);
+    // longest items first: tiles that cross absorbing slabs (and the wider
+    // halo of the plain kernel) cost more per plane, so they are issued before
+    // the interior tiles, which then fill the tail of the launch
+    std::vector<std::pair<double, int4>> work;
     for (int z0 = 0; z0 < desc.nz; z0 += depth) {
       const int z1 = std::min(desc.nz, z0 + depth);
       for (int ty = 0; ty < tny; ++ty)
-        for (int tx = 0; tx < tnx; ++tx) items.push_back(make_int4(0, tx * ox, ty * oy, z0 | (z1 << 16)));
+        for (int tx = 0; tx < tnx; ++tx) {
+          const int4 it = make_int4(0, tx * ox, ty * oy, z0 | (z1 << 16));
+          work.push_back({item_cost(it, ox, oy), it});
+        }
     }
+    std::stable_sort(work.begin(), work.end(), [](const std::pair<double, int4>& a, const std::pair<double, int4>& b) {
+      return a.first > b.first;
+    });
+    for (auto& w : work) items.push_back(w.second);
     oitems.clear();
     if (og.nprobe) oitems.push_back(make_int4(0, -1, 0, 1));
     for (int f = 0; f < og.nflux; ++f)

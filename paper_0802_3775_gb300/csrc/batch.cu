@@ -55,7 +55,7 @@ struct BatchImpl final : BatchBase {
       g->kernel_kind = kernel_kind;
       g->bx = bx;
       g->by = by;
-      g->zdepth = zdepth > 0 ? zdepth : 10;  // default: short z-ranges (balance across SMs)
+      g->zdepth = zdepth > 0 ? zdepth : 16;  // default: short z-ranges (balance across SMs)
       g->grid_blocks = 0;
       int r = g->finalized ? g->replan() : g->finalize();
       if (r != FDTD_OK) return r;
@@ -74,6 +74,7 @@ struct BatchImpl final : BatchBase {
     std::vector<ObsGrid<T>> hog(ng);
     items.clear();
     oitems.clear();
+    std::vector<std::pair<double, int4>> ranked;
     for (int q = 0; q < ng; ++q) {
       GridBase* g = grids[q];
       std::memcpy(&hsg[q], g->step_record(), sizeof(StepGrid<T>));
@@ -82,15 +83,21 @@ struct BatchImpl final : BatchBase {
       hsg[q].step_end = hog[q].step_end = g->step_limit;
       std::vector<int4> si, oi;
       g->work_items(si, oi);
-      for (auto it : si) {
+      // members' lists are ordered longest first; merge them by position so
+      // the batch also issues its slab-heavy items first
+      for (size_t r = 0; r < si.size(); ++r) {
+        int4 it = si[r];
         it.x = q;
-        items.push_back(it);
+        ranked.push_back({(double)r / (double)si.size(), it});
       }
       for (auto it : oi) {
         it.x = q;
         oitems.push_back(it);
       }
     }
+    std::stable_sort(ranked.begin(), ranked.end(),
+                     [](const std::pair<double, int4>& a, const std::pair<double, int4>& b) { return a.first < b.first; });
+    for (auto& w : ranked) items.push_back(w.second);
     mem.release_all();
     d_sg = (StepGrid<T>*)mem.get(sizeof(StepGrid<T>) * ng);
     d_og = (ObsGrid<T>*)mem.get(sizeof(ObsGrid<T>) * ng);

@@ -83,6 +83,22 @@ __device__ __forceinline__ T pml_term(T D, const T* const* pr, int pos, const T*
   return fmad(pr[0][pos], D, p);
 }
 
+// CPML memory of one slab axis of a node, fetched ahead of its update:
+// H-side slots 0, 1 (set sel) and E-side slots 0, 1.  axis < 0: nothing fetched.
+template <typename T>
+struct PsiPre {
+  int axis;
+  T h0, h1, e0, e1;
+};
+
+// pml_term with the old psi value already in hand.
+template <typename T>
+__device__ __forceinline__ T pml_term_v(T D, const T* const* pr, int pos, T psi_old, T* psi_out, int pi) {
+  const T p = fmad(pr[1][pos], psi_old, pr[2][pos] * D);
+  if (psi_out) psi_out[pi] = p;
+  return fmad(pr[0][pos], D, p);
+}
+
 // Slab coordinate of node index q on an axis of length n with slabs L0, L1 (-1 outside).
 __device__ __forceinline__ int slab_index(int q, int n, int L0, int L1) {
   if (q < L0) return q;
@@ -168,21 +184,43 @@ __device__ __forceinline__ Plane make_plane(const StepGrid<T>& G, int k) {
 template <typename T>
 __device__ __forceinline__ void h_node(const StepGrid<T>& G, const Column& c, const Plane& p, int sel, bool wr,
                                        T dyEz, T dzEy, T dzEx, T dxEz, T dxEy, T dyEx, T hOx, T hOy, T hOz, T& hx,
-                                       T& hy, T& hz) {
+                                       T& hy, T& hz, const PsiPre<T>* pre = nullptr) {
+  const int pa = pre ? pre->axis : -1;
   if (c.sx >= 0) {
     const int pi = p.px_plane + c.px0;
-    dxEz = pml_term(dxEz, G.prof[0][1], c.i, G.psiH[sel][0][0], wr ? G.psiH[sel ^ 1][0][0] : (T*)nullptr, pi);
-    dxEy = pml_term(dxEy, G.prof[0][1], c.i, G.psiH[sel][0][1], wr ? G.psiH[sel ^ 1][0][1] : (T*)nullptr, pi);
+    T* o0 = wr ? G.psiH[sel ^ 1][0][0] : (T*)nullptr;
+    T* o1 = wr ? G.psiH[sel ^ 1][0][1] : (T*)nullptr;
+    if (pa == 0) {
+      dxEz = pml_term_v(dxEz, G.prof[0][1], c.i, pre->h0, o0, pi);
+      dxEy = pml_term_v(dxEy, G.prof[0][1], c.i, pre->h1, o1, pi);
+    } else {
+      dxEz = pml_term(dxEz, G.prof[0][1], c.i, G.psiH[sel][0][0], o0, pi);
+      dxEy = pml_term(dxEy, G.prof[0][1], c.i, G.psiH[sel][0][1], o1, pi);
+    }
   }
   if (c.sy >= 0) {
     const int pi = p.py_plane + c.py0;
-    dyEx = pml_term(dyEx, G.prof[1][1], c.j, G.psiH[sel][1][0], wr ? G.psiH[sel ^ 1][1][0] : (T*)nullptr, pi);
-    dyEz = pml_term(dyEz, G.prof[1][1], c.j, G.psiH[sel][1][1], wr ? G.psiH[sel ^ 1][1][1] : (T*)nullptr, pi);
+    T* o0 = wr ? G.psiH[sel ^ 1][1][0] : (T*)nullptr;
+    T* o1 = wr ? G.psiH[sel ^ 1][1][1] : (T*)nullptr;
+    if (pa == 1) {
+      dyEx = pml_term_v(dyEx, G.prof[1][1], c.j, pre->h0, o0, pi);
+      dyEz = pml_term_v(dyEz, G.prof[1][1], c.j, pre->h1, o1, pi);
+    } else {
+      dyEx = pml_term(dyEx, G.prof[1][1], c.j, G.psiH[sel][1][0], o0, pi);
+      dyEz = pml_term(dyEz, G.prof[1][1], c.j, G.psiH[sel][1][1], o1, pi);
+    }
   }
   if (p.sz >= 0) {
     const int pi = p.pz_plane + c.pz0;
-    dzEy = pml_term(dzEy, G.prof[2][1], p.k, G.psiH[sel][2][0], wr ? G.psiH[sel ^ 1][2][0] : (T*)nullptr, pi);
-    dzEx = pml_term(dzEx, G.prof[2][1], p.k, G.psiH[sel][2][1], wr ? G.psiH[sel ^ 1][2][1] : (T*)nullptr, pi);
+    T* o0 = wr ? G.psiH[sel ^ 1][2][0] : (T*)nullptr;
+    T* o1 = wr ? G.psiH[sel ^ 1][2][1] : (T*)nullptr;
+    if (pa == 2) {
+      dzEy = pml_term_v(dzEy, G.prof[2][1], p.k, pre->h0, o0, pi);
+      dzEx = pml_term_v(dzEx, G.prof[2][1], p.k, pre->h1, o1, pi);
+    } else {
+      dzEy = pml_term(dzEy, G.prof[2][1], p.k, G.psiH[sel][2][0], o0, pi);
+      dzEx = pml_term(dzEx, G.prof[2][1], p.k, G.psiH[sel][2][1], o1, pi);
+    }
   }
   const T cH = G.cH;
   hx = fmad(-cH, dyEz - dzEy, hOx);
@@ -270,21 +308,37 @@ template <typename T, bool GAIN>
 __device__ __forceinline__ void e_node(const StepGrid<T>& G, const double* sg, const Column& c, const Plane& p,
                                        int sel, long long n, long long cidx, unsigned m, bool gcell,
                                        const GainState<T>& gs, T dyHz, T dzHy, T dzHx, T dxHz, T dxHy, T dyHx, T eCx,
-                                       T eCy, T eCz, T& enx, T& eny, T& enz) {
+                                       T eCy, T eCz, T& enx, T& eny, T& enz, const PsiPre<T>* pre = nullptr) {
+  const int pa = pre ? pre->axis : -1;
   if (c.sx >= 0) {
     const int pi = p.px_plane + c.px0;
-    dxHz = pml_term(dxHz, G.prof[0][0], c.i, G.psiE[0][0], G.psiE[0][0], pi);
-    dxHy = pml_term(dxHy, G.prof[0][0], c.i, G.psiE[0][1], G.psiE[0][1], pi);
+    if (pa == 0) {
+      dxHz = pml_term_v(dxHz, G.prof[0][0], c.i, pre->e0, G.psiE[0][0], pi);
+      dxHy = pml_term_v(dxHy, G.prof[0][0], c.i, pre->e1, G.psiE[0][1], pi);
+    } else {
+      dxHz = pml_term(dxHz, G.prof[0][0], c.i, G.psiE[0][0], G.psiE[0][0], pi);
+      dxHy = pml_term(dxHy, G.prof[0][0], c.i, G.psiE[0][1], G.psiE[0][1], pi);
+    }
   }
   if (c.sy >= 0) {
     const int pi = p.py_plane + c.py0;
-    dyHx = pml_term(dyHx, G.prof[1][0], c.j, G.psiE[1][0], G.psiE[1][0], pi);
-    dyHz = pml_term(dyHz, G.prof[1][0], c.j, G.psiE[1][1], G.psiE[1][1], pi);
+    if (pa == 1) {
+      dyHx = pml_term_v(dyHx, G.prof[1][0], c.j, pre->e0, G.psiE[1][0], pi);
+      dyHz = pml_term_v(dyHz, G.prof[1][0], c.j, pre->e1, G.psiE[1][1], pi);
+    } else {
+      dyHx = pml_term(dyHx, G.prof[1][0], c.j, G.psiE[1][0], G.psiE[1][0], pi);
+      dyHz = pml_term(dyHz, G.prof[1][0], c.j, G.psiE[1][1], G.psiE[1][1], pi);
+    }
   }
   if (p.sz >= 0) {
     const int pi = p.pz_plane + c.pz0;
-    dzHy = pml_term(dzHy, G.prof[2][0], p.k, G.psiE[2][0], G.psiE[2][0], pi);
-    dzHx = pml_term(dzHx, G.prof[2][0], p.k, G.psiE[2][1], G.psiE[2][1], pi);
+    if (pa == 2) {
+      dzHy = pml_term_v(dzHy, G.prof[2][0], p.k, pre->e0, G.psiE[2][0], pi);
+      dzHx = pml_term_v(dzHx, G.prof[2][0], p.k, pre->e1, G.psiE[2][1], pi);
+    } else {
+      dzHy = pml_term(dzHy, G.prof[2][0], p.k, G.psiE[2][0], G.psiE[2][0], pi);
+      dzHx = pml_term(dzHx, G.prof[2][0], p.k, G.psiE[2][1], G.psiE[2][1], pi);
+    }
   }
   const T curlx = dyHz - dzHy;
   const T curly = dzHx - dxHz;

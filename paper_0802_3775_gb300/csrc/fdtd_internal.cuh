@@ -15,7 +15,10 @@ constexpr int kMaxProbes = 64;
 constexpr int kMaxFlux = 16;
 constexpr int kMaxFluxParts = 64;
 constexpr int kEnergyBlocks = 256;
-constexpr int kTmaStages = 4;     // planes resident or in flight per block (TMA step kernel)
+#ifndef FDTD_TMA_STAGES
+#define FDTD_TMA_STAGES 3
+#endif
+constexpr int kTmaStages = FDTD_TMA_STAGES;  // planes resident or in flight per block (TMA step kernel)
 constexpr int kTmaOX = 32;        // owned tile width of the TMA step kernel
 
 // Physical constants (CODATA; mu0 of the 2019 SI, hbar exact).

@@ -320,6 +320,19 @@ __device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void*
       : "memory");
 }
 
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc) {
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
@@ -337,9 +350,13 @@ struct TmaLayout {
   static constexpr size_t sg_off = align128(sizeof(StepGrid<T>));
   static constexpr size_t bar_off = sg_off + align128(kMaxSrc * sizeof(double));
   static constexpr size_t stage_off = bar_off + 128;
+  static constexpr int NT = kTmaOX * OY;          // threads = owned nodes of a tile plane
+  static constexpr int NH = kTmaOX + OY;           // halo nodes (-y row, -x column)
   static constexpr size_t field_bytes = align128((size_t)6 * PL * sizeof(T));
   static constexpr size_t mat_bytes = align128((size_t)kTmaOX * OY);
-  static constexpr size_t stage_bytes = field_bytes + mat_bytes;
+  // CPML memory fetched ahead per thread: 4 slots per owned node, 2 per halo node
+  static constexpr size_t psi_bytes = align128((size_t)(4 * NT + 2 * NH) * sizeof(T));
+  static constexpr size_t stage_bytes = field_bytes + mat_bytes + psi_bytes;
   static constexpr size_t out_off = stage_off + (size_t)kTmaStages * stage_bytes;
   static constexpr size_t h_off = out_off + align128((size_t)6 * OPL * sizeof(T));
   static constexpr size_t total = h_off + (size_t)3 * HPL * sizeof(T) + 128;  // + base alignment slack
@@ -435,6 +452,51 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
     // halo node of this thread, if any: -y row (ty == 0) or -x column (ty == 1, tx < OY)
     const bool hrow = (ty == 0) && y0 > 0 && i < nx;
     const bool hcolm = (ty == 1) && tx < OY && x0 > 0 && y0 + tx < ny;
+    const int hid = ty == 0 ? tx : OX + tx;
+    const int hi = hrow ? i : x0 - 1, hj = hrow ? y0 - 1 : y0 + tx;
+
+    // slab axis whose CPML memory is fetched ahead for a node: z for the planes
+    // of a z slab, else x or y for the columns of an x or y slab
+    const int col_axis = col.sx >= 0 ? 0 : (col.sy >= 0 ? 1 : -1);
+    const int zs_lo = G.Sd[2] ? G.L[4] : 0, zs_hi = G.Sd[2] ? G.nz - G.L[5] : G.nz;
+    auto plane_slab = [&](int plane) { return (plane < zs_lo || plane >= zs_hi) ? slab_index(plane, G.nz, G.L[4], G.L[5]) : -1; };
+    auto psi_index = [&](const Column& c, int a, int plane, int sz) {
+      if (a == 2) return sz * ny * nx + c.pz0;
+      if (a == 0) return plane * ny * G.Sd[0] + c.px0;
+      return plane * G.Sd[1] * nx + c.py0;
+    };
+    // fetch this thread's CPML memory of `plane` into the stage slots (one commit group per plane)
+    auto issue_psi = [&](int plane, int stage) {
+      T* slots = reinterpret_cast<T*>(stages + (size_t)stage * L::stage_bytes + L::field_bytes + L::mat_bytes);
+      const int sz = plane_slab(plane);
+      if (plane < z1 && (sz >= 0 || col_axis >= 0 || hrow || hcolm)) {
+        if (own) {
+          const int a = sz >= 0 ? 2 : col_axis;
+          if (a >= 0) {
+            const int pi = psi_index(col, a, plane, sz);
+            cp_async_elem(slots + tid, G.psiH[sel][a][0] + pi);
+            cp_async_elem(slots + L::NT + tid, G.psiH[sel][a][1] + pi);
+            if (plane >= z0) {  // E-side memory of the planes this tile updates
+              cp_async_elem(slots + 2 * L::NT + tid, G.psiE[a][0] + pi);
+              cp_async_elem(slots + 3 * L::NT + tid, G.psiE[a][1] + pi);
+            }
+          }
+        }
+        if (hrow || hcolm) {
+          Column hc;
+          make_column(G, hi, hj, hc, false);
+          const int a = sz >= 0 ? 2 : (hc.sx >= 0 ? 0 : (hc.sy >= 0 ? 1 : -1));
+          if (a >= 0) {
+            const int pi = psi_index(hc, a, plane, sz);
+            cp_async_elem(slots + 4 * L::NT + hid, G.psiH[sel][a][0] + pi);
+            cp_async_elem(slots + 4 * L::NT + L::NH + hid, G.psiH[sel][a][1] + pi);
+          }
+        }
+      }
+      cp_async_commit();
+    };
+    for (int p = 0; p < S; ++p) issue_psi(kstart + p, (int)((q0 + p) % S));
+
     T hPx = T(0), hPy = T(0);
     bool ok = true;
 
@@ -443,9 +505,12 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
       const unsigned q = q0 + p;
       if (p == 0) ok = ok && mbar_wait(&full[q % S], (q / S) & 1);
       ok = ok && mbar_wait(&full[(q + 1) % S], ((q + 1) / S) & 1);
-      const T* Fk = reinterpret_cast<const T*>(stages + (size_t)(q % S) * L::stage_bytes);
+      cp_async_wait<S - 1>();  // this thread's CPML memory of plane p
+      const unsigned char* stg = stages + (size_t)(q % S) * L::stage_bytes;
+      const T* Fk = reinterpret_cast<const T*>(stg);
       const T* Fn = reinterpret_cast<const T*>(stages + (size_t)((q + 1) % S) * L::stage_bytes);
-      const uint8_t* Mk = stages + (size_t)(q % S) * L::stage_bytes + L::field_bytes;
+      const uint8_t* Mk = stg + L::field_bytes;
+      const T* slots = reinterpret_cast<const T*>(stg + L::field_bytes + L::mat_bytes);
       const bool active = k >= z0;
       const Plane pl = make_plane(G, k);
       const long long cidx = cbase + (long long)k * pstride;
@@ -459,16 +524,27 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
         gcell = GAIN && G.gain && ((m >> 6) & 1);
         if (GAIN && gcell) load_gain(G, sel, cidx, gs);
       }
+      PsiPre<T> pre;
+      pre.axis = own ? (pl.sz >= 0 ? 2 : col_axis) : -1;
+      if (pre.axis >= 0) {
+        pre.h0 = slots[tid];
+        pre.h1 = slots[L::NT + tid];
+        pre.e0 = slots[2 * L::NT + tid];
+        pre.e1 = slots[3 * L::NT + tid];
+      } else {
+        pre.h0 = pre.h1 = pre.e0 = pre.e1 = T(0);
+      }
 
       // H^{n+1/2} of plane k at the staged node with offset o
-      auto h_at = [&](const Column& c, int o, bool wr, T& hx, T& hy, T& hz) {
+      auto h_at = [&](const Column& c, int o, bool wr, T& hx, T& hy, T& hz, const PsiPre<T>* pp) {
         const T ex = Fk[o], ey = Fk[PL + o], ez = Fk[2 * PL + o];
         h_node(G, c, pl, sel, wr, Fk[2 * PL + o + BXT] - ez, Fn[PL + o] - ey, Fn[o] - ex, Fk[2 * PL + o + 1] - ez,
-               Fk[PL + o + 1] - ey, Fk[o + BXT] - ex, Fk[3 * PL + o], Fk[4 * PL + o], Fk[5 * PL + o], hx, hy, hz);
+               Fk[PL + o + 1] - ey, Fk[o + BXT] - ex, Fk[3 * PL + o], Fk[4 * PL + o], Fk[5 * PL + o], hx, hy, hz,
+               pp);
       };
 
       T hx = T(0), hy = T(0), hz = T(0);
-      if (ok && own) h_at(col, oe, active, hx, hy, hz);
+      if (ok && own) h_at(col, oe, active, hx, hy, hz, &pre);
       sHx[oh] = hx;
       sHy[oh] = hy;
       sHz[oh] = hz;
@@ -476,9 +552,13 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
         T a = T(0), b = T(0), c = T(0);
         if (ok && (hrow || hcolm)) {
           Column hc;
-          if (hrow) make_column(G, i, y0 - 1, hc, false);
-          else make_column(G, x0 - 1, y0 + tx, hc, false);
-          h_at(hc, hrow ? tx + xo : (tx + 1) * BXT + xo - 1, false, a, b, c);
+          make_column(G, hi, hj, hc, false);
+          PsiPre<T> hp;
+          hp.axis = pl.sz >= 0 ? 2 : (hc.sx >= 0 ? 0 : (hc.sy >= 0 ? 1 : -1));
+          hp.h0 = slots[4 * L::NT + hid];
+          hp.h1 = slots[4 * L::NT + L::NH + hid];
+          hp.e0 = hp.e1 = T(0);
+          h_at(hc, hrow ? tx + xo : (tx + 1) * BXT + xo - 1, false, a, b, c, &hp);
         }
         const int slot = ty == 0 ? tx + 1 : (tx + 1) * HW;
         sHx[slot] = a;
@@ -488,6 +568,7 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
       // the output tile buffer must have been read by the previous plane's store
       if (tid == 0) bulk_wait_read0();
       if (__syncthreads_or(!ok)) {
+        cp_async_wait<0>();
         if (tid == 0) {
           atomicOr(G.err, 2);
           bulk_wait0();
@@ -500,7 +581,7 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
         if (own)
           e_node<T, GAIN>(G, sg, col, pl, sel, n, cidx, m, gcell, gs, hz - sHz[oh - HW], hy - hPy, hx - hPx,
                           hz - sHz[oh - 1], hy - sHy[oh - 1], hx - sHx[oh - HW], Fk[oe], Fk[PL + oe],
-                          Fk[2 * PL + oe], enx, eny, enz);
+                          Fk[2 * PL + oe], enx, eny, enz, &pre);
         out[tid] = enx;
         out[OPL + tid] = eny;
         out[2 * OPL + tid] = enz;
@@ -524,9 +605,11 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
           issue(q + S, kstart + p + S);
         }
       }
+      issue_psi(kstart + p + S, (int)(q % S));
     }
     ld = q0 + (unsigned)NP;
   }
+  cp_async_wait<0>();
   if (tid == 0) bulk_wait0();
 }
 
