@@ -428,6 +428,7 @@ struct GridImpl final : GridBase {
       while (depth > 4 && (long long)tiles * ((desc.nz + depth - 1) / depth) < 2LL * wave) depth -= 2;
     }
     depth = std::min(depth, desc.nz);
+    if (use_tma) depth = std::min(depth, kTmaZMax - 1);  // the item's planes' coefficients fit in shared memory
     // longest items first: tiles that cross absorbing slabs (and the wider
     // halo of the plain kernel) cost more per plane, so they are issued before
     // the interior tiles, which then fill the tail of the launch

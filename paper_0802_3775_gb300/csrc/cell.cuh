@@ -75,12 +75,35 @@ __device__ __forceinline__ void gain_normals(unsigned long long seed, long long 
   c = sqrt(-2.0 * log(u2)) * cospi(2.0 * u3);
 }
 
-// CPML-modified difference: D / kappa + psi with psi <- b psi + c D.
+// CPML grading coefficients of a node: c(axis, h, q) with h = 0 for the
+// E-curl (integer) node and 1 for the H-curl (half-integer) node, q = 0, 1, 2
+// for 1/kappa, b, c.  CoefGlobal reads the grid's profile arrays; the TMA
+// kernel stages the tile's coefficients in shared memory (CoefShared).
 template <typename T>
-__device__ __forceinline__ T pml_term(T D, const T* const* pr, int pos, const T* psi_in, T* psi_out, int pi) {
-  const T p = fmad(pr[1][pos], psi_in[pi], pr[2][pos] * D);
+struct CoefGlobal {
+  const StepGrid<T>* G;
+  int i, j, k;
+  __device__ __forceinline__ T x(int h, int q) const { return G->prof[0][h][q][i]; }
+  __device__ __forceinline__ T y(int h, int q) const { return G->prof[1][h][q][j]; }
+  __device__ __forceinline__ T z(int h, int q) const { return G->prof[2][h][q][k]; }
+};
+
+template <typename T>
+struct CoefShared {
+  const T* px;  // 6 values (h, q) of the node's column, row and plane
+  const T* py;
+  const T* pz;
+  __device__ __forceinline__ T x(int h, int q) const { return px[h * 3 + q]; }
+  __device__ __forceinline__ T y(int h, int q) const { return py[h * 3 + q]; }
+  __device__ __forceinline__ T z(int h, int q) const { return pz[h * 3 + q]; }
+};
+
+// CPML-modified difference D / kappa + psi with psi <- b psi + c D.
+template <typename T>
+__device__ __forceinline__ T pml_term_c(T D, T ik, T b, T c, T psi_old, T* psi_out, int pi) {
+  const T p = fmad(b, psi_old, c * D);
   if (psi_out) psi_out[pi] = p;
-  return fmad(pr[0][pos], D, p);
+  return fmad(ik, D, p);
 }
 
 // CPML memory of one slab axis of a node, fetched ahead of its update:
@@ -90,14 +113,6 @@ struct PsiPre {
   int axis;
   T h0, h1, e0, e1;
 };
-
-// pml_term with the old psi value already in hand.
-template <typename T>
-__device__ __forceinline__ T pml_term_v(T D, const T* const* pr, int pos, T psi_old, T* psi_out, int pi) {
-  const T p = fmad(pr[1][pos], psi_old, pr[2][pos] * D);
-  if (psi_out) psi_out[pi] = p;
-  return fmad(pr[0][pos], D, p);
-}
 
 // Slab coordinate of node index q on an axis of length n with slabs L0, L1 (-1 outside).
 __device__ __forceinline__ int slab_index(int q, int n, int L0, int L1) {
@@ -181,46 +196,40 @@ __device__ __forceinline__ Plane make_plane(const StepGrid<T>& G, int k) {
 // H~^{n+1/2} at node (c.i, c.j, p.k) from the six forward differences of E^n.
 // Inside a slab the difference becomes D/kappa + psi; psi^{n-1/2} is read from
 // set `sel`, psi^{n+1/2} written to set sel^1 when `wr` (owner of the node).
-template <typename T>
+template <typename T, typename CF>
 __device__ __forceinline__ void h_node(const StepGrid<T>& G, const Column& c, const Plane& p, int sel, bool wr,
-                                       T dyEz, T dzEy, T dzEx, T dxEz, T dxEy, T dyEx, T hOx, T hOy, T hOz, T& hx,
-                                       T& hy, T& hz, const PsiPre<T>* pre = nullptr) {
+                                       const CF& cf, T dyEz, T dzEy, T dzEx, T dxEz, T dxEy, T dyEx, T hOx, T hOy,
+                                       T hOz, T& hx, T& hy, T& hz, const PsiPre<T>* pre = nullptr) {
   const int pa = pre ? pre->axis : -1;
   if (c.sx >= 0) {
     const int pi = p.px_plane + c.px0;
     T* o0 = wr ? G.psiH[sel ^ 1][0][0] : (T*)nullptr;
     T* o1 = wr ? G.psiH[sel ^ 1][0][1] : (T*)nullptr;
-    if (pa == 0) {
-      dxEz = pml_term_v(dxEz, G.prof[0][1], c.i, pre->h0, o0, pi);
-      dxEy = pml_term_v(dxEy, G.prof[0][1], c.i, pre->h1, o1, pi);
-    } else {
-      dxEz = pml_term(dxEz, G.prof[0][1], c.i, G.psiH[sel][0][0], o0, pi);
-      dxEy = pml_term(dxEy, G.prof[0][1], c.i, G.psiH[sel][0][1], o1, pi);
-    }
+    const T ik = cf.x(1, 0), b = cf.x(1, 1), cc = cf.x(1, 2);
+    const T s0 = pa == 0 ? pre->h0 : G.psiH[sel][0][0][pi];
+    const T s1 = pa == 0 ? pre->h1 : G.psiH[sel][0][1][pi];
+    dxEz = pml_term_c(dxEz, ik, b, cc, s0, o0, pi);
+    dxEy = pml_term_c(dxEy, ik, b, cc, s1, o1, pi);
   }
   if (c.sy >= 0) {
     const int pi = p.py_plane + c.py0;
     T* o0 = wr ? G.psiH[sel ^ 1][1][0] : (T*)nullptr;
     T* o1 = wr ? G.psiH[sel ^ 1][1][1] : (T*)nullptr;
-    if (pa == 1) {
-      dyEx = pml_term_v(dyEx, G.prof[1][1], c.j, pre->h0, o0, pi);
-      dyEz = pml_term_v(dyEz, G.prof[1][1], c.j, pre->h1, o1, pi);
-    } else {
-      dyEx = pml_term(dyEx, G.prof[1][1], c.j, G.psiH[sel][1][0], o0, pi);
-      dyEz = pml_term(dyEz, G.prof[1][1], c.j, G.psiH[sel][1][1], o1, pi);
-    }
+    const T ik = cf.y(1, 0), b = cf.y(1, 1), cc = cf.y(1, 2);
+    const T s0 = pa == 1 ? pre->h0 : G.psiH[sel][1][0][pi];
+    const T s1 = pa == 1 ? pre->h1 : G.psiH[sel][1][1][pi];
+    dyEx = pml_term_c(dyEx, ik, b, cc, s0, o0, pi);
+    dyEz = pml_term_c(dyEz, ik, b, cc, s1, o1, pi);
   }
   if (p.sz >= 0) {
     const int pi = p.pz_plane + c.pz0;
     T* o0 = wr ? G.psiH[sel ^ 1][2][0] : (T*)nullptr;
     T* o1 = wr ? G.psiH[sel ^ 1][2][1] : (T*)nullptr;
-    if (pa == 2) {
-      dzEy = pml_term_v(dzEy, G.prof[2][1], p.k, pre->h0, o0, pi);
-      dzEx = pml_term_v(dzEx, G.prof[2][1], p.k, pre->h1, o1, pi);
-    } else {
-      dzEy = pml_term(dzEy, G.prof[2][1], p.k, G.psiH[sel][2][0], o0, pi);
-      dzEx = pml_term(dzEx, G.prof[2][1], p.k, G.psiH[sel][2][1], o1, pi);
-    }
+    const T ik = cf.z(1, 0), b = cf.z(1, 1), cc = cf.z(1, 2);
+    const T s0 = pa == 2 ? pre->h0 : G.psiH[sel][2][0][pi];
+    const T s1 = pa == 2 ? pre->h1 : G.psiH[sel][2][1][pi];
+    dzEy = pml_term_c(dzEy, ik, b, cc, s0, o0, pi);
+    dzEx = pml_term_c(dzEx, ik, b, cc, s1, o1, pi);
   }
   const T cH = G.cH;
   hx = fmad(-cH, dyEz - dzEy, hOx);
@@ -304,41 +313,36 @@ __device__ __forceinline__ void source_drive(const StepGrid<T>& G, const double*
 // H~^{n+1/2}, with the CPML (E-side memory updated in place), the soft
 // sources, the gain polarization current and populations (state `gs` of a
 // gain cell), and the PEC hold of tangential E on index-0 planes.
-template <typename T, bool GAIN>
+template <typename T, bool GAIN, typename CF>
 __device__ __forceinline__ void e_node(const StepGrid<T>& G, const double* sg, const Column& c, const Plane& p,
                                        int sel, long long n, long long cidx, unsigned m, bool gcell,
-                                       const GainState<T>& gs, T dyHz, T dzHy, T dzHx, T dxHz, T dxHy, T dyHx, T eCx,
-                                       T eCy, T eCz, T& enx, T& eny, T& enz, const PsiPre<T>* pre = nullptr) {
+                                       const GainState<T>& gs, const CF& cf, T dyHz, T dzHy, T dzHx, T dxHz, T dxHy,
+                                       T dyHx, T eCx, T eCy, T eCz, T& enx, T& eny, T& enz,
+                                       const PsiPre<T>* pre = nullptr) {
   const int pa = pre ? pre->axis : -1;
   if (c.sx >= 0) {
     const int pi = p.px_plane + c.px0;
-    if (pa == 0) {
-      dxHz = pml_term_v(dxHz, G.prof[0][0], c.i, pre->e0, G.psiE[0][0], pi);
-      dxHy = pml_term_v(dxHy, G.prof[0][0], c.i, pre->e1, G.psiE[0][1], pi);
-    } else {
-      dxHz = pml_term(dxHz, G.prof[0][0], c.i, G.psiE[0][0], G.psiE[0][0], pi);
-      dxHy = pml_term(dxHy, G.prof[0][0], c.i, G.psiE[0][1], G.psiE[0][1], pi);
-    }
+    const T ik = cf.x(0, 0), b = cf.x(0, 1), cc = cf.x(0, 2);
+    const T s0 = pa == 0 ? pre->e0 : G.psiE[0][0][pi];
+    const T s1 = pa == 0 ? pre->e1 : G.psiE[0][1][pi];
+    dxHz = pml_term_c(dxHz, ik, b, cc, s0, G.psiE[0][0], pi);
+    dxHy = pml_term_c(dxHy, ik, b, cc, s1, G.psiE[0][1], pi);
   }
   if (c.sy >= 0) {
     const int pi = p.py_plane + c.py0;
-    if (pa == 1) {
-      dyHx = pml_term_v(dyHx, G.prof[1][0], c.j, pre->e0, G.psiE[1][0], pi);
-      dyHz = pml_term_v(dyHz, G.prof[1][0], c.j, pre->e1, G.psiE[1][1], pi);
-    } else {
-      dyHx = pml_term(dyHx, G.prof[1][0], c.j, G.psiE[1][0], G.psiE[1][0], pi);
-      dyHz = pml_term(dyHz, G.prof[1][0], c.j, G.psiE[1][1], G.psiE[1][1], pi);
-    }
+    const T ik = cf.y(0, 0), b = cf.y(0, 1), cc = cf.y(0, 2);
+    const T s0 = pa == 1 ? pre->e0 : G.psiE[1][0][pi];
+    const T s1 = pa == 1 ? pre->e1 : G.psiE[1][1][pi];
+    dyHx = pml_term_c(dyHx, ik, b, cc, s0, G.psiE[1][0], pi);
+    dyHz = pml_term_c(dyHz, ik, b, cc, s1, G.psiE[1][1], pi);
   }
   if (p.sz >= 0) {
     const int pi = p.pz_plane + c.pz0;
-    if (pa == 2) {
-      dzHy = pml_term_v(dzHy, G.prof[2][0], p.k, pre->e0, G.psiE[2][0], pi);
-      dzHx = pml_term_v(dzHx, G.prof[2][0], p.k, pre->e1, G.psiE[2][1], pi);
-    } else {
-      dzHy = pml_term(dzHy, G.prof[2][0], p.k, G.psiE[2][0], G.psiE[2][0], pi);
-      dzHx = pml_term(dzHx, G.prof[2][0], p.k, G.psiE[2][1], G.psiE[2][1], pi);
-    }
+    const T ik = cf.z(0, 0), b = cf.z(0, 1), cc = cf.z(0, 2);
+    const T s0 = pa == 2 ? pre->e0 : G.psiE[2][0][pi];
+    const T s1 = pa == 2 ? pre->e1 : G.psiE[2][1][pi];
+    dzHy = pml_term_c(dzHy, ik, b, cc, s0, G.psiE[2][0], pi);
+    dzHx = pml_term_c(dzHx, ik, b, cc, s1, G.psiE[2][1], pi);
   }
   const T curlx = dyHz - dzHy;
   const T curly = dzHx - dxHz;

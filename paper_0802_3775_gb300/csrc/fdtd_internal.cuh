@@ -20,6 +20,7 @@ constexpr int kEnergyBlocks = 256;
 #endif
 constexpr int kTmaStages = FDTD_TMA_STAGES;  // planes resident or in flight per block (TMA step kernel)
 constexpr int kTmaOX = 32;        // owned tile width of the TMA step kernel
+constexpr int kTmaZMax = 32;      // planes of one TMA work item, its lower halo plane included
 
 // Physical constants (CODATA; mu0 of the 2019 SI, hbar exact).
 constexpr double kC0 = 299792458.0;

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(512) k_step(const StepGrid<T>* __restrict__ gr
 
       T hx = T(0), hy = T(0), hz = T(0);
       if (valid && vk) {
-        h_node(G, col, pl, sel, owner && active, sEz[se + EW] - eCz, eNy - eCy, eNx - eCx, sEz[se + 1] - eCz,
+        h_node(G, col, pl, sel, owner && active, CoefGlobal<T>{&G, col.i, col.j, pl.k}, sEz[se + EW] - eCz, eNy - eCy, eNx - eCx, sEz[se + 1] - eCz,
                sEy[se + 1] - eCy, sEx[se + EW] - eCx, hOx, hOy, hOz, hx, hy, hz);
       }
       sHx[tid] = hx;
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(512) k_step(const StepGrid<T>* __restrict__ gr
         GainState<T> gs{};
         if (GAIN && gcell) load_gain(G, sel, cidx, gs);
         T enx, eny, enz;
-        e_node<T, GAIN>(G, sg, col, pl, sel, n, cidx, m, gcell, gs, hz - sHz[tid - bx], hy - hPy, hx - hPx,
+        e_node<T, GAIN>(G, sg, col, pl, sel, n, cidx, m, gcell, gs, CoefGlobal<T>{&G, col.i, col.j, pl.k}, hz - sHz[tid - bx], hy - hPy, hx - hPx,
                         hz - sHz[tid - 1], hy - sHy[tid - 1], hx - sHx[tid - bx], eCx, eCy, eCz, enx, eny, enz);
         G.F[sel ^ 1][0][cidx] = enx;
         G.F[sel ^ 1][1][cidx] = eny;
@@ -359,7 +359,11 @@ struct TmaLayout {
   static constexpr size_t stage_bytes = field_bytes + mat_bytes + psi_bytes;
   static constexpr size_t out_off = stage_off + (size_t)kTmaStages * stage_bytes;
   static constexpr size_t h_off = out_off + align128((size_t)6 * OPL * sizeof(T));
-  static constexpr size_t total = h_off + (size_t)3 * HPL * sizeof(T) + 128;  // + base alignment slack
+  // CPML grading coefficients of the item: (OX + 1) columns, (OY + 1) rows
+  // (the -x / -y halo first) and up to kTmaZMax planes, 6 values each
+  static constexpr int CXN = (kTmaOX + 1) * 6, CYN = (OY + 1) * 6, CZN = kTmaZMax * 6;
+  static constexpr size_t coef_off = h_off + align128((size_t)3 * HPL * sizeof(T));
+  static constexpr size_t total = coef_off + (size_t)(CXN + CYN + CZN) * sizeof(T) + 128;  // + base alignment slack
 };
 
 template <typename T>
@@ -393,6 +397,9 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
   T* sHx = reinterpret_cast<T*>(smem + L::h_off);
   T* sHy = sHx + HPL;
   T* sHz = sHy + HPL;
+  T* cfx = reinterpret_cast<T*>(smem + L::coef_off);
+  T* cfy = cfx + L::CXN;
+  T* cfz = cfy + L::CYN;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * OX + tx;
 
@@ -495,7 +502,28 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
       }
       cp_async_commit();
     };
+    // grading coefficients of the columns, rows and planes this item touches
+    // (joined to the first plane's copy group; visible after the barrier below)
+    {
+      const bool any_slab = G.Sd[0] || G.Sd[1] || G.Sd[2];
+      for (int e = tid; any_slab && e < L::CXN + L::CYN + 6 * (NP - 1); e += OX * OY) {
+        int a, pos;
+        T* dst;
+        if (e < L::CXN) {
+          a = 0; pos = x0 - 1 + e / 6; dst = cfx + e;
+        } else if (e < L::CXN + L::CYN) {
+          a = 1; pos = y0 - 1 + (e - L::CXN) / 6; dst = cfy + (e - L::CXN);
+        } else {
+          a = 2; pos = kstart + (e - L::CXN - L::CYN) / 6; dst = cfz + (e - L::CXN - L::CYN);
+        }
+        const int hq = e % 6;  // CXN and CYN are multiples of 6
+        const int lim = a == 0 ? nx : (a == 1 ? ny : G.nz);
+        if (G.Sd[a] && pos >= 0 && pos < lim) cp_async_elem(dst, G.prof[a][hq / 3][hq % 3] + pos);
+      }
+    }
     for (int p = 0; p < S; ++p) issue_psi(kstart + p, (int)((q0 + p) % S));
+    cp_async_wait<S - 1>();
+    __syncthreads();
 
     T hPx = T(0), hPy = T(0);
     bool ok = true;
@@ -536,15 +564,18 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
       }
 
       // H^{n+1/2} of plane k at the staged node with offset o
-      auto h_at = [&](const Column& c, int o, bool wr, T& hx, T& hy, T& hz, const PsiPre<T>* pp) {
+      const T* cz = cfz + 6 * p;
+      auto h_at = [&](const Column& c, const CoefShared<T>& cf, int o, bool wr, T& hx, T& hy, T& hz,
+                      const PsiPre<T>* pp) {
         const T ex = Fk[o], ey = Fk[PL + o], ez = Fk[2 * PL + o];
-        h_node(G, c, pl, sel, wr, Fk[2 * PL + o + BXT] - ez, Fn[PL + o] - ey, Fn[o] - ex, Fk[2 * PL + o + 1] - ez,
+        h_node(G, c, pl, sel, wr, cf, Fk[2 * PL + o + BXT] - ez, Fn[PL + o] - ey, Fn[o] - ex, Fk[2 * PL + o + 1] - ez,
                Fk[PL + o + 1] - ey, Fk[o + BXT] - ex, Fk[3 * PL + o], Fk[4 * PL + o], Fk[5 * PL + o], hx, hy, hz,
                pp);
       };
 
       T hx = T(0), hy = T(0), hz = T(0);
-      if (ok && own) h_at(col, oe, active, hx, hy, hz, &pre);
+      const CoefShared<T> ocf{cfx + 6 * (tx + 1), cfy + 6 * (ty + 1), cz};
+      if (ok && own) h_at(col, ocf, oe, active, hx, hy, hz, &pre);
       sHx[oh] = hx;
       sHy[oh] = hy;
       sHz[oh] = hz;
@@ -558,7 +589,8 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
           hp.h0 = slots[4 * L::NT + hid];
           hp.h1 = slots[4 * L::NT + L::NH + hid];
           hp.e0 = hp.e1 = T(0);
-          h_at(hc, hrow ? tx + xo : (tx + 1) * BXT + xo - 1, false, a, b, c, &hp);
+          const CoefShared<T> hcf{hrow ? cfx + 6 * (tx + 1) : cfx, hrow ? cfy : cfy + 6 * (tx + 1), cz};
+          h_at(hc, hcf, hrow ? tx + xo : (tx + 1) * BXT + xo - 1, false, a, b, c, &hp);
         }
         const int slot = ty == 0 ? tx + 1 : (tx + 1) * HW;
         sHx[slot] = a;
@@ -579,7 +611,7 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
       if (active) {
         T enx = T(0), eny = T(0), enz = T(0);
         if (own)
-          e_node<T, GAIN>(G, sg, col, pl, sel, n, cidx, m, gcell, gs, hz - sHz[oh - HW], hy - hPy, hx - hPx,
+          e_node<T, GAIN>(G, sg, col, pl, sel, n, cidx, m, gcell, gs, ocf, hz - sHz[oh - HW], hy - hPy, hx - hPx,
                           hz - sHz[oh - 1], hy - sHy[oh - 1], hx - sHx[oh - HW], Fk[oe], Fk[PL + oe],
                           Fk[2 * PL + oe], enx, eny, enz, &pre);
         out[tid] = enx;
