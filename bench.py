@@ -150,6 +150,18 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def configure_grid(args, g):
+    if args.kernel != "auto":
+        g.set_kernel(args.kernel)
+    if args.by:
+        g.set_launch(32, args.by, 0, 0)
+
+
+def configure_batch(args, b):
+    if args.kernel != "auto" or args.by:
+        b.set_launch(args.kernel, args.by or 8, 0, 0)
+
+
 def run_gpu(args, rank, world, dist):
     import torch
 
@@ -162,6 +174,8 @@ def run_gpu(args, rank, world, dist):
     specs = workload_specs(args.workload, rank, args.steps + args.warmup)
     cap = args.steps + args.warmup + 16
     grids = [Grid.from_spec(s, record_capacity=cap) for s in specs]
+    for g in grids:
+        configure_grid(args, g)
     gain_cells = []
     for g, s in zip(grids, specs):
         gain_cells.append(int(np.count_nonzero(g.get_material() & 64)) if s.gain is not None else 0)
@@ -169,6 +183,7 @@ def run_gpu(args, rank, world, dist):
     if len(grids) > 1:
         from paper_0802_3775_gb300.fdtd import Batch
         batch = Batch(grids)
+        configure_batch(args, batch)
         stepper = batch
     else:
         stepper = grids[0]
@@ -197,6 +212,8 @@ def run_gpu(args, rank, world, dist):
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     kernel = [stepper.kernel_time()]
+    kind, rows = grids[0].kernel_in_use()
+    kname = {1: "k_step", 2: "k_step_tma", 3: "k_step_pair"}[kind]
     stepper.set_timing(False)
     stepper.sync()
     ms_max = ms
@@ -236,7 +253,8 @@ def run_gpu(args, rank, world, dist):
                    "launch": "direct launches with per-launch events in the timed region"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "k_step_tma", "algorithmic_bytes_per_launch": bytes_step,
+                     "kernel": kname, "tile": [32 if kind > 1 else None, rows],
+                     "algorithmic_bytes_per_launch": bytes_step,
                      "mean_launch_ms": round(per_launch_ms, 5), "peak_source": f"{peak_kind} hbm_gbs"},
         "e2e": e2e,
         "gpu_launches": launches,
@@ -266,11 +284,13 @@ def run_e2e(args, specs, rank, dist):
     gs = []
     for s in specs:
         g = Grid.from_spec(s, record_capacity=args.steps + 16)
+        configure_grid(args, g)
         h2d += s.spheres.nbytes if s.spheres is not None else 0
         gs.append(g)
     if len(gs) > 1:
         from paper_0802_3775_gb300.fdtd import Batch
         b = Batch(gs)
+        configure_batch(args, b)
         b.set_graph(min(50, args.steps))
         b.step(args.steps)
         b.sync()
@@ -372,6 +392,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="planewave")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma", "pair"],
+                    help="step kernel (default: the library's automatic choice)")
+    ap.add_argument("--by", type=int, default=0, help="tile rows of the step kernel (0: library default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

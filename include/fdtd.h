@@ -125,8 +125,9 @@ int fdtd_destroy_grid(fdtd_grid* g);
 int fdtd_set_eps_from_spheres(fdtd_grid* g, const double* spheres, int64_t n, const double box_lo[3],
                               const double box_hi[3]);
 
-/* Set / read the material bytes directly (uint8[nz][ny][nx], host).
- * set: before the first step only. */
+/* Set / read the material bytes directly (uint8[nz][ny][nx], host), in the
+ * layout above.  set: before the first step only; E_INVAL if a byte holds
+ * class 3 in any of its three 2-bit fields or has bit 7 set. */
 int fdtd_set_material(fdtd_grid* g, const uint8_t* mat);
 int fdtd_get_material(fdtd_grid* g, uint8_t* mat);
 
@@ -196,9 +197,18 @@ int fdtd_set_launch(fdtd_grid* g, int32_t bx, int32_t by, int32_t zdepth, int32_
 /* Step-kernel variant: 0 = automatic (the TMA-staged kernel when no axis is
  * periodic, else the plain-load kernel), 1 = plain-load kernel (blocks of
  * bx x by threads own (bx-1) x (by-1) columns), 2 = TMA-staged kernel (blocks
- * of 32 x by threads own 32 x by columns; E_INVAL on periodic grids).  Both
- * perform the same arithmetic per node and give identical results. */
+ * of 32 x by threads own 32 x by columns; E_INVAL on periodic grids),
+ * 3 = paired TMA-staged kernel, binary32 grids only (each thread updates two
+ * x-adjacent nodes with packed f32x2 arithmetic; tiles of 32 x 16 columns, or
+ * 32 x 8 when by == 8; E_INVAL on periodic or binary64 grids).  All perform
+ * the same arithmetic per node and give identical results. */
 int fdtd_set_kernel(fdtd_grid* g, int32_t kind);
+
+/* The step kernel the grid's launches use under its current settings
+ * (1 plain, 2 TMA, 3 paired), and the rows of its tile (*rows: the tile of
+ * owned columns is 32 x rows for kinds 2 and 3, (bx-1) x (by-1) for kind 1).
+ * Valid after the first step (or a batch build); E_STATE before. */
+int fdtd_kernel_in_use(fdtd_grid* g, int32_t* kind, int32_t* rows);
 
 /* Per-launch timing of the step kernel: while on, every step-kernel launch
  * is bracketed by a pair of CUDA events on the grid's stream.

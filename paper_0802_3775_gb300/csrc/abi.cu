@@ -192,6 +192,12 @@ int fdtd_set_material(fdtd_grid* g, const uint8_t* mat) {
     CHECK_GRID(g);
     BEFORE_FIRST_STEP(G, "fdtd_set_material");
     if (!mat) return set_error(FDTD_E_INVAL, "null material");
+    const long long cells = (long long)G->desc.nx * G->desc.ny * G->desc.nz;
+    for (long long q = 0; q < cells; ++q) {
+      const unsigned b = mat[q];
+      if ((b & 0x80u) || (b & 3u) == 3u || ((b >> 2) & 3u) == 3u || ((b >> 4) & 3u) == 3u)
+        return set_error(FDTD_E_INVAL, "material byte %u at cell %lld: class 3 or bit 7 set", b, q);
+    }
     const int r = G->set_material(mat);
     if (r != FDTD_OK) return r;
     G->material_set = true;
@@ -298,16 +304,29 @@ int fdtd_set_launch(fdtd_grid* g, int32_t bx, int32_t by, int32_t zdepth, int32_
 int fdtd_set_kernel(fdtd_grid* g, int32_t kind) {
   return guarded([&]() -> int {
     CHECK_GRID(g);
-    if (kind < 0 || kind > 2) return set_error(FDTD_E_INVAL, "kernel kind must be 0 (auto), 1 (plain) or 2 (TMA)");
+    if (kind < 0 || kind > 3)
+      return set_error(FDTD_E_INVAL, "kernel kind must be 0 (auto), 1 (plain), 2 (TMA) or 3 (paired TMA)");
     const fdtd_grid_desc& d = G->desc;
-    if (kind == 2 && (d.periodic[0] || d.periodic[1] || d.periodic[2]))
-      return set_error(FDTD_E_INVAL, "the TMA step kernel does not handle periodic axes");
+    if ((kind == 2 || kind == 3) && (d.periodic[0] || d.periodic[1] || d.periodic[2]))
+      return set_error(FDTD_E_INVAL, "the TMA step kernels do not handle periodic axes");
+    if (kind == 3 && d.precision != FDTD_FP32) return set_error(FDTD_E_INVAL, "the paired step kernel is binary32 only");
     G->kernel_kind = kind;
     if (G->finalized) {
       cudaError_t e = cudaStreamSynchronize(G->stream);
       if (e != cudaSuccess) return fdtd::cuda_error(e, "sync");
       return G->replan();
     }
+    return FDTD_OK;
+  });
+}
+
+int fdtd_kernel_in_use(fdtd_grid* g, int32_t* kind, int32_t* rows) {
+  return guarded([&]() -> int {
+    CHECK_GRID(g);
+    if (!kind || !rows) return set_error(FDTD_E_INVAL, "null output");
+    if (!G->finalized) return set_error(FDTD_E_STATE, "the launch plan is made at the first step");
+    *kind = G->uses_pair() ? 3 : (G->uses_tma() ? 2 : 1);
+    *rows = G->uses_tma() ? G->tile_rows() : G->by - 1;
     return FDTD_OK;
   });
 }
@@ -488,7 +507,7 @@ int fdtd_batch_destroy(fdtd_batch* b) {
 int fdtd_batch_set_launch(fdtd_batch* b, int32_t kernel, int32_t by, int32_t zdepth, int32_t grid_blocks) {
   return guarded([&]() -> int {
     CHECK_BATCH(b);
-    if (kernel < 0 || kernel > 2 || by < 2 || by > 16 || zdepth < 0 || grid_blocks < 0)
+    if (kernel < 0 || kernel > 3 || by < 2 || by > 16 || zdepth < 0 || grid_blocks < 0)
       return set_error(FDTD_E_INVAL, "batch launch shape");
     B->kernel_kind = kernel;
     B->bx = 32;

@@ -169,6 +169,8 @@ struct GridImpl final : GridBase {
   T* d_prof = nullptr;
   TmaGrid* d_tma = nullptr;
   bool use_tma = false;
+  bool use_pair = false;  // paired binary32 kernel (TMA staging, tiles of 32 x tile_oy)
+  int tile_oy = 8;
   double n_total = 0.0, neq[4] = {0, 0, 0, 0};
 
   int precision() const override { return sizeof(T) == 4 ? FDTD_FP32 : FDTD_FP64; }
@@ -409,10 +411,13 @@ struct GridImpl final : GridBase {
   void plan_items() {
     items.clear();
     const bool periodic = desc.periodic[0] || desc.periodic[1] || desc.periodic[2];
-    use_tma = (kernel_kind == 2 || (kernel_kind == 0 && !periodic)) && !periodic && (by == 4 || by == 8) &&
-              tensor_map_encoder() != nullptr;
+    const bool enc = tensor_map_encoder() != nullptr;
+    const int kind = (kernel_kind == 3 && sizeof(T) != 4) ? 2 : kernel_kind;  // paired kernel: binary32 only
+    use_pair = sizeof(T) == 4 && kind == 3 && !periodic && enc;
+    use_tma = use_pair || ((kind == 2 || (kind == 0 && !periodic)) && !periodic && (by == 4 || by == 8) && enc);
+    tile_oy = use_pair ? (by == 8 ? 8 : 16) : by;
     const int ox = use_tma ? kTmaOX : bx - 1;
-    const int oy = use_tma ? by : by - 1;
+    const int oy = use_tma ? tile_oy : by - 1;
     const int tnx = (desc.nx + ox - 1) / ox, tny = (desc.ny + oy - 1) / oy;
     const int tiles = tnx * tny;
     int depth = zdepth;
@@ -423,7 +428,8 @@ struct GridImpl final : GridBase {
       int dev = 0, sms = 152;
       if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       cudaGetLastError();
-      const int wave = sms * step_blocks_per_sm<T>(use_tma, sg.gain != 0, bx, by);
+      const int wave = sms * (use_pair ? step_pair_blocks_per_sm(sg.gain != 0, tile_oy)
+                                       : step_blocks_per_sm<T>(use_tma, sg.gain != 0, bx, by));
       depth = 16;
       while (depth > 4 && (long long)tiles * ((desc.nz + depth - 1) / depth) < 2LL * wave) depth -= 2;
     }
@@ -461,7 +467,7 @@ struct GridImpl final : GridBase {
     const cuuint64_t fdim[4] = {(cuuint64_t)desc.nx, (cuuint64_t)desc.ny, (cuuint64_t)desc.nz, 12};
     const cuuint64_t fstr[3] = {(cuuint64_t)px * sizeof(T), (cuuint64_t)px * desc.ny * sizeof(T),
                                 (cuuint64_t)nstore * sizeof(T)};
-    const cuuint32_t fbox[4] = {(cuuint32_t)(kTmaOX + 2 * AX), (cuuint32_t)(by + 2), 1, 6};
+    const cuuint32_t fbox[4] = {(cuuint32_t)(kTmaOX + 2 * AX), (cuuint32_t)(tile_oy + 2), 1, 6};
     const cuuint32_t one[4] = {1, 1, 1, 1};
     CUresult r = enc(&h.fields, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
                      (void*)d_F, fdim, fstr, fbox, one, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -469,12 +475,12 @@ struct GridImpl final : GridBase {
     if (r != CUDA_SUCCESS) return set_error(FDTD_E_CUDA, "tensor map (fields) encode failed: %d", (int)r);
     const cuuint64_t mdim[3] = {(cuuint64_t)desc.nx, (cuuint64_t)desc.ny, (cuuint64_t)desc.nz};
     const cuuint64_t mstr[2] = {(cuuint64_t)px, (cuuint64_t)px * desc.ny};
-    const cuuint32_t mbox[3] = {(cuuint32_t)kTmaOX, (cuuint32_t)by, 1};
+    const cuuint32_t mbox[3] = {(cuuint32_t)kTmaOX, (cuuint32_t)tile_oy, 1};
     r = enc(&h.mat, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, (void*)d_mat, mdim, mstr, mbox, one,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(FDTD_E_CUDA, "tensor map (material) encode failed: %d", (int)r);
-    const cuuint32_t sbox[4] = {(cuuint32_t)kTmaOX, (cuuint32_t)by, 1, 6};
+    const cuuint32_t sbox[4] = {(cuuint32_t)kTmaOX, (cuuint32_t)tile_oy, 1, 6};
     r = enc(&h.store, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
             (void*)d_F, fdim, fstr, sbox, one, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -557,7 +563,10 @@ struct GridImpl final : GridBase {
       for (int s = 0; s < chunk; ++s) {
         const auto ev = timer.next();
         if (ev.first) cudaEventRecord(ev.first, stream);
-        if (use_tma)
+        if (use_pair)
+          e = launch_step_pair(reinterpret_cast<const StepGrid<float>*>(d_sg), d_tma, d_items, (int)items.size(), s,
+                               tile_oy, sg.gain != 0, grid_blocks, stream);
+        else if (use_tma)
           e = launch_step_tma<T>(d_sg, d_tma, d_items, (int)items.size(), s, by, sg.gain != 0, grid_blocks, stream);
         else
           e = launch_step<T>(d_sg, d_items, (int)items.size(), s, bx, by, sg.gain != 0, grid_blocks, stream);
@@ -700,6 +709,8 @@ struct GridImpl final : GridBase {
   int has_gain() const override { return sg.gain; }
   const void* tma_device() const override { return d_tma; }
   bool uses_tma() const override { return use_tma; }
+  bool uses_pair() const override { return use_pair; }
+  int tile_rows() const override { return tile_oy; }
   void work_items(std::vector<int4>& si, std::vector<int4>& oi) const override {
     si = items;
     oi = oitems;

@@ -32,6 +32,8 @@ struct BatchImpl final : BatchBase {
   int4* d_oitems = nullptr;
   std::vector<int4> items, oitems;
   bool gain = false;
+  bool pair = false;  // every member on the paired binary32 kernel
+  int oy = 8;
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
   int graph_built_for = 0;
@@ -50,6 +52,7 @@ struct BatchImpl final : BatchBase {
       if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_error(e, "sync member");
     }
     tma = true;
+    pair = true;
     gain = false;
     for (GridBase* g : grids) {
       g->kernel_kind = kernel_kind;
@@ -61,8 +64,18 @@ struct BatchImpl final : BatchBase {
       if (r != FDTD_OK) return r;
       g->finalized = true;
       tma = tma && g->uses_tma();
+      pair = pair && g->uses_pair();
       gain = gain || g->has_gain();
     }
+    // one launch serves all members: they must agree on the kernel
+    if (tma && !pair)
+      for (GridBase* g : grids)
+        if (g->uses_pair()) {
+          g->kernel_kind = 2;
+          int r = g->replan();
+          if (r != FDTD_OK) return r;
+        }
+    if (!tma) pair = false;
     if (!tma)
       for (GridBase* g : grids)
         if (g->uses_tma()) {
@@ -70,6 +83,7 @@ struct BatchImpl final : BatchBase {
           int r = g->replan();
           if (r != FDTD_OK) return r;
         }
+    oy = grids.empty() ? by : grids[0]->tile_rows();
     std::vector<StepGrid<T>> hsg(ng);
     std::vector<ObsGrid<T>> hog(ng);
     items.clear();
@@ -139,7 +153,10 @@ struct BatchImpl final : BatchBase {
     cudaError_t e;
     const auto ev = timed ? timer.next() : std::pair<cudaEvent_t, cudaEvent_t>{nullptr, nullptr};
     if (ev.first) cudaEventRecord(ev.first, stream);
-    if (tma)
+    if (pair)
+      e = launch_step_pair(reinterpret_cast<const StepGrid<float>*>(d_sg), d_tma, d_items, (int)items.size(), offset,
+                           oy, gain, grid_blocks, stream);
+    else if (tma)
       e = launch_step_tma<T>(d_sg, d_tma, d_items, (int)items.size(), offset, by, gain, grid_blocks, stream);
     else
       e = launch_step<T>(d_sg, d_items, (int)items.size(), offset, bx, by, gain, grid_blocks, stream);

@@ -74,7 +74,7 @@ struct GridBase {
   long long ncell = 0;   // nx * ny * nz
   int px = 0;            // x pitch of the device arrays (nx rounded up to 16)
   long long nstore = 0;  // px * ny * nz
-  int kernel_kind = 0;   // 0 auto (TMA when no axis is periodic), 1 plain loads, 2 TMA
+  int kernel_kind = 0;   // 0 auto, 1 plain loads, 2 TMA, 3 paired TMA (binary32)
   long long steps = 0;
   double S = 0, dx = 0, dt = 0;
   bool material_set = false;
@@ -115,6 +115,8 @@ struct GridBase {
   // batch support: device TMA descriptors, kernel path, work items (grid index 0)
   virtual const void* tma_device() const = 0;
   virtual bool uses_tma() const = 0;
+  virtual bool uses_pair() const = 0;
+  virtual int tile_rows() const = 0;
   virtual void work_items(std::vector<int4>& step_items, std::vector<int4>& obs_items) const = 0;
 
   int get_material(uint8_t* out) {

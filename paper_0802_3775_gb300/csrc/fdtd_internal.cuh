@@ -124,6 +124,14 @@ cudaError_t launch_step_tma(const StepGrid<T>* grids, const TmaGrid* maps, const
 template <typename T>
 size_t step_tma_smem_bytes(int oy);
 
+// Paired binary32 step kernel (two x-adjacent nodes per thread, f32x2
+// arithmetic): tiles of 32 x oy columns (oy 8 or 16), the TMA descriptors of
+// the single-node TMA kernel for the same oy.
+cudaError_t launch_step_pair(const StepGrid<float>* grids, const TmaGrid* maps, const int4* items, int nitems,
+                             int offset, int oy, bool gain, int grid_blocks, cudaStream_t st);
+size_t step_pair_smem_bytes(int oy);
+int step_pair_blocks_per_sm(bool gain, int oy);
+
 // Resident blocks per SM of the step kernel for a launch shape.
 template <typename T>
 int step_blocks_per_sm(bool tma, bool gain, int bx, int by);

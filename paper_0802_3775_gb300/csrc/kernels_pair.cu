@@ -1,0 +1,637 @@
+// Paired binary32 step kernel: one time step n -> n+1 of a list of work items
+// (32-column x OY-row tile x z-range of some binary32 grid, no periodic axis),
+// each thread updating two x-adjacent nodes with packed f32x2 arithmetic.
+//
+// Same staging as the single-node TMA kernel: every plane of the six fields
+// (tile plus a one-node halo, x padded by one 16-byte unit each side) and the
+// tile's material bytes arrive in shared memory by two TMA bulk-tensor copies
+// into a 3-stage mbarrier pipeline; CPML memory of the planes ahead is fetched
+// per thread with cp.async; the new E and H of a plane leave by one TMA
+// bulk-tensor store.  What differs:
+//   - 16 x OY owner threads, each owning the node pair (x0 + 2 tx, x0 + 2 tx + 1):
+//     the pair's values travel as 64-bit shared-memory words and every
+//     difference, curl and update of the interior cell is one f32x2 add, sub,
+//     mul or fma (sm_100 family), half the instructions of the scalar form;
+//   - a ninth warp recomputes H on the -y halo row (16 pairs) and the -x halo
+//     column (OY pairs, the x0-1 node kept) while the owners compute their
+//     own H, and issues the TMA copies, so no owner warp carries halo work;
+//   - the material classes of both nodes index a 64-entry table of
+//     (S/eps_x, S/eps_y, S/eps_z) built once per grid record.
+// Every operation is the one the scalar kernels perform on that node, in the
+// same order and rounding (f32x2 lanes round like the scalar instruction), so
+// the results equal theirs bit for bit.
+//
+// Paper: Yee FDTD (Sec. "Sample and numerical approach"), four-level
+// Maxwell-Bloch gain solved at the Yee cell (same section), noise as a
+// stochastic source (same section).
+#include <math.h>
+
+#include "cell.cuh"
+#include "fdtd_internal.cuh"
+#include "tma.cuh"
+
+namespace fdtd {
+
+// ---------------------------------------------------------------- f32x2
+__device__ __forceinline__ unsigned long long pk2(float2 v) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(r);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(r);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+  return upk2(r);
+}
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+
+// Shared-memory layout of the paired kernel (host and device agree).
+template <int OY>
+struct PairLayout {
+  static constexpr int OX = kTmaOX;             // owned tile width (32)
+  static constexpr int PXT = OX / 2;            // pair threads per row
+  static constexpr int NTO = PXT * OY;          // owner threads
+  static constexpr int NT = NTO + 32;           // + the halo / copy warp
+  static constexpr int AX = 4;                  // x pad: one 16-byte unit each side
+  static constexpr int BXT = OX + 2 * AX;       // staged box width
+  static constexpr int PL = BXT * (OY + 2);     // one component plane of a stage (rows y0-1 .. y0+OY)
+  static constexpr int HW = OX + 2;             // H row: column 0 = x0-2, 1 = x0-1, 2 + l = x0 + l
+  static constexpr int HPL = (OY + 1) * HW;     // row 0 = y0-1
+  static constexpr int OPL = OX * OY;           // one component of the output tile
+  static constexpr int NC = OPL;                // owned nodes
+  static constexpr int NHC = 64;                // halo nodes (32 lanes x 2)
+  static constexpr size_t sg_off = align128(sizeof(StepGrid<float>));
+  static constexpr size_t bar_off = sg_off + align128(kMaxSrc * sizeof(double));
+  static constexpr size_t ctab_off = bar_off + 128;
+  static constexpr size_t stage_off = ctab_off + 64 * sizeof(float4);
+  static constexpr size_t field_bytes = align128((size_t)6 * PL * sizeof(float));
+  static constexpr size_t mat_bytes = align128((size_t)OPL);
+  // CPML memory fetched ahead: 4 slots per owned node, 2 per halo node
+  static constexpr size_t psi_bytes = align128((size_t)(4 * NC + 2 * NHC) * sizeof(float));
+  static constexpr size_t stage_bytes = field_bytes + mat_bytes + psi_bytes;
+  static constexpr size_t out_off = stage_off + (size_t)kTmaStages * stage_bytes;
+  static constexpr size_t h_off = out_off + align128((size_t)6 * OPL * sizeof(float));
+  // CPML grading coefficients: x as [h*3+q][HW column], y as [row][h*3+q], z as [plane][h*3+q]
+  static constexpr int CXN = 6 * HW, CYN = 6 * (OY + 1), CZN = 6 * kTmaZMax;
+  static constexpr size_t coef_off = h_off + align128((size_t)3 * HPL * sizeof(float));
+  static constexpr size_t total = coef_off + (size_t)(CXN + CYN + CZN) * sizeof(float) + 128;
+};
+
+size_t step_pair_smem_bytes(int oy) { return oy == 8 ? PairLayout<8>::total : PairLayout<16>::total; }
+
+// The facts of a node pair (i0, i0 + 1) in row j that stay fixed during a z-march.
+struct PairCol {
+  int i0, j;
+  int sx0, sx1, sy;   // slab coordinates (-1 outside); sx1 = -1 also when node 1 is off the grid
+  int px0, px1;       // x-slab psi offsets of the two nodes in plane 0
+  int py0, pz0;       // y-slab psi offset in plane 0, z-slab offset within a plane (node 0; node 1 is +1)
+  bool own1;          // node 1 is on the grid
+};
+
+__device__ __forceinline__ void make_pair_col(const StepGrid<float>& G, int i0, int j, PairCol& c) {
+  c.i0 = i0;
+  c.j = j;
+  c.own1 = i0 + 1 < G.nx;
+  c.sx0 = G.Sd[0] ? slab_index(i0, G.nx, G.L[0], G.L[1]) : -1;
+  c.sx1 = (G.Sd[0] && c.own1) ? slab_index(i0 + 1, G.nx, G.L[0], G.L[1]) : -1;
+  c.sy = G.Sd[1] ? slab_index(j, G.ny, G.L[2], G.L[3]) : -1;
+  c.px0 = j * G.Sd[0] + c.sx0;
+  c.px1 = j * G.Sd[0] + c.sx1;
+  c.py0 = c.sy * G.nx + i0;
+  c.pz0 = j * G.nx + i0;
+}
+
+// CPML on the pair's differences along x (per node), y and z (both nodes
+// share the row and the plane).  h = 1: H-curl node (memory of set `sel`
+// read, set sel^1 written when `wr`); h = 0: E-curl node (memory updated in
+// place when `wr`).  d[a][s]: the difference that psi slot s of axis a
+// modifies.  pa: axis whose old memory is in `pre` (-1: none); pre[s] holds
+// slot s of the pair (node 0 in .x, node 1 in .y).
+template <int H>
+__device__ __forceinline__ void pair_cpml(const StepGrid<float>& G, const PairCol& c, const Plane& pl, int sel,
+                                          bool wr, const float* cfx, int xcol, const float* cfy, const float* cfz,
+                                          int pa, const float2* pre, float2& dxA, float2& dxB, float2& dyA,
+                                          float2& dyB, float2& dzA, float2& dzB) {
+  // psi arrays: H side reads set sel, writes set sel^1; E side in place
+  auto rd = [&](int a, int s) -> const float* { return H ? G.psiH[sel][a][s] : G.psiE[a][s]; };
+  auto wt = [&](int a, int s) -> float* { return wr ? (H ? G.psiH[sel ^ 1][a][s] : G.psiE[a][s]) : (float*)nullptr; };
+  if (c.sx0 >= 0 || c.sx1 >= 0) {
+    float* o0 = wt(0, 0);
+    float* o1 = wt(0, 1);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int sx = e ? c.sx1 : c.sx0;
+      if (sx < 0) continue;
+      const int pi = pl.px_plane + (e ? c.px1 : c.px0);
+      const float ik = cfx[(3 * H + 0) * PairLayout<8>::HW + xcol + e];
+      const float b = cfx[(3 * H + 1) * PairLayout<8>::HW + xcol + e];
+      const float cc = cfx[(3 * H + 2) * PairLayout<8>::HW + xcol + e];
+      const float s0 = pa == 0 ? (e ? pre[0].y : pre[0].x) : rd(0, 0)[pi];
+      const float s1 = pa == 0 ? (e ? pre[1].y : pre[1].x) : rd(0, 1)[pi];
+      float& A = e ? dxA.y : dxA.x;
+      float& B = e ? dxB.y : dxB.x;
+      A = pml_term_c(A, ik, b, cc, s0, o0, pi);
+      B = pml_term_c(B, ik, b, cc, s1, o1, pi);
+    }
+  }
+  // y and z: the two nodes share the coefficients
+  auto both = [&](int a, int pi, const float* cf, float2& A, float2& B) {
+    const float2 ik = bc2(cf[3 * H + 0]), b = bc2(cf[3 * H + 1]), cc = bc2(cf[3 * H + 2]);
+    float2 s0, s1;
+    if (pa == a) {
+      s0 = pre[0];
+      s1 = pre[1];
+    } else {
+      const float* r0 = rd(a, 0);
+      const float* r1 = rd(a, 1);
+      s0 = make_float2(r0[pi], c.own1 ? r0[pi + 1] : 0.0f);
+      s1 = make_float2(r1[pi], c.own1 ? r1[pi + 1] : 0.0f);
+    }
+    const float2 p0 = fma2(b, s0, mul2(cc, A));
+    const float2 p1 = fma2(b, s1, mul2(cc, B));
+    float* o0 = wt(a, 0);
+    float* o1 = wt(a, 1);
+    if (o0) {
+      o0[pi] = p0.x;
+      o1[pi] = p1.x;
+      if (c.own1) {
+        o0[pi + 1] = p0.y;
+        o1[pi + 1] = p1.y;
+      }
+    }
+    A = fma2(ik, A, p0);
+    B = fma2(ik, B, p1);
+  };
+  if (c.sy >= 0) both(1, pl.py_plane + c.py0, cfy, dyA, dyB);
+  if (pl.sz >= 0) both(2, pl.pz_plane + c.pz0, cfz, dzA, dzB);
+}
+
+// H~^{n+1/2} of the pair whose node 0 sits at staged offset o (even).
+__device__ __forceinline__ void pair_h(const StepGrid<float>& G, const PairCol& c, const Plane& pl, int sel, bool wr,
+                                       const float* Fk, const float* Fn, int o, int PL, int BXT, const float* cfx,
+                                       int xcol, const float* cfy, const float* cfz, int pa, const float2* pre,
+                                       float2& hx, float2& hy, float2& hz) {
+  const float2 ex = ld2(Fk + o), ey = ld2(Fk + PL + o), ez = ld2(Fk + 2 * PL + o);
+  float2 dyEz = sub2(ld2(Fk + 2 * PL + o + BXT), ez);
+  float2 dzEy = sub2(ld2(Fn + PL + o), ey);
+  float2 dzEx = sub2(ld2(Fn + o), ex);
+  float2 dxEz = sub2(make_float2(ez.y, Fk[2 * PL + o + 2]), ez);
+  float2 dxEy = sub2(make_float2(ey.y, Fk[PL + o + 2]), ey);
+  float2 dyEx = sub2(ld2(Fk + o + BXT), ex);
+  if (c.sx0 >= 0 || c.sx1 >= 0 || c.sy >= 0 || pl.sz >= 0)
+    pair_cpml<1>(G, c, pl, sel, wr, cfx, xcol, cfy, cfz, pa, pre, dxEz, dxEy, dyEx, dyEz, dzEy, dzEx);
+  const float2 ncH = bc2(-G.cH);
+  hx = fma2(ncH, sub2(dyEz, dzEy), ld2(Fk + 3 * PL + o));
+  hy = fma2(ncH, sub2(dzEx, dxEz), ld2(Fk + 4 * PL + o));
+  hz = fma2(ncH, sub2(dxEy, dyEx), ld2(Fk + 5 * PL + o));
+}
+
+// Sources, gain and PEC of one node of the pair (the general part of the E
+// update, scalar): `en` holds fmad(cE, curl, E^n) on entry.
+template <bool GAIN>
+__device__ __forceinline__ void node_extras(const StepGrid<float>& G, const double* sg, int i, int j,
+                                            const Plane& pl, int sel, long long n, long long cidx, unsigned m,
+                                            unsigned srcmask, const float ec[3], float en[3]) {
+  float src[3] = {0.0f, 0.0f, 0.0f};
+  if (srcmask) {
+    Column c;
+    c.i = i;
+    c.j = j;
+    c.src = srcmask;
+    source_drive(G, sg, c, pl, src[0], src[1], src[2]);
+  }
+  const bool gcell = GAIN && G.gain && ((m >> 6) & 1);
+  float dP[3] = {0.0f, 0.0f, 0.0f};
+  GainState<float> gs{};
+  if (GAIN && gcell) {
+    load_gain(G, sel, cidx, gs);
+    const float dn12 = G.n12eq + (gs.d1 - gs.d2);
+    const float drive = G.a3 * dn12;
+    const float a1 = G.a1, a2 = G.a2;
+    float Pn[3];
+    Pn[0] = fmad(drive, ec[0], fmad(a1, gs.pnx, -(a2 * gs.pmx)));
+    Pn[1] = fmad(drive, ec[1], fmad(a1, gs.pny, -(a2 * gs.pmy)));
+    Pn[2] = fmad(drive, ec[2], fmad(a1, gs.pnz, -(a2 * gs.pmz)));
+    if (G.noise != 0.0f) {
+      float xa, xb, xc;
+      const long long lcell = ((long long)pl.k * G.ny + j) * G.nx + i;
+      gain_normals(G.seed, lcell, n, xa, xb, xc);
+      Pn[0] = fmad(G.noise, xa, Pn[0]);
+      Pn[1] = fmad(G.noise, xb, Pn[1]);
+      Pn[2] = fmad(G.noise, xc, Pn[2]);
+    }
+    dP[0] = Pn[0] - gs.pnx;
+    dP[1] = Pn[1] - gs.pny;
+    dP[2] = Pn[2] - gs.pnz;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) G.P[sel ^ 1][q][cidx] = Pn[q];
+  }
+  if (srcmask || (GAIN && gcell)) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) en[q] = fmad(-G.cP[(m >> (2 * q)) & 3], dP[q] + src[q], en[q]);
+  }
+  if (j == 0 || pl.pecz) en[0] = 0.0f;
+  if (i == 0 || pl.pecz) en[1] = 0.0f;
+  if (i == 0 || j == 0) en[2] = 0.0f;
+  if (GAIN && gcell) {
+    const float hx_ = 0.5f * (en[0] + ec[0]), hy_ = 0.5f * (en[1] + ec[1]), hz_ = 0.5f * (en[2] + ec[2]);
+    const float r = G.q * fmad(hz_, dP[2], fmad(hy_, dP[1], hx_ * dP[0]));
+    const float inc1 = fmad(G.w[0], r, fmad(G.D[0][2], gs.d3, fmad(G.D[0][1], gs.d2, G.D[0][0] * gs.d1)));
+    const float inc2 = fmad(G.w[1], r, fmad(G.D[1][2], gs.d3, fmad(G.D[1][1], gs.d2, G.D[1][0] * gs.d1)));
+    const float inc3 = fmad(G.w[2], r, fmad(G.D[2][2], gs.d3, fmad(G.D[2][1], gs.d2, G.D[2][0] * gs.d1)));
+    // compensated (Kahan) accumulation of the population deviations
+    const float y1 = inc1 - gs.c1, y2 = inc2 - gs.c2, y3 = inc3 - gs.c3;
+    const float t1 = gs.d1 + y1, t2 = gs.d2 + y2, t3 = gs.d3 + y3;
+    G.cmp[0][cidx] = (t1 - gs.d1) - y1;
+    G.cmp[1][cidx] = (t2 - gs.d2) - y2;
+    G.cmp[2][cidx] = (t3 - gs.d3) - y3;
+    G.dN[0][cidx] = t1;
+    G.dN[1][cidx] = t2;
+    G.dN[2][cidx] = t3;
+  }
+}
+
+// Sources of the grid that can touch node (i, j) (bit s: source s).
+__device__ __forceinline__ unsigned node_sources(const StepGrid<float>& G, int i, int j) {
+  unsigned m = 0;
+  for (int s = 0; s < G.nsrc; ++s) {
+    const SrcDev& S = G.src[s];
+    bool hit;
+    if (S.kind == 0) hit = (i == S.i && j == S.j);
+    else if (S.axis == 2) hit = (i >= S.lo1 && i < S.hi1 && j >= S.lo2 && j < S.hi2);
+    else if (S.axis == 0) hit = (i == S.index && j >= S.lo1 && j < S.hi1);
+    else hit = (j == S.index && i >= S.lo2 && i < S.hi2);
+    if (hit) m |= 1u << s;
+  }
+  return m;
+}
+
+#ifndef FDTD_PAIR_MIN_BLOCKS
+#define FDTD_PAIR_MIN_BLOCKS 2
+#endif
+
+template <bool GAIN, int OY>
+__global__ void __launch_bounds__(PairLayout<OY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 / OY)
+    k_step_pair(const StepGrid<float>* __restrict__ grids, const TmaGrid* __restrict__ maps,
+                const int4* __restrict__ items, int nitems, int offset) {
+  using L = PairLayout<OY>;
+  constexpr int S = kTmaStages;
+  constexpr int AX = L::AX, BXT = L::BXT, PL = L::PL, HW = L::HW, OPL = L::OPL, NTO = L::NTO, NC = L::NC;
+  constexpr unsigned TX_BYTES = (unsigned)(6 * PL * sizeof(float) + L::OX * OY);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  StepGrid<float>& G = *reinterpret_cast<StepGrid<float>*>(smem);
+  double* sg = reinterpret_cast<double*>(smem + L::sg_off);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::bar_off);
+  float4* ctab = reinterpret_cast<float4*>(smem + L::ctab_off);
+  unsigned char* stages = smem + L::stage_off;
+  float* out = reinterpret_cast<float*>(smem + L::out_off);
+  float* sHx = reinterpret_cast<float*>(smem + L::h_off);
+  float* sHy = sHx + L::HPL;
+  float* sHz = sHy + L::HPL;
+  float* cfx = reinterpret_cast<float*>(smem + L::coef_off);
+  float* cfy = cfx + L::CXN;
+  float* cfz = cfy + L::CYN;
+  const int tid = threadIdx.x;
+  const bool halo = tid >= NTO;       // the ninth warp
+  const int lane = tid & 31;
+  const bool producer = tid == NTO;   // issues the TMA copies
+  const int tx = halo ? 0 : tid % L::PXT, ty = halo ? 0 : tid / L::PXT;
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  unsigned ld = 0;  // plane loads issued by this block so far (same value in every thread)
+  int cur = -1;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int4 item = items[it];
+    __syncthreads();
+    const bool fresh = item.x != cur;
+    if (fresh) {
+      load_record(grids + item.x, smem, tid, L::NT);
+      cur = item.x;
+    }
+    __syncthreads();
+    if (fresh && tid < 64) {
+      // S/eps of the three E components for every material class triple
+      const int c0 = tid & 3, c1 = (tid >> 2) & 3, c2 = (tid >> 4) & 3;
+      ctab[tid] = make_float4(G.cE[c0 < 3 ? c0 : 2], G.cE[c1 < 3 ? c1 : 2], G.cE[c2 < 3 ? c2 : 2], 0.0f);
+    }
+    const long long n = G.step + offset;
+    if (n >= G.step_end) continue;
+    source_waveforms(G, n, tid, sg);
+
+    const int nx = G.nx, ny = G.ny, px = G.px;
+    const int x0 = item.y, y0 = item.z, z0 = item.w & 0xffff, z1 = (item.w >> 16) & 0xffff;
+    const int kstart = z0 > 0 ? z0 - 1 : z0;
+    const int NP = z1 - kstart + 1;  // planes kstart .. z1 (E of plane z1 feeds H of plane z1-1)
+    const int sel = (int)(n & 1);
+    const CUtensorMap* fmap = &maps[item.x].fields;
+    const CUtensorMap* mmap = &maps[item.x].mat;
+    const CUtensorMap* smap = &maps[item.x].store;
+    const unsigned q0 = ld;
+
+    auto issue = [&](unsigned q, int plane) {
+      const int s = (int)(q % S);
+      unsigned char* dst = stages + (size_t)s * L::stage_bytes;
+      mbar_arrive_expect_tx(&full[s], TX_BYTES);
+      tma_load_4d(dst, fmap, x0 - AX, y0 - 1, plane, sel * 6, &full[s]);
+      tma_load_3d(dst + L::field_bytes, mmap, x0, y0, plane, &full[s]);
+    };
+    if (producer) {
+      fence_proxy_async_smem();
+      for (int p = 0; p < S && p < NP; ++p) issue(q0 + p, kstart + p);
+    }
+    ld = q0 + (unsigned)(NP < S ? NP : S);
+
+    // this thread's node pair: owned (i0, j), or on the halo row / column
+    bool valid;   // node 0 of the pair is a grid node whose H this thread provides
+    int o;        // staged offset of node 0
+    int hcol;     // H buffer offset of node 0
+    PairCol pc;
+    if (!halo) {
+      const int i0 = x0 + 2 * tx, j = y0 + ty;
+      valid = i0 < nx && j < ny;
+      make_pair_col(G, valid ? i0 : 0, valid ? j : 0, pc);
+      o = (ty + 1) * BXT + AX + 2 * tx;
+      hcol = (ty + 1) * HW + 2 + 2 * tx;
+    } else if (lane < 16) {
+      const int i0 = x0 + 2 * lane, j = y0 - 1;
+      valid = y0 > 0 && i0 < nx;
+      make_pair_col(G, valid ? i0 : 0, valid ? j : 0, pc);
+      o = AX + 2 * lane;
+      hcol = 2 + 2 * lane;
+    } else {
+      const int r = lane - 16, j = y0 + r;
+      valid = r < OY && x0 > 0 && j < ny;  // node 1 of the pair (x0-2, x0-1) is the halo node
+      make_pair_col(G, valid ? x0 - 2 : 0, valid ? j : 0, pc);
+      pc.sx0 = -1;  // node x0-2 is recomputed only to keep the pair aligned: no CPML for it
+      o = (r + 1) * BXT + AX - 2;
+      hcol = (r + 1) * HW;
+    }
+    if (!valid) pc.sx0 = pc.sx1 = pc.sy = -1;
+    const int xcol = hcol - (hcol / HW) * HW;  // column of node 0 in the x coefficient rows
+    const int yrow = halo ? (lane < 16 ? 0 : lane - 15) : ty + 1;
+    const long long cbase = (long long)pc.j * px + pc.i0;
+    const long long pstride = (long long)px * ny;
+    unsigned src0 = 0, src1 = 0;
+    if (!halo && valid && G.nsrc) {
+      src0 = node_sources(G, pc.i0, pc.j);
+      src1 = pc.own1 ? node_sources(G, pc.i0 + 1, pc.j) : 0u;
+    }
+
+    // slab axis whose CPML memory is fetched ahead: z for the planes of a z
+    // slab, else x for pairs in an x slab, else y
+    const int col_axis = (pc.sx0 >= 0 || pc.sx1 >= 0) ? 0 : (pc.sy >= 0 ? 1 : -1);
+    const int zs_lo = G.Sd[2] ? G.L[4] : 0, zs_hi = G.Sd[2] ? G.nz - G.L[5] : G.nz;
+    auto plane_slab = [&](int plane) {
+      return (plane < zs_lo || plane >= zs_hi) ? slab_index(plane, G.nz, G.L[4], G.L[5]) : -1;
+    };
+    // slot base of this thread's pair in a stage's psi area
+    const int sbase = halo ? 4 * NC + 2 * lane : 2 * tid;
+    const int sstride = halo ? L::NHC : NC;
+    auto issue_psi = [&](int plane, int stage) {
+      float* slots = reinterpret_cast<float*>(stages + (size_t)stage * L::stage_bytes + L::field_bytes + L::mat_bytes);
+      const int sz = plane_slab(plane);
+      if (valid && plane < z1 && (sz >= 0 || col_axis >= 0)) {
+        const int a = sz >= 0 ? 2 : col_axis;
+        const bool eside = !halo && plane >= z0;  // E-side memory of the planes this tile updates
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          int pi;
+          if (a == 2) {
+            if (e == 1 && !pc.own1) continue;
+            pi = sz * ny * nx + pc.pz0 + e;
+          } else if (a == 0) {
+            if ((e ? pc.sx1 : pc.sx0) < 0) continue;
+            pi = plane * ny * G.Sd[0] + (e ? pc.px1 : pc.px0);
+          } else {
+            if (e == 1 && !pc.own1) continue;
+            pi = plane * G.Sd[1] * nx + pc.py0 + e;
+          }
+          cp_async_elem(slots + sbase + e, G.psiH[sel][a][0] + pi);
+          cp_async_elem(slots + sstride + sbase + e, G.psiH[sel][a][1] + pi);
+          if (eside) {
+            cp_async_elem(slots + 2 * NC + sbase + e, G.psiE[a][0] + pi);
+            cp_async_elem(slots + 3 * NC + sbase + e, G.psiE[a][1] + pi);
+          }
+        }
+      }
+      cp_async_commit();
+    };
+
+    // grading coefficients of the columns, rows and planes this item touches
+    // (joined to the first plane's copy group; visible after the barrier below)
+    {
+      const bool any_slab = G.Sd[0] || G.Sd[1] || G.Sd[2];
+      for (int e = tid; any_slab && e < L::CXN + L::CYN + 6 * (NP - 1); e += L::NT) {
+        int a, pos, hq;
+        float* dst;
+        if (e < L::CXN) {
+          hq = e / HW;
+          a = 0; pos = x0 - 2 + (e - hq * HW); dst = cfx + e;
+        } else if (e < L::CXN + L::CYN) {
+          const int r = e - L::CXN;
+          hq = r % 6;
+          a = 1; pos = y0 - 1 + r / 6; dst = cfy + r;
+        } else {
+          const int r = e - L::CXN - L::CYN;
+          hq = r % 6;
+          a = 2; pos = kstart + r / 6; dst = cfz + r;
+        }
+        const int lim = a == 0 ? nx : (a == 1 ? ny : G.nz);
+        if (G.Sd[a] && pos >= 0 && pos < lim) cp_async_elem(dst, G.prof[a][hq / 3][hq % 3] + pos);
+      }
+    }
+    for (int p = 0; p < S; ++p) issue_psi(kstart + p, (int)((q0 + p) % S));
+    cp_async_wait<S - 1>();
+    __syncthreads();
+
+    float2 hPx = make_float2(0.0f, 0.0f), hPy = make_float2(0.0f, 0.0f);
+    bool ok = true;
+
+    for (int p = 0; p < NP - 1; ++p) {
+      const int k = kstart + p;
+      const unsigned q = q0 + p;
+      if (p == 0) ok = ok && mbar_wait(&full[q % S], (q / S) & 1);
+      ok = ok && mbar_wait(&full[(q + 1) % S], ((q + 1) / S) & 1);
+      cp_async_wait<S - 1>();  // this thread's CPML memory of plane p
+      const unsigned char* stg = stages + (size_t)(q % S) * L::stage_bytes;
+      const float* Fk = reinterpret_cast<const float*>(stg);
+      const float* Fn = reinterpret_cast<const float*>(stages + (size_t)((q + 1) % S) * L::stage_bytes);
+      const float* slots = reinterpret_cast<const float*>(stg + L::field_bytes + L::mat_bytes);
+      const bool active = k >= z0;
+      const Plane pl = make_plane(G, k);
+      const float* cz = cfz + 6 * p;
+
+      // CPML memory of this pair fetched ahead
+      float2 pre[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+      float2 preE[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+      const int pa = valid ? (pl.sz >= 0 ? 2 : col_axis) : -1;
+      if (pa >= 0) {
+        pre[0] = ld2(slots + sbase);
+        pre[1] = ld2(slots + sstride + sbase);
+        if (!halo) {
+          preE[0] = ld2(slots + 2 * NC + sbase);
+          preE[1] = ld2(slots + 3 * NC + sbase);
+        }
+      }
+
+      float2 hx = make_float2(0.0f, 0.0f), hy = hx, hz = hx;
+      if (ok && valid) {
+        pair_h(G, pc, pl, sel, !halo && active, Fk, Fn, o, PL, BXT, cfx, xcol, cfy + 6 * yrow, cz, pa, pre, hx, hy,
+               hz);
+        if (!pc.own1) hx.y = hy.y = hz.y = 0.0f;
+      }
+      if (halo && lane >= 16) {
+        if (lane - 16 < OY) {
+          sHx[hcol + 1] = hx.y;
+          sHy[hcol + 1] = hy.y;
+          sHz[hcol + 1] = hz.y;
+        }
+      } else {
+        st2(sHx + hcol, hx);
+        st2(sHy + hcol, hy);
+        st2(sHz + hcol, hz);
+      }
+      // the output tile buffer must have been read by the previous plane's store
+      if (producer) bulk_wait_read0();
+      if (__syncthreads_or(!ok)) {
+        cp_async_wait<0>();
+        if (producer) {
+          atomicOr(G.err, 2);
+          bulk_wait0();
+        }
+        return;
+      }
+
+      if (active && !halo) {
+        float2 enx = make_float2(0.0f, 0.0f), eny = enx, enz = enx;
+        if (valid) {
+          const int oh = hcol;
+          const float2 ex = ld2(Fk + o), ey = ld2(Fk + PL + o), ez = ld2(Fk + 2 * PL + o);
+          float2 dyHz = sub2(hz, ld2(sHz + oh - HW));
+          float2 dzHy = sub2(hy, hPy);
+          float2 dzHx = sub2(hx, hPx);
+          float2 dxHz = sub2(hz, make_float2(sHz[oh - 1], hz.x));
+          float2 dxHy = sub2(hy, make_float2(sHy[oh - 1], hy.x));
+          float2 dyHx = sub2(hx, ld2(sHx + oh - HW));
+          if (pc.sx0 >= 0 || pc.sx1 >= 0 || pc.sy >= 0 || pl.sz >= 0)
+            pair_cpml<0>(G, pc, pl, sel, true, cfx, xcol, cfy + 6 * yrow, cz, pa, preE, dxHz, dxHy, dyHx, dyHz,
+                         dzHy, dzHx);
+          const float2 curlx = sub2(dyHz, dzHy);
+          const float2 curly = sub2(dzHx, dxHz);
+          const float2 curlz = sub2(dxHy, dyHx);
+          const unsigned mm = *reinterpret_cast<const unsigned short*>(stg + L::field_bytes + 2 * tid);
+          const unsigned m0 = mm & 0xffu, m1 = mm >> 8;
+          const float4 c0 = ctab[m0 & 63u], c1 = ctab[m1 & 63u];
+          enx = fma2(make_float2(c0.x, c1.x), curlx, ex);
+          eny = fma2(make_float2(c0.y, c1.y), curly, ey);
+          enz = fma2(make_float2(c0.z, c1.z), curlz, ez);
+          const bool pec = pc.i0 == 0 || pc.j == 0 || pl.pecz;
+          const bool gainpair = GAIN && G.gain && (((m0 | m1) >> 6) & 1);
+          if (src0 | src1 | pec | gainpair) {
+            const long long cidx = cbase + (long long)k * pstride;
+            float ec[3] = {ex.x, ey.x, ez.x}, en[3] = {enx.x, eny.x, enz.x};
+            node_extras<GAIN>(G, sg, pc.i0, pc.j, pl, sel, n, cidx, m0, src0, ec, en);
+            enx.x = en[0];
+            eny.x = en[1];
+            enz.x = en[2];
+            if (pc.own1) {
+              float ec1[3] = {ex.y, ey.y, ez.y}, en1[3] = {enx.y, eny.y, enz.y};
+              node_extras<GAIN>(G, sg, pc.i0 + 1, pc.j, pl, sel, n, cidx + 1, m1, src1, ec1, en1);
+              enx.y = en1[0];
+              eny.y = en1[1];
+              enz.y = en1[2];
+            }
+          }
+        }
+        st2(out + 2 * tid, enx);
+        st2(out + OPL + 2 * tid, eny);
+        st2(out + 2 * OPL + 2 * tid, enz);
+        st2(out + 3 * OPL + 2 * tid, hx);
+        st2(out + 4 * OPL + 2 * tid, hy);
+        st2(out + 5 * OPL + 2 * tid, hz);
+        fence_proxy_async_smem();
+      }
+      hPx = hx;
+      hPy = hy;
+      __syncthreads();
+      if (producer) {
+        if (active) {
+          // E^{n+1} and H~^{n+1/2} of the owned tile (clipped at the grid edge) to set (n+1)&1
+          tma_store_4d(smap, out, x0, y0, k, (sel ^ 1) * 6);
+          bulk_commit();
+        }
+        // stage of plane p is free: refill it with plane p + S
+        if (p + S < NP) {
+          fence_proxy_async_smem();
+          issue(q + S, kstart + p + S);
+        }
+      }
+      issue_psi(kstart + p + S, (int)(q % S));
+    }
+    ld = q0 + (unsigned)NP;
+  }
+  cp_async_wait<0>();
+  if (producer) bulk_wait0();
+}
+
+int step_pair_blocks_per_sm(bool gain, int oy) {
+  const size_t smem = step_pair_smem_bytes(oy);
+  const void* f;
+  int threads;
+  if (oy == 8) {
+    f = gain ? (const void*)k_step_pair<true, 8> : (const void*)k_step_pair<false, 8>;
+    threads = PairLayout<8>::NT;
+  } else {
+    f = gain ? (const void*)k_step_pair<true, 16> : (const void*)k_step_pair<false, 16>;
+    threads = PairLayout<16>::NT;
+  }
+  cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_step_pair(const StepGrid<float>* grids, const TmaGrid* maps, const int4* items, int nitems,
+                             int offset, int oy, bool gain, int grid_blocks, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  const int blocks = (grid_blocks > 0 && grid_blocks < nitems) ? grid_blocks : nitems;
+  const size_t smem = step_pair_smem_bytes(oy);
+  if (oy == 8) {
+    auto f = gain ? k_step_pair<true, 8> : k_step_pair<false, 8>;
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    f<<<blocks, PairLayout<8>::NT, smem, st>>>(grids, maps, items, nitems, offset);
+  } else {
+    auto f = gain ? k_step_pair<true, 16> : k_step_pair<false, 16>;
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    f<<<blocks, PairLayout<16>::NT, smem, st>>>(grids, maps, items, nitems, offset);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace fdtd

@@ -73,6 +73,7 @@ SIGNATURES = {
                             C.POINTER(C.c_int32)],
     "fdtd_set_launch": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
     "fdtd_set_kernel": [_P, C.c_int32],
+    "fdtd_kernel_in_use": [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "fdtd_step_n": [_P, C.c_int64],
     "fdtd_sync": [_P],
     "fdtd_steps_done": [_P, C.POINTER(C.c_int64)],
@@ -267,9 +268,17 @@ class Grid:
         check(self._lib.fdtd_set_launch(self.h, int(bx), int(by), int(zdepth), int(grid_blocks)))
 
     def set_kernel(self, kind):
-        """0 automatic, 1 plain-load step kernel, 2 TMA-staged step kernel."""
-        kinds = {"auto": 0, "plain": 1, "tma": 2}
+        """0 automatic, 1 plain-load step kernel, 2 TMA-staged step kernel,
+        3 paired TMA-staged kernel (binary32 grids)."""
+        kinds = {"auto": 0, "plain": 1, "tma": 2, "pair": 3}
         check(self._lib.fdtd_set_kernel(self.h, int(kinds.get(kind, kind))))
+
+    def kernel_in_use(self):
+        """(kind, rows): the step kernel of the grid's launches (1 plain, 2 TMA,
+        3 paired) and the rows of its tile; valid after the first step."""
+        kind, rows = C.c_int32(), C.c_int32()
+        check(self._lib.fdtd_kernel_in_use(self.h, C.byref(kind), C.byref(rows)))
+        return int(kind.value), int(rows.value)
 
     def set_step_limit(self, limit):
         check(self._lib.fdtd_set_step_limit(self.h, int(limit)))
@@ -371,7 +380,7 @@ class Grid:
         self.close()
 
 
-KERNELS = {"auto": 0, "plain": 1, "tma": 2}
+KERNELS = {"auto": 0, "plain": 1, "tma": 2, "pair": 3}
 
 
 class Batch:

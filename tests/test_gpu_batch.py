@@ -31,7 +31,7 @@ def _state(g):
     return out
 
 
-@pytest.mark.parametrize("kernel,graph", [("tma", 0), ("tma", 7), ("plain", 0), ("plain", 5)])
+@pytest.mark.parametrize("kernel,graph", [("tma", 0), ("tma", 7), ("plain", 0), ("plain", 5), ("pair", 0), ("pair", 7)])
 def test_batch_equals_members_alone(kernel, graph):
     from paper_0802_3775_gb300.fdtd import Batch, Grid
     specs = _members()
@@ -44,7 +44,7 @@ def test_batch_equals_members_alone(kernel, graph):
         g.close()
     grids = [Grid.from_spec(s) for s in specs]
     b = Batch(grids)
-    b.set_launch(kernel, 8 if kernel == "tma" else 8, 0, 0)
+    b.set_launch(kernel, 16 if kernel == "pair" else 8, 0, 0)
     b.set_graph(graph)
     b.step(23)
     b.step(37)
@@ -56,13 +56,14 @@ def test_batch_equals_members_alone(kernel, graph):
     b.close()
 
 
-def test_batch_step_limits_and_persistent_launch():
+@pytest.mark.parametrize("kernel,by", [("tma", 4), ("pair", 16)])
+def test_batch_step_limits_and_persistent_launch(kernel, by):
     from paper_0802_3775_gb300.fdtd import Batch, Grid
     specs = _members()
     grids = [Grid.from_spec(s) for s in specs]
     grids[1].set_step_limit(25)
     b = Batch(grids)
-    b.set_launch("tma", 4, 9, 40)   # persistent: 40 blocks looping over the items
+    b.set_launch(kernel, by, 9, 40)   # persistent: 40 blocks looping over the items
     b.step(50)
     b.sync()
     assert grids[1].steps_done == 25

@@ -82,7 +82,8 @@ def test_fp64_small_opal_all_observers(source):
 
 
 LAUNCHES = [("tma", (32, 8, 0, 0)), ("tma", (32, 4, 7, 0)), ("tma", (32, 2, 3, 5)), ("plain", (32, 8, 0, 0)),
-            ("plain", (64, 4, 7, 0)), ("plain", (32, 16, 3, 5)), ("plain", (16, 2, 0, 0))]
+            ("plain", (64, 4, 7, 0)), ("plain", (32, 16, 3, 5)), ("plain", (16, 2, 0, 0)),
+            ("pair", (32, 16, 0, 0)), ("pair", (32, 8, 5, 0)), ("pair", (32, 16, 3, 7))]
 
 
 @pytest.mark.parametrize("kernel,launch", LAUNCHES)
@@ -129,8 +130,53 @@ def test_results_do_not_depend_on_launch_shape():
             assert np.array_equal(P, runs[0][1])
             assert np.array_equal(N, runs[0][2])
             assert np.array_equal(T, runs[0][3])
-    # the two kernels share the per-node arithmetic
+    # the kernels share the per-node arithmetic; the paired kernel performs
+    # the TMA kernel's operations lane by lane
     assert rel_l2(out["tma"][0][0], out["plain"][0][0]) <= 1e-6
+    for a, b in zip(out["pair"][0], out["tma"][0]):
+        assert np.array_equal(a, b)
+
+
+def _ragged_spec(gain):
+    """Odd grid sizes and odd absorbing-slab thicknesses: node pairs that
+    straddle a slab edge, a last pair with one node off the grid, partial
+    tiles in x and y."""
+    spec = small_opal(n_cells=2, res=9, npml=5, precision="f32", source="sheet", gain=gain, sigma=0.07, seed=11)
+    spec.npml = (5, 6, 7, 5, 5, 6)
+    spec.sources.append(inputs.SourceSpec(kind="point", comp=1, pos=(9, 7, 11), f0_hat=0.75, rel_bw=0.3))
+    return spec
+
+
+@pytest.mark.parametrize("with_gain", [False, True])
+def test_paired_kernel_is_bitwise_equal_to_tma_kernel(with_gain):
+    gain = inputs.GainSpec(pump=5e11, noise_amp=1e-3, init="ground") if with_gain else None
+    spec = _ragged_spec(gain)
+    runs = []
+    for kernel, launch in [("tma", (32, 8, 0, 0)), ("pair", (32, 16, 0, 0)), ("pair", (32, 8, 4, 3))]:
+        g = gpu_grid(spec)
+        g.set_kernel(kernel)
+        g.set_launch(*launch)
+        g.step(160)
+        r = [g.read_fields(), g.read_probes(), g.read_flux()]
+        if with_gain:
+            r += [g.read_gain(0), g.read_gain(1), g.read_gain(3)]
+        runs.append(r)
+    for other in runs[1:]:
+        for a, b in zip(other, runs[0]):
+            assert np.array_equal(a, b)
+
+
+def test_paired_kernel_matches_oracle_on_ragged_grid():
+    gain = inputs.GainSpec(pump=5e11, noise_amp=1e-3, init="ground")
+    spec = _ragged_spec(gain)
+    g = gpu_grid(spec)
+    g.set_kernel("pair")
+    o = oracle_grid(spec, coef32=True)
+    g.step(250)
+    o.step(250)
+    assert _fields_gpu_vs_oracle(g, o) <= 1e-5
+    assert rel_l2(g.read_flux(0), o.flux_series()[0]) <= 1e-4
+    assert rel_l2(g.read_gain(3), o.dN[1:].transpose(0, 3, 2, 1)) <= 1e-6
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])
