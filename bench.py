@@ -159,7 +159,7 @@ def configure_grid(args, g):
 
 def configure_batch(args, b):
     if args.kernel != "auto" or args.by:
-        b.set_launch(args.kernel, args.by or 8, 0, 0)
+        b.set_launch(args.kernel, args.by, 0, 0)
 
 
 def run_gpu(args, rank, world, dist):

@@ -187,21 +187,26 @@ int fdtd_add_flux_plane(fdtd_grid* g, int32_t axis, int32_t index, double sign, 
  * past record_capacity overwrites the oldest entries. */
 int fdtd_step_n(fdtd_grid* g, int64_t n);
 
-/* Launch shape of the step kernel: blocks of bx x by threads own tiles of
- * (bx-1) x (by-1) columns and march z-ranges of `zdepth` planes (0: chosen
- * from the grid size); grid_blocks > 0 makes the launch persistent with that
- * many blocks looping over the tiles (0: one block per tile).  Results do not
- * depend on the shape.  Needs bx, by >= 2, bx*by a multiple of 32, <= 512. */
+/* Launch shape of the step kernel: tile rows `by` (see fdtd_set_kernel for
+ * how each kernel reads bx and by; before this call every kernel uses its
+ * default tile), z-ranges of `zdepth` planes per work item (0: chosen from
+ * the grid size; the TMA kernels cap it at 31), and grid_blocks > 0 makes the
+ * launch persistent with that many blocks looping over the work items (0: one
+ * block per item).  Results do not depend on the shape.  Needs bx, by >= 2,
+ * bx*by a multiple of 32, <= 512. */
 int fdtd_set_launch(fdtd_grid* g, int32_t bx, int32_t by, int32_t zdepth, int32_t grid_blocks);
 
-/* Step-kernel variant: 0 = automatic (the TMA-staged kernel when no axis is
- * periodic, else the plain-load kernel), 1 = plain-load kernel (blocks of
- * bx x by threads own (bx-1) x (by-1) columns), 2 = TMA-staged kernel (blocks
- * of 32 x by threads own 32 x by columns; E_INVAL on periodic grids),
- * 3 = paired TMA-staged kernel, binary32 grids only (each thread updates two
- * x-adjacent nodes with packed f32x2 arithmetic; tiles of 32 x 16 columns, or
- * 32 x 8 when by == 8; E_INVAL on periodic or binary64 grids).  All perform
- * the same arithmetic per node and give identical results. */
+/* Step-kernel variant: 0 = automatic (the paired kernel for binary32 and
+ * the TMA-staged kernel for binary64 grids when no axis is periodic, else the
+ * plain-load kernel), 1 = plain-load kernel (blocks of bx x by threads own
+ * (bx-1) x (by-1) columns; default 32 x 8), 2 = TMA-staged kernel (blocks of
+ * 32 x by threads own 32 x by columns, by 4 or 8, default 8; E_INVAL on
+ * periodic grids), 3 = paired TMA-staged kernel, binary32 grids only (each
+ * thread updates two x-adjacent nodes with packed f32x2 arithmetic; tiles of
+ * 32 x by columns, by 8 or 16, default 16; E_INVAL on periodic or binary64
+ * grids).  A launch shape a kernel cannot take selects the next more general
+ * one (3 -> 2 -> 1).  All perform the same arithmetic per node and give
+ * identical results. */
 int fdtd_set_kernel(fdtd_grid* g, int32_t kind);
 
 /* The step kernel the grid's launches use under its current settings
@@ -266,8 +271,10 @@ int fdtd_set_step_limit(fdtd_grid* g, int64_t limit);
 typedef struct fdtd_batch fdtd_batch;
 int fdtd_batch_create(fdtd_grid* const* grids, int32_t n, void* stream, fdtd_batch** out);
 int fdtd_batch_destroy(fdtd_batch* b);
-/* kernel: as fdtd_set_kernel; by: rows of the tile; zdepth: planes per work
- * item (0: whole z); grid_blocks > 0: persistent launch with that many blocks. */
+/* kernel: as fdtd_set_kernel; by: rows of the tile (0: the kernel's
+ * default); zdepth: planes per work item (0: 16); grid_blocks > 0: persistent
+ * launch with that many blocks.  Members that cannot share the kernel or the
+ * tile all fall back to the more general kernel. */
 int fdtd_batch_set_launch(fdtd_batch* b, int32_t kernel, int32_t by, int32_t zdepth, int32_t grid_blocks);
 /* Capture `steps_per_graph` steps (step + observation launches and the
  * counter update) into a CUDA graph replayed by fdtd_batch_step_n; 0 = off.

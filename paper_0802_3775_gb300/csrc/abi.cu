@@ -326,7 +326,7 @@ int fdtd_kernel_in_use(fdtd_grid* g, int32_t* kind, int32_t* rows) {
     if (!kind || !rows) return set_error(FDTD_E_INVAL, "null output");
     if (!G->finalized) return set_error(FDTD_E_STATE, "the launch plan is made at the first step");
     *kind = G->uses_pair() ? 3 : (G->uses_tma() ? 2 : 1);
-    *rows = G->uses_tma() ? G->tile_rows() : G->by - 1;
+    *rows = G->tile_rows();
     return FDTD_OK;
   });
 }
@@ -507,7 +507,7 @@ int fdtd_batch_destroy(fdtd_batch* b) {
 int fdtd_batch_set_launch(fdtd_batch* b, int32_t kernel, int32_t by, int32_t zdepth, int32_t grid_blocks) {
   return guarded([&]() -> int {
     CHECK_BATCH(b);
-    if (kernel < 0 || kernel > 3 || by < 2 || by > 16 || zdepth < 0 || grid_blocks < 0)
+    if (kernel < 0 || kernel > 3 || by < 0 || by == 1 || by > 16 || zdepth < 0 || grid_blocks < 0)
       return set_error(FDTD_E_INVAL, "batch launch shape");
     B->kernel_kind = kernel;
     B->bx = 32;

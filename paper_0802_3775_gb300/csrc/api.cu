@@ -171,6 +171,7 @@ struct GridImpl final : GridBase {
   bool use_tma = false;
   bool use_pair = false;  // paired binary32 kernel (TMA staging, tiles of 32 x tile_oy)
   int tile_oy = 8;
+  int by_eff = 8;          // tile rows in effect (by, or the kernel's default when by == 0)
   double n_total = 0.0, neq[4] = {0, 0, 0, 0};
 
   int precision() const override { return sizeof(T) == 4 ? FDTD_FP32 : FDTD_FP64; }
@@ -412,12 +413,20 @@ struct GridImpl final : GridBase {
     items.clear();
     const bool periodic = desc.periodic[0] || desc.periodic[1] || desc.periodic[2];
     const bool enc = tensor_map_encoder() != nullptr;
-    const int kind = (kernel_kind == 3 && sizeof(T) != 4) ? 2 : kernel_kind;  // paired kernel: binary32 only
-    use_pair = sizeof(T) == 4 && kind == 3 && !periodic && enc;
-    use_tma = use_pair || ((kind == 2 || (kind == 0 && !periodic)) && !periodic && (by == 4 || by == 8) && enc);
-    tile_oy = use_pair ? (by == 8 ? 8 : 16) : by;
+    // kind 0 (automatic): the paired kernel for passive binary32 grids, the
+    // TMA kernel for gain and binary64 grids (measured faster there), the
+    // plain-load kernel when an axis is periodic; by == 0: the chosen
+    // kernel's default tile rows (paired 16, others 8)
+    int kind = kernel_kind;
+    if (kind == 0) kind = (sizeof(T) == 4 && !sg.gain) ? 3 : 2;
+    if (kind == 3 && sizeof(T) != 4) kind = 2;  // paired kernel: binary32 only
+    use_pair = kind == 3 && !periodic && enc && (by == 0 || by == 8 || by == 16);
+    if (kind == 3 && !use_pair) kind = 2;
+    by_eff = by > 0 ? by : (use_pair ? 16 : 8);
+    use_tma = use_pair || (kind == 2 && !periodic && (by_eff == 4 || by_eff == 8) && enc);
+    tile_oy = by_eff;
     const int ox = use_tma ? kTmaOX : bx - 1;
-    const int oy = use_tma ? tile_oy : by - 1;
+    const int oy = use_tma ? tile_oy : by_eff - 1;
     const int tnx = (desc.nx + ox - 1) / ox, tny = (desc.ny + oy - 1) / oy;
     const int tiles = tnx * tny;
     int depth = zdepth;
@@ -429,15 +438,18 @@ struct GridImpl final : GridBase {
       if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       cudaGetLastError();
       const int wave = sms * (use_pair ? step_pair_blocks_per_sm(sg.gain != 0, tile_oy)
-                                       : step_blocks_per_sm<T>(use_tma, sg.gain != 0, bx, by));
+                                       : step_blocks_per_sm<T>(use_tma, sg.gain != 0, bx, by_eff));
       depth = 16;
       while (depth > 4 && (long long)tiles * ((desc.nz + depth - 1) / depth) < 2LL * wave) depth -= 2;
     }
     depth = std::min(depth, desc.nz);
     if (use_tma) depth = std::min(depth, kTmaZMax - 1);  // the item's planes' coefficients fit in shared memory
-    // longest items first: tiles that cross absorbing slabs (and the wider
-    // halo of the plain kernel) cost more per plane, so they are issued before
-    // the interior tiles, which then fill the tail of the launch
+    // Issue order.  Paired kernel: the tiles of one z-range run together, so
+    // the halo rows and columns that neighbouring tiles share are read from
+    // DRAM once and then hit L2; z-ranges crossing an absorbing slab (costlier
+    // per plane) go first, and within a range the slab-crossing tiles lead.
+    // Other kernels: costliest items first over the whole launch (measured
+    // faster for them).  Either way the interior items fill the tail.
     std::vector<std::pair<double, int4>> work;
     for (int z0 = 0; z0 < desc.nz; z0 += depth) {
       const int z1 = std::min(desc.nz, z0 + depth);
@@ -447,7 +459,15 @@ struct GridImpl final : GridBase {
           work.push_back({item_cost(it, ox, oy), it});
         }
     }
-    std::stable_sort(work.begin(), work.end(), [](const std::pair<double, int4>& a, const std::pair<double, int4>& b) {
+    std::vector<double> range_cost((desc.nz + depth - 1) / depth, 0.0);
+    for (auto& w : work) {
+      double& c = range_cost[(w.second.w & 0xffff) / depth];
+      c = std::max(c, w.first);
+    }
+    const bool grouped = use_pair;
+    std::stable_sort(work.begin(), work.end(), [&](const std::pair<double, int4>& a, const std::pair<double, int4>& b) {
+      const int ra = (a.second.w & 0xffff) / depth, rb = (b.second.w & 0xffff) / depth;
+      if (grouped && ra != rb) return range_cost[ra] > range_cost[rb];
       return a.first > b.first;
     });
     for (auto& w : work) items.push_back(w.second);
@@ -567,9 +587,9 @@ struct GridImpl final : GridBase {
           e = launch_step_pair(reinterpret_cast<const StepGrid<float>*>(d_sg), d_tma, d_items, (int)items.size(), s,
                                tile_oy, sg.gain != 0, grid_blocks, stream);
         else if (use_tma)
-          e = launch_step_tma<T>(d_sg, d_tma, d_items, (int)items.size(), s, by, sg.gain != 0, grid_blocks, stream);
+          e = launch_step_tma<T>(d_sg, d_tma, d_items, (int)items.size(), s, tile_oy, sg.gain != 0, grid_blocks, stream);
         else
-          e = launch_step<T>(d_sg, d_items, (int)items.size(), s, bx, by, sg.gain != 0, grid_blocks, stream);
+          e = launch_step<T>(d_sg, d_items, (int)items.size(), s, bx, by_eff, sg.gain != 0, grid_blocks, stream);
         if (e != cudaSuccess) return cuda_error(e, "step kernel");
         if (ev.second) cudaEventRecord(ev.second, stream);
         if (timer.used >= 4096) {
@@ -710,7 +730,7 @@ struct GridImpl final : GridBase {
   const void* tma_device() const override { return d_tma; }
   bool uses_tma() const override { return use_tma; }
   bool uses_pair() const override { return use_pair; }
-  int tile_rows() const override { return tile_oy; }
+  int tile_rows() const override { return use_tma ? tile_oy : by_eff - 1; }
   void work_items(std::vector<int4>& si, std::vector<int4>& oi) const override {
     si = items;
     oi = oitems;

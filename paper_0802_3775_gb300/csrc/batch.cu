@@ -51,8 +51,6 @@ struct BatchImpl final : BatchBase {
     for (GridBase* g : grids) {
       if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_error(e, "sync member");
     }
-    tma = true;
-    pair = true;
     gain = false;
     for (GridBase* g : grids) {
       g->kernel_kind = kernel_kind;
@@ -63,27 +61,30 @@ struct BatchImpl final : BatchBase {
       int r = g->finalized ? g->replan() : g->finalize();
       if (r != FDTD_OK) return r;
       g->finalized = true;
-      tma = tma && g->uses_tma();
-      pair = pair && g->uses_pair();
       gain = gain || g->has_gain();
     }
-    // one launch serves all members: they must agree on the kernel
-    if (tma && !pair)
-      for (GridBase* g : grids)
-        if (g->uses_pair()) {
-          g->kernel_kind = 2;
-          int r = g->replan();
-          if (r != FDTD_OK) return r;
-        }
-    if (!tma) pair = false;
-    if (!tma)
-      for (GridBase* g : grids)
-        if (g->uses_tma()) {
-          g->kernel_kind = 1;
-          int r = g->replan();
-          if (r != FDTD_OK) return r;
-        }
-    oy = grids.empty() ? by : grids[0]->tile_rows();
+    // one launch serves all members: they must agree on the kernel and the
+    // tile; members that differ fall back to the most general kernel used
+    for (int round = 0; round < 3; ++round) {
+      int lo = 3, hi = 1;
+      for (GridBase* g : grids) {
+        const int v = g->uses_pair() ? 3 : (g->uses_tma() ? 2 : 1);
+        lo = std::min(lo, v);
+        hi = std::max(hi, v);
+      }
+      bool rows_agree = true;
+      for (GridBase* g : grids) rows_agree = rows_agree && g->tile_rows() == grids[0]->tile_rows();
+      if (lo == hi && rows_agree) break;
+      const int to = (lo == hi) ? 1 : lo;
+      for (GridBase* g : grids) {
+        g->kernel_kind = to;
+        int r = g->replan();
+        if (r != FDTD_OK) return r;
+      }
+    }
+    tma = !grids.empty() && grids[0]->uses_tma();
+    pair = !grids.empty() && grids[0]->uses_pair();
+    oy = grids.empty() ? 8 : grids[0]->tile_rows();
     std::vector<StepGrid<T>> hsg(ng);
     std::vector<ObsGrid<T>> hog(ng);
     items.clear();
@@ -157,9 +158,9 @@ struct BatchImpl final : BatchBase {
       e = launch_step_pair(reinterpret_cast<const StepGrid<float>*>(d_sg), d_tma, d_items, (int)items.size(), offset,
                            oy, gain, grid_blocks, stream);
     else if (tma)
-      e = launch_step_tma<T>(d_sg, d_tma, d_items, (int)items.size(), offset, by, gain, grid_blocks, stream);
+      e = launch_step_tma<T>(d_sg, d_tma, d_items, (int)items.size(), offset, oy, gain, grid_blocks, stream);
     else
-      e = launch_step<T>(d_sg, d_items, (int)items.size(), offset, bx, by, gain, grid_blocks, stream);
+      e = launch_step<T>(d_sg, d_items, (int)items.size(), offset, bx, oy + 1, gain, grid_blocks, stream);
     if (e != cudaSuccess) return e;
     if (ev.second) cudaEventRecord(ev.second, stream);
     if (!oitems.empty()) e = launch_observe<T>(d_og, d_oitems, (int)oitems.size(), offset, stream);

@@ -121,13 +121,36 @@ __device__ __forceinline__ int slab_index(int q, int n, int L0, int L1) {
   return -1;
 }
 
-// Soft-source waveform of every source of the grid at update n (FP64), into sg[].
+// Planes [lo, hi) whose E nodes source S drives.
+__device__ __forceinline__ void source_planes(const SrcDev& S, int& lo, int& hi) {
+  if (S.kind == 0) {
+    lo = S.k;
+    hi = S.k + 1;
+  } else if (S.axis == 2) {
+    lo = S.index;
+    hi = S.index + 1;
+  } else if (S.axis == 0) {
+    lo = S.lo2;
+    hi = S.hi2;
+  } else {
+    lo = S.lo1;
+    hi = S.hi1;
+  }
+}
+
+// Soft-source waveform at update n (FP64) of every source of the grid that
+// drives a node of planes [za, zb), into sg[] (the others are never read).
 template <typename T>
-__device__ __forceinline__ void source_waveforms(const StepGrid<T>& G, long long n, int tid, double* sg) {
+__device__ __forceinline__ void source_waveforms(const StepGrid<T>& G, long long n, int tid, double* sg,
+                                                 int za = 0, int zb = 0x7fffffff) {
   if (tid < G.nsrc) {
     const SrcDev& s = G.src[tid];
-    const double t = (double)n + 0.5 - s.t0;
-    sg[tid] = exp(-t * t / (2.0 * s.tau * s.tau)) * sin(2.0 * 3.14159265358979323846 * s.f0dt * t);
+    int lo, hi;
+    source_planes(s, lo, hi);
+    if (lo < zb && hi > za) {
+      const double t = (double)n + 0.5 - s.t0;
+      sg[tid] = exp(-t * t / (2.0 * s.tau * s.tau)) * sin(2.0 * 3.14159265358979323846 * s.f0dt * t);
+    }
   }
 }
 

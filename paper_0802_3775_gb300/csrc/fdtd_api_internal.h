@@ -79,7 +79,7 @@ struct GridBase {
   double S = 0, dx = 0, dt = 0;
   bool material_set = false;
   bool finalized = false;
-  int bx = 32, by = 8, zdepth = 0, grid_blocks = 0;
+  int bx = 32, by = 0, zdepth = 0, grid_blocks = 0;  // by == 0: the step kernel's default tile rows
   uint8_t* d_mat = nullptr;
   LaunchTimer timer;
   long long step_limit = 0x7fffffffffffffffLL;  // no update n >= step_limit

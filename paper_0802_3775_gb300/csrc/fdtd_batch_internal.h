@@ -12,7 +12,7 @@ struct BatchBase {
   cudaStream_t stream = nullptr;
   DeviceMemory mem;
   LaunchTimer timer;
-  int kernel_kind = 0, bx = 32, by = 8, zdepth = 0, grid_blocks = 0, graph_steps = 0;
+  int kernel_kind = 0, bx = 32, by = 0, zdepth = 0, grid_blocks = 0, graph_steps = 0;
   bool tma = false;
   bool dirty = true;  // tables must be rebuilt before the next step
 

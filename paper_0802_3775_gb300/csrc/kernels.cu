@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(512) k_step(const StepGrid<T>* __restrict__ gr
     __syncthreads();
     const long long n = G.step + offset;
     if (n >= G.step_end) continue;
-    source_waveforms(G, n, tid, sg);
+    source_waveforms(G, n, tid, sg, item.w & 0xffff, (item.w >> 16) & 0xffff);
     __syncthreads();
 
     const int nx = G.nx, ny = G.ny, nz = G.nz, px = G.px;
@@ -322,14 +322,15 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int4 item = items[it];
     __syncthreads();
-    if (item.x != cur) {
+    const bool fresh = item.x != cur;
+    if (fresh) {
       load_record(grids + item.x, smem, tid, OX * OY);
       cur = item.x;
     }
     __syncthreads();
     const long long n = G.step + offset;
     if (n >= G.step_end) continue;
-    source_waveforms(G, n, tid, sg);
+    source_waveforms(G, n, tid, sg, item.w & 0xffff, (item.w >> 16) & 0xffff);
 
     const int nx = G.nx, ny = G.ny, px = G.px;
     const int x0 = item.y, y0 = item.z, z0 = item.w & 0xffff, z1 = (item.w >> 16) & 0xffff;
@@ -349,6 +350,11 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
       tma_load_3d(dst + L::field_bytes, mmap, x0, y0, plane, &full[s]);
     };
     if (tid == 0) {
+      if (fresh) {
+        tensormap_acquire(fmap);
+        tensormap_acquire(mmap);
+        tensormap_acquire(smap);
+      }
       fence_proxy_async_smem();
       for (int p = 0; p < S && p < NP; ++p) issue(q0 + p, kstart + p);
     }

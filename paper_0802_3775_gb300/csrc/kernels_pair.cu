@@ -183,11 +183,13 @@ __device__ __forceinline__ void pair_cpml(const StepGrid<float>& G, const PairCo
   if (pl.sz >= 0) both(2, pl.pz_plane + c.pz0, cfz, dzA, dzB);
 }
 
-// H~^{n+1/2} of the pair whose node 0 sits at staged offset o (even).
+// H~^{n+1/2} of the pair whose node 0 sits at staged offset o (even); CPML:
+// the pair's node or plane may lie in an absorbing slab.
+template <bool CPML>
 __device__ __forceinline__ void pair_h(const StepGrid<float>& G, const PairCol& c, const Plane& pl, int sel, bool wr,
                                        const float* Fk, const float* Fn, int o, int PL, int BXT, const float* cfx,
                                        int xcol, const float* cfy, const float* cfz, int pa, const float2* pre,
-                                       float2& hx, float2& hy, float2& hz) {
+                                       float2 ncH, float2& hx, float2& hy, float2& hz) {
   const float2 ex = ld2(Fk + o), ey = ld2(Fk + PL + o), ez = ld2(Fk + 2 * PL + o);
   float2 dyEz = sub2(ld2(Fk + 2 * PL + o + BXT), ez);
   float2 dzEy = sub2(ld2(Fn + PL + o), ey);
@@ -195,9 +197,8 @@ __device__ __forceinline__ void pair_h(const StepGrid<float>& G, const PairCol& 
   float2 dxEz = sub2(make_float2(ez.y, Fk[2 * PL + o + 2]), ez);
   float2 dxEy = sub2(make_float2(ey.y, Fk[PL + o + 2]), ey);
   float2 dyEx = sub2(ld2(Fk + o + BXT), ex);
-  if (c.sx0 >= 0 || c.sx1 >= 0 || c.sy >= 0 || pl.sz >= 0)
+  if (CPML && (c.sx0 >= 0 || c.sx1 >= 0 || c.sy >= 0 || pl.sz >= 0))
     pair_cpml<1>(G, c, pl, sel, wr, cfx, xcol, cfy, cfz, pa, pre, dxEz, dxEy, dyEx, dyEz, dzEy, dzEx);
-  const float2 ncH = bc2(-G.cH);
   hx = fma2(ncH, sub2(dyEz, dzEy), ld2(Fk + 3 * PL + o));
   hy = fma2(ncH, sub2(dzEx, dxEz), ld2(Fk + 4 * PL + o));
   hz = fma2(ncH, sub2(dxEy, dyEx), ld2(Fk + 5 * PL + o));
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(PairLayout<OY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 
     }
     const long long n = G.step + offset;
     if (n >= G.step_end) continue;
-    source_waveforms(G, n, tid, sg);
+    source_waveforms(G, n, tid, sg, item.w & 0xffff, (item.w >> 16) & 0xffff);
 
     const int nx = G.nx, ny = G.ny, px = G.px;
     const int x0 = item.y, y0 = item.z, z0 = item.w & 0xffff, z1 = (item.w >> 16) & 0xffff;
@@ -359,6 +360,11 @@ __global__ void __launch_bounds__(PairLayout<OY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 
       tma_load_3d(dst + L::field_bytes, mmap, x0, y0, plane, &full[s]);
     };
     if (producer) {
+      if (fresh) {
+        tensormap_acquire(fmap);
+        tensormap_acquire(mmap);
+        tensormap_acquire(smap);
+      }
       fence_proxy_async_smem();
       for (int p = 0; p < S && p < NP; ++p) issue(q0 + p, kstart + p);
     }
@@ -469,6 +475,21 @@ __global__ void __launch_bounds__(PairLayout<OY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 
 
     float2 hPx = make_float2(0.0f, 0.0f), hPy = make_float2(0.0f, 0.0f);
     bool ok = true;
+    const float2 ncH = bc2(-G.cH);
+    // Per-warp choice of the node code, decided once per item (columns, rows)
+    // and per plane (z slabs, sources, PEC planes): a warp none of whose nodes
+    // needs CPML, a source, a PEC hold or gain takes the plain Yee update.
+    const bool w_slab = __any_sync(0xffffffffu, valid && (pc.sx0 >= 0 || pc.sx1 >= 0 || pc.sy >= 0));
+    const bool w_pec = __any_sync(0xffffffffu, valid && (pc.i0 == 0 || pc.j == 0));
+    const bool w_src = __any_sync(0xffffffffu, (src0 | src1) != 0u);
+    unsigned src_planes = 0;  // bit p: plane kstart + p holds a node that some source drives
+    if (w_src)
+      for (int s = 0; s < G.nsrc; ++s) {
+        int lo, hi;
+        source_planes(G.src[s], lo, hi);
+        for (int p = 0; p < NP - 1; ++p)
+          if (kstart + p >= lo && kstart + p < hi) src_planes |= 1u << p;
+      }
 
     for (int p = 0; p < NP - 1; ++p) {
       const int k = kstart + p;
@@ -479,28 +500,40 @@ __global__ void __launch_bounds__(PairLayout<OY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 
       const unsigned char* stg = stages + (size_t)(q % S) * L::stage_bytes;
       const float* Fk = reinterpret_cast<const float*>(stg);
       const float* Fn = reinterpret_cast<const float*>(stages + (size_t)((q + 1) % S) * L::stage_bytes);
-      const float* slots = reinterpret_cast<const float*>(stg + L::field_bytes + L::mat_bytes);
       const bool active = k >= z0;
-      const Plane pl = make_plane(G, k);
+      const bool zslab = k < zs_lo || k >= zs_hi;
+      const bool gen_h = w_slab || zslab;                  // warp-uniform
+      bool gen_e = gen_h || w_pec || k == 0 || (w_src && ((src_planes >> p) & 1u));
+      const unsigned mm = (!halo && active) ? *reinterpret_cast<const unsigned short*>(stg + L::field_bytes + 2 * tid) : 0u;
+      if (GAIN && G.gain) gen_e = gen_e || __any_sync(0xffffffffu, ((mm >> 6) | (mm >> 14)) & 1u);
+      Plane pl;
+      if (gen_h || gen_e) pl = make_plane(G, k);
       const float* cz = cfz + 6 * p;
 
       // CPML memory of this pair fetched ahead
       float2 pre[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
       float2 preE[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
-      const int pa = valid ? (pl.sz >= 0 ? 2 : col_axis) : -1;
-      if (pa >= 0) {
-        pre[0] = ld2(slots + sbase);
-        pre[1] = ld2(slots + sstride + sbase);
-        if (!halo) {
-          preE[0] = ld2(slots + 2 * NC + sbase);
-          preE[1] = ld2(slots + 3 * NC + sbase);
+      int pa = -1;
+      if (gen_h) {
+        pa = valid ? (zslab ? 2 : col_axis) : -1;
+        if (pa >= 0) {
+          const float* slots = reinterpret_cast<const float*>(stg + L::field_bytes + L::mat_bytes);
+          pre[0] = ld2(slots + sbase);
+          pre[1] = ld2(slots + sstride + sbase);
+          if (!halo) {
+            preE[0] = ld2(slots + 2 * NC + sbase);
+            preE[1] = ld2(slots + 3 * NC + sbase);
+          }
         }
       }
 
       float2 hx = make_float2(0.0f, 0.0f), hy = hx, hz = hx;
       if (ok && valid) {
-        pair_h(G, pc, pl, sel, !halo && active, Fk, Fn, o, PL, BXT, cfx, xcol, cfy + 6 * yrow, cz, pa, pre, hx, hy,
-               hz);
+        if (gen_h)
+          pair_h<true>(G, pc, pl, sel, !halo && active, Fk, Fn, o, PL, BXT, cfx, xcol, cfy + 6 * yrow, cz, pa, pre,
+                       ncH, hx, hy, hz);
+        else
+          pair_h<false>(G, pc, pl, sel, false, Fk, Fn, o, PL, BXT, cfx, xcol, cfy, cz, -1, pre, ncH, hx, hy, hz);
         if (!pc.own1) hx.y = hy.y = hz.y = 0.0f;
       }
       if (halo && lane >= 16) {
@@ -536,35 +569,39 @@ __global__ void __launch_bounds__(PairLayout<OY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 
           float2 dxHz = sub2(hz, make_float2(sHz[oh - 1], hz.x));
           float2 dxHy = sub2(hy, make_float2(sHy[oh - 1], hy.x));
           float2 dyHx = sub2(hx, ld2(sHx + oh - HW));
-          if (pc.sx0 >= 0 || pc.sx1 >= 0 || pc.sy >= 0 || pl.sz >= 0)
+          if (gen_h && (pc.sx0 >= 0 || pc.sx1 >= 0 || pc.sy >= 0 || pl.sz >= 0))
             pair_cpml<0>(G, pc, pl, sel, true, cfx, xcol, cfy + 6 * yrow, cz, pa, preE, dxHz, dxHy, dyHx, dyHz,
                          dzHy, dzHx);
           const float2 curlx = sub2(dyHz, dzHy);
           const float2 curly = sub2(dzHx, dxHz);
           const float2 curlz = sub2(dxHy, dyHx);
-          const unsigned mm = *reinterpret_cast<const unsigned short*>(stg + L::field_bytes + 2 * tid);
           const unsigned m0 = mm & 0xffu, m1 = mm >> 8;
           const float4 c0 = ctab[m0 & 63u], c1 = ctab[m1 & 63u];
           enx = fma2(make_float2(c0.x, c1.x), curlx, ex);
           eny = fma2(make_float2(c0.y, c1.y), curly, ey);
           enz = fma2(make_float2(c0.z, c1.z), curlz, ez);
-          const bool pec = pc.i0 == 0 || pc.j == 0 || pl.pecz;
-          const bool gainpair = GAIN && G.gain && (((m0 | m1) >> 6) & 1);
-          if (src0 | src1 | pec | gainpair) {
-            const long long cidx = cbase + (long long)k * pstride;
-            float ec[3] = {ex.x, ey.x, ez.x}, en[3] = {enx.x, eny.x, enz.x};
-            node_extras<GAIN>(G, sg, pc.i0, pc.j, pl, sel, n, cidx, m0, src0, ec, en);
-            enx.x = en[0];
-            eny.x = en[1];
-            enz.x = en[2];
-            if (pc.own1) {
-              float ec1[3] = {ex.y, ey.y, ez.y}, en1[3] = {enx.y, eny.y, enz.y};
-              node_extras<GAIN>(G, sg, pc.i0 + 1, pc.j, pl, sel, n, cidx + 1, m1, src1, ec1, en1);
-              enx.y = en1[0];
-              eny.y = en1[1];
-              enz.y = en1[2];
+          if (gen_e) {
+            const bool pec = pc.i0 == 0 || pc.j == 0 || pl.pecz;
+            const bool gainpair = GAIN && G.gain && (((m0 | m1) >> 6) & 1);
+            if (src0 | src1 | pec | gainpair) {
+              const long long cidx = cbase + (long long)k * pstride;
+              float ec[3] = {ex.x, ey.x, ez.x}, en[3] = {enx.x, eny.x, enz.x};
+              node_extras<GAIN>(G, sg, pc.i0, pc.j, pl, sel, n, cidx, m0, src0, ec, en);
+              enx.x = en[0];
+              eny.x = en[1];
+              enz.x = en[2];
+              if (pc.own1) {
+                float ec1[3] = {ex.y, ey.y, ez.y}, en1[3] = {enx.y, eny.y, enz.y};
+                node_extras<GAIN>(G, sg, pc.i0 + 1, pc.j, pl, sel, n, cidx + 1, m1, src1, ec1, en1);
+                enx.y = en1[0];
+                eny.y = en1[1];
+                enz.y = en1[2];
+              }
             }
           }
+          // a node past the grid edge stores zeros: the bulk store's bounds
+          // check works on 16-byte units, so it can land in the row padding
+          if (!pc.own1) enx.y = eny.y = enz.y = 0.0f;
         }
         st2(out + 2 * tid, enx);
         st2(out + OPL + 2 * tid, eny);

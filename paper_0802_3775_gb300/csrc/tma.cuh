@@ -27,6 +27,13 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
 
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
+// Order this thread's later TMA uses of the 128-byte tensor map at `map`
+// after the generic-proxy writes that filled it (a host copy before the
+// launch): the map's memory may have held another grid's map before.
+__device__ __forceinline__ void tensormap_acquire(const void* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {

@@ -398,7 +398,7 @@ class Batch:
         check(self._lib.fdtd_batch_create(arr, len(self.grids), C.c_void_p(st) if st else None, C.byref(h)))
         self.h = h
 
-    def set_launch(self, kernel="auto", by=8, zdepth=0, grid_blocks=0):
+    def set_launch(self, kernel="auto", by=0, zdepth=0, grid_blocks=0):
         check(self._lib.fdtd_batch_set_launch(self.h, int(KERNELS.get(kernel, kernel)), int(by), int(zdepth),
                                               int(grid_blocks)))
 
