@@ -390,7 +390,7 @@ struct GridImpl final : GridBase {
     og.flux_v0[f] = v0;
     og.flux_v1[f] = v1;
     const long long faces = (long long)(u1 - u0) * (v1 - v0);
-    int parts = (int)((faces + 1023) / 1024);
+    int parts = (int)((faces + 255) / 256);  // one face per thread: short, latency-bound blocks
     og.flux_parts[f] = std::max(1, std::min(kMaxFluxParts, parts));
     return FDTD_OK;
   }

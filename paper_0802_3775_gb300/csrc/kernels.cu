@@ -691,15 +691,20 @@ __global__ void __launch_bounds__(256) k_observe(const ObsGrid<T>* __restrict__ 
     last = (prev == (unsigned)(nparts - 1));
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
+  if (last) {
+    // the last block folds the parts in a fixed order (thread t: parts t,
+    // t + 256, ... in sequence, then the fixed block reduction)
     __threadfence();
-    double tot = 0.0;
     const volatile double* pp = G.partials + f * kMaxFluxParts;
-    for (int q = 0; q < nparts; ++q) tot += pp[q];
-    const double T_n = G.flux_sign[f] * G.dx2_over_eta0 * tot;
-    G.flux_ring[slot * G.nflux + f] = T_n;
-    if (!isfinite(T_n)) atomicOr(G.err, 1);
-    G.counters[f] = 0u;
+    double acc2 = 0.0;
+    for (int q = threadIdx.x; q < nparts; q += blockDim.x) acc2 += pp[q];
+    const double tot = block_sum(acc2, red);
+    if (threadIdx.x == 0) {
+      const double T_n = G.flux_sign[f] * G.dx2_over_eta0 * tot;
+      G.flux_ring[slot * G.nflux + f] = T_n;
+      if (!isfinite(T_n)) atomicOr(G.err, 1);
+      G.counters[f] = 0u;
+    }
   }
 }
 

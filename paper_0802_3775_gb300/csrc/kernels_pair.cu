@@ -189,8 +189,11 @@ template <bool CPML>
 __device__ __forceinline__ void pair_h(const StepGrid<float>& G, const PairCol& c, const Plane& pl, int sel, bool wr,
                                        const float* Fk, const float* Fn, int o, int PL, int BXT, const float* cfx,
                                        int xcol, const float* cfy, const float* cfz, int pa, const float2* pre,
-                                       float2 ncH, float2& hx, float2& hy, float2& hz) {
-  const float2 ex = ld2(Fk + o), ey = ld2(Fk + PL + o), ez = ld2(Fk + 2 * PL + o);
+                                       float2 ncH, float2& ex, float2& ey, float2& ez, float2& hx, float2& hy,
+                                       float2& hz) {
+  ex = ld2(Fk + o);
+  ey = ld2(Fk + PL + o);
+  ez = ld2(Fk + 2 * PL + o);
   float2 dyEz = sub2(ld2(Fk + 2 * PL + o + BXT), ez);
   float2 dzEy = sub2(ld2(Fn + PL + o), ey);
   float2 dzEx = sub2(ld2(Fn + o), ex);
@@ -288,13 +291,25 @@ __device__ __forceinline__ unsigned node_sources(const StepGrid<float>& G, int i
 #define FDTD_PAIR_MIN_BLOCKS 2
 #endif
 
-template <bool GAIN, int OY>
-__global__ void __launch_bounds__(PairLayout<OY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 / OY)
+// Owner threads of a tile of OY rows when each owns RY rows of node pairs.
+template <int OY, int RY>
+struct PairThreads {
+  static constexpr int NTO = 16 * OY / RY;  // owner threads
+  static constexpr int NT = NTO + 32;       // + the halo / copy warp
+};
+
+#ifndef FDTD_PAIR_RY
+#define FDTD_PAIR_RY 1  // rows of node pairs per owner thread in 32 x 16 tiles (2 measured slower: fewer warps)
+#endif
+
+template <bool GAIN, int OY, int RY>
+__global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 / OY)
     k_step_pair(const StepGrid<float>* __restrict__ grids, const TmaGrid* __restrict__ maps,
                 const int4* __restrict__ items, int nitems, int offset) {
   using L = PairLayout<OY>;
   constexpr int S = kTmaStages;
-  constexpr int AX = L::AX, BXT = L::BXT, PL = L::PL, HW = L::HW, OPL = L::OPL, NTO = L::NTO, NC = L::NC;
+  constexpr int AX = L::AX, BXT = L::BXT, PL = L::PL, HW = L::HW, OPL = L::OPL, NC = L::NC;
+  constexpr int NTO = PairThreads<OY, RY>::NTO, NT = PairThreads<OY, RY>::NT;
   constexpr unsigned TX_BYTES = (unsigned)(6 * PL * sizeof(float) + L::OX * OY);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -311,10 +326,11 @@ __global__ void __launch_bounds__(PairLayout<OY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 
   float* cfy = cfx + L::CXN;
   float* cfz = cfy + L::CYN;
   const int tid = threadIdx.x;
-  const bool halo = tid >= NTO;       // the ninth warp
+  const bool halo = tid >= NTO;       // the last warp
   const int lane = tid & 31;
   const bool producer = tid == NTO;   // issues the TMA copies
-  const int tx = halo ? 0 : tid % L::PXT, ty = halo ? 0 : tid / L::PXT;
+  const int tx = halo ? 0 : tid % 16, ty0 = halo ? 0 : (tid / 16) * RY;  // first owned row of the thread
+  const int nrows = halo ? 1 : RY;
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
@@ -322,14 +338,15 @@ __global__ void __launch_bounds__(PairLayout<OY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 
   }
   __syncthreads();
 
-  unsigned ld = 0;  // plane loads issued by this block so far (same value in every thread)
+  unsigned ld = 0;     // plane loads issued by this block so far (same value in every thread)
+  unsigned phase = 0;  // bit s: parity of the next completion of stage s's barrier
   int cur = -1;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int4 item = items[it];
     __syncthreads();
     const bool fresh = item.x != cur;
     if (fresh) {
-      load_record(grids + item.x, smem, tid, L::NT);
+      load_record(grids + item.x, smem, tid, NT);
       cur = item.x;
     }
     __syncthreads();
@@ -352,8 +369,7 @@ __global__ void __launch_bounds__(PairLayout<OY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 
     const CUtensorMap* smap = &maps[item.x].store;
     const unsigned q0 = ld;
 
-    auto issue = [&](unsigned q, int plane) {
-      const int s = (int)(q % S);
+    auto issue = [&](int s, int plane) {
       unsigned char* dst = stages + (size_t)s * L::stage_bytes;
       mbar_arrive_expect_tx(&full[s], TX_BYTES);
       tma_load_4d(dst, fmap, x0 - AX, y0 - 1, plane, sel * 6, &full[s]);
@@ -366,80 +382,99 @@ __global__ void __launch_bounds__(PairLayout<OY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 
         tensormap_acquire(smap);
       }
       fence_proxy_async_smem();
-      for (int p = 0; p < S && p < NP; ++p) issue(q0 + p, kstart + p);
+      for (int p = 0; p < S && p < NP; ++p) issue((int)((q0 + p) % S), kstart + p);
     }
     ld = q0 + (unsigned)(NP < S ? NP : S);
 
-    // this thread's node pair: owned (i0, j), or on the halo row / column
-    bool valid;   // node 0 of the pair is a grid node whose H this thread provides
-    int o;        // staged offset of node 0
-    int hcol;     // H buffer offset of node 0
-    PairCol pc;
-    if (!halo) {
-      const int i0 = x0 + 2 * tx, j = y0 + ty;
-      valid = i0 < nx && j < ny;
-      make_pair_col(G, valid ? i0 : 0, valid ? j : 0, pc);
-      o = (ty + 1) * BXT + AX + 2 * tx;
-      hcol = (ty + 1) * HW + 2 + 2 * tx;
-    } else if (lane < 16) {
-      const int i0 = x0 + 2 * lane, j = y0 - 1;
-      valid = y0 > 0 && i0 < nx;
-      make_pair_col(G, valid ? i0 : 0, valid ? j : 0, pc);
-      o = AX + 2 * lane;
-      hcol = 2 + 2 * lane;
-    } else {
-      const int r = lane - 16, j = y0 + r;
-      valid = r < OY && x0 > 0 && j < ny;  // node 1 of the pair (x0-2, x0-1) is the halo node
-      make_pair_col(G, valid ? x0 - 2 : 0, valid ? j : 0, pc);
-      pc.sx0 = -1;  // node x0-2 is recomputed only to keep the pair aligned: no CPML for it
-      o = (r + 1) * BXT + AX - 2;
-      hcol = (r + 1) * HW;
+    // this thread's node pairs: RY owned rows (i0, j), or one on the halo row / column
+    bool valid[RY];   // node 0 of the pair is a grid node whose H this thread provides
+    int o[RY];        // staged offset of node 0
+    int hcol[RY];     // H buffer offset of node 0
+    int yrow[RY];     // row of the y coefficients
+    int sbase[RY];    // slot of node 0 in a stage's CPML area
+    int cell[RY];     // pair index in the tile (owned rows): slots, material, output
+    PairCol pc[RY];
+    unsigned src0[RY], src1[RY];
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      valid[r] = false;
+      src0[r] = src1[r] = 0u;
+      if (r >= nrows) {
+        make_pair_col(G, 0, 0, pc[r]);
+        o[r] = hcol[r] = yrow[r] = sbase[r] = cell[r] = 0;
+      } else if (!halo) {
+        const int i0 = x0 + 2 * tx, j = y0 + ty0 + r;
+        valid[r] = i0 < nx && j < ny;
+        make_pair_col(G, valid[r] ? i0 : 0, valid[r] ? j : 0, pc[r]);
+        o[r] = (ty0 + r + 1) * BXT + AX + 2 * tx;
+        hcol[r] = (ty0 + r + 1) * HW + 2 + 2 * tx;
+        yrow[r] = ty0 + r + 1;
+        cell[r] = (ty0 + r) * 16 + tx;
+        sbase[r] = 2 * cell[r];
+        if (valid[r] && G.nsrc) {
+          src0[r] = node_sources(G, i0, j);
+          src1[r] = pc[r].own1 ? node_sources(G, i0 + 1, j) : 0u;
+        }
+      } else if (lane < 16) {
+        const int i0 = x0 + 2 * lane, j = y0 - 1;
+        valid[r] = y0 > 0 && i0 < nx;
+        make_pair_col(G, valid[r] ? i0 : 0, valid[r] ? j : 0, pc[r]);
+        o[r] = AX + 2 * lane;
+        hcol[r] = 2 + 2 * lane;
+        yrow[r] = 0;
+        cell[r] = 0;
+        sbase[r] = 4 * NC + 2 * lane;
+      } else {
+        const int rr = lane - 16, j = y0 + rr;
+        valid[r] = rr < OY && x0 > 0 && j < ny;  // node 1 of the pair (x0-2, x0-1) is the halo node
+        make_pair_col(G, valid[r] ? x0 - 2 : 0, valid[r] ? j : 0, pc[r]);
+        pc[r].sx0 = -1;  // node x0-2 is recomputed only to keep the pair aligned: no CPML for it
+        o[r] = (rr + 1) * BXT + AX - 2;
+        hcol[r] = (rr + 1) * HW;
+        yrow[r] = rr + 1;
+        cell[r] = 0;
+        sbase[r] = 4 * NC + 2 * lane;
+      }
+      if (!valid[r]) pc[r].sx0 = pc[r].sx1 = pc[r].sy = -1;
     }
-    if (!valid) pc.sx0 = pc.sx1 = pc.sy = -1;
-    const int xcol = hcol - (hcol / HW) * HW;  // column of node 0 in the x coefficient rows
-    const int yrow = halo ? (lane < 16 ? 0 : lane - 15) : ty + 1;
-    const long long cbase = (long long)pc.j * px + pc.i0;
+    const int sstride = halo ? L::NHC : NC;
+    const int xcol = hcol[0] - (hcol[0] / HW) * HW;  // column of node 0 in the x coefficient rows
     const long long pstride = (long long)px * ny;
-    unsigned src0 = 0, src1 = 0;
-    if (!halo && valid && G.nsrc) {
-      src0 = node_sources(G, pc.i0, pc.j);
-      src1 = pc.own1 ? node_sources(G, pc.i0 + 1, pc.j) : 0u;
-    }
 
     // slab axis whose CPML memory is fetched ahead: z for the planes of a z
     // slab, else x for pairs in an x slab, else y
-    const int col_axis = (pc.sx0 >= 0 || pc.sx1 >= 0) ? 0 : (pc.sy >= 0 ? 1 : -1);
+    int col_axis[RY];
+#pragma unroll
+    for (int r = 0; r < RY; ++r)
+      col_axis[r] = (pc[r].sx0 >= 0 || pc[r].sx1 >= 0) ? 0 : (pc[r].sy >= 0 ? 1 : -1);
     const int zs_lo = G.Sd[2] ? G.L[4] : 0, zs_hi = G.Sd[2] ? G.nz - G.L[5] : G.nz;
-    auto plane_slab = [&](int plane) {
-      return (plane < zs_lo || plane >= zs_hi) ? slab_index(plane, G.nz, G.L[4], G.L[5]) : -1;
-    };
-    // slot base of this thread's pair in a stage's psi area
-    const int sbase = halo ? 4 * NC + 2 * lane : 2 * tid;
-    const int sstride = halo ? L::NHC : NC;
     auto issue_psi = [&](int plane, int stage) {
       float* slots = reinterpret_cast<float*>(stages + (size_t)stage * L::stage_bytes + L::field_bytes + L::mat_bytes);
-      const int sz = plane_slab(plane);
-      if (valid && plane < z1 && (sz >= 0 || col_axis >= 0)) {
-        const int a = sz >= 0 ? 2 : col_axis;
-        const bool eside = !halo && plane >= z0;  // E-side memory of the planes this tile updates
+      const bool zs = plane < zs_lo || plane >= zs_hi;
+      const int sz = zs ? slab_index(plane, G.nz, G.L[4], G.L[5]) : -1;
+      const bool eside = !halo && plane >= z0;  // E-side memory of the planes this tile updates
+#pragma unroll
+      for (int r = 0; r < RY; ++r) {
+        if (!(valid[r] && plane < z1 && (zs || col_axis[r] >= 0))) continue;
+        const int a = zs ? 2 : col_axis[r];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           int pi;
           if (a == 2) {
-            if (e == 1 && !pc.own1) continue;
-            pi = sz * ny * nx + pc.pz0 + e;
+            if (e == 1 && !pc[r].own1) continue;
+            pi = sz * ny * nx + pc[r].pz0 + e;
           } else if (a == 0) {
-            if ((e ? pc.sx1 : pc.sx0) < 0) continue;
-            pi = plane * ny * G.Sd[0] + (e ? pc.px1 : pc.px0);
+            if ((e ? pc[r].sx1 : pc[r].sx0) < 0) continue;
+            pi = plane * ny * G.Sd[0] + (e ? pc[r].px1 : pc[r].px0);
           } else {
-            if (e == 1 && !pc.own1) continue;
-            pi = plane * G.Sd[1] * nx + pc.py0 + e;
+            if (e == 1 && !pc[r].own1) continue;
+            pi = plane * G.Sd[1] * nx + pc[r].py0 + e;
           }
-          cp_async_elem(slots + sbase + e, G.psiH[sel][a][0] + pi);
-          cp_async_elem(slots + sstride + sbase + e, G.psiH[sel][a][1] + pi);
+          cp_async_elem(slots + sbase[r] + e, G.psiH[sel][a][0] + pi);
+          cp_async_elem(slots + sstride + sbase[r] + e, G.psiH[sel][a][1] + pi);
           if (eside) {
-            cp_async_elem(slots + 2 * NC + sbase + e, G.psiE[a][0] + pi);
-            cp_async_elem(slots + 3 * NC + sbase + e, G.psiE[a][1] + pi);
+            cp_async_elem(slots + 2 * NC + sbase[r] + e, G.psiE[a][0] + pi);
+            cp_async_elem(slots + 3 * NC + sbase[r] + e, G.psiE[a][1] + pi);
           }
         }
       }
@@ -450,20 +485,20 @@ __global__ void __launch_bounds__(PairLayout<OY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 
     // (joined to the first plane's copy group; visible after the barrier below)
     {
       const bool any_slab = G.Sd[0] || G.Sd[1] || G.Sd[2];
-      for (int e = tid; any_slab && e < L::CXN + L::CYN + 6 * (NP - 1); e += L::NT) {
+      for (int e = tid; any_slab && e < L::CXN + L::CYN + 6 * (NP - 1); e += NT) {
         int a, pos, hq;
         float* dst;
         if (e < L::CXN) {
           hq = e / HW;
           a = 0; pos = x0 - 2 + (e - hq * HW); dst = cfx + e;
         } else if (e < L::CXN + L::CYN) {
-          const int r = e - L::CXN;
-          hq = r % 6;
-          a = 1; pos = y0 - 1 + r / 6; dst = cfy + r;
+          const int rr = e - L::CXN;
+          hq = rr % 6;
+          a = 1; pos = y0 - 1 + rr / 6; dst = cfy + rr;
         } else {
-          const int r = e - L::CXN - L::CYN;
-          hq = r % 6;
-          a = 2; pos = kstart + r / 6; dst = cfz + r;
+          const int rr = e - L::CXN - L::CYN;
+          hq = rr % 6;
+          a = 2; pos = kstart + rr / 6; dst = cfz + rr;
         }
         const int lim = a == 0 ? nx : (a == 1 ? ny : G.nz);
         if (G.Sd[a] && pos >= 0 && pos < lim) cp_async_elem(dst, G.prof[a][hq / 3][hq % 3] + pos);
@@ -473,15 +508,24 @@ __global__ void __launch_bounds__(PairLayout<OY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 
     cp_async_wait<S - 1>();
     __syncthreads();
 
-    float2 hPx = make_float2(0.0f, 0.0f), hPy = make_float2(0.0f, 0.0f);
+    float2 hPx[RY], hPy[RY];
+#pragma unroll
+    for (int r = 0; r < RY; ++r) hPx[r] = hPy[r] = make_float2(0.0f, 0.0f);
     bool ok = true;
     const float2 ncH = bc2(-G.cH);
     // Per-warp choice of the node code, decided once per item (columns, rows)
     // and per plane (z slabs, sources, PEC planes): a warp none of whose nodes
     // needs CPML, a source, a PEC hold or gain takes the plain Yee update.
-    const bool w_slab = __any_sync(0xffffffffu, valid && (pc.sx0 >= 0 || pc.sx1 >= 0 || pc.sy >= 0));
-    const bool w_pec = __any_sync(0xffffffffu, valid && (pc.i0 == 0 || pc.j == 0));
-    const bool w_src = __any_sync(0xffffffffu, (src0 | src1) != 0u);
+    bool t_slab = false, t_pec = false, t_src = false;
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      t_slab = t_slab || (valid[r] && (pc[r].sx0 >= 0 || pc[r].sx1 >= 0 || pc[r].sy >= 0));
+      t_pec = t_pec || (valid[r] && (pc[r].i0 == 0 || pc[r].j == 0));
+      t_src = t_src || ((src0[r] | src1[r]) != 0u);
+    }
+    const bool w_slab = __any_sync(0xffffffffu, t_slab);
+    const bool w_pec = __any_sync(0xffffffffu, t_pec);
+    const bool w_src = __any_sync(0xffffffffu, t_src);
     unsigned src_planes = 0;  // bit p: plane kstart + p holds a node that some source drives
     if (w_src)
       for (int s = 0; s < G.nsrc; ++s) {
@@ -491,61 +535,85 @@ __global__ void __launch_bounds__(PairLayout<OY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 
           if (kstart + p >= lo && kstart + p < hi) src_planes |= 1u << p;
       }
 
+    // stages of the current and the next plane, advanced by rotation
+    int sk = (int)(q0 % S), sn = sk + 1 == S ? 0 : sk + 1;
+    auto wait_stage = [&](int s) {
+      ok = ok && mbar_wait(&full[s], (phase >> s) & 1u);
+      phase ^= 1u << s;
+    };
     for (int p = 0; p < NP - 1; ++p) {
       const int k = kstart + p;
-      const unsigned q = q0 + p;
-      if (p == 0) ok = ok && mbar_wait(&full[q % S], (q / S) & 1);
-      ok = ok && mbar_wait(&full[(q + 1) % S], ((q + 1) / S) & 1);
+      if (p == 0) wait_stage(sk);
+      wait_stage(sn);
       cp_async_wait<S - 1>();  // this thread's CPML memory of plane p
-      const unsigned char* stg = stages + (size_t)(q % S) * L::stage_bytes;
+      const unsigned char* stg = stages + (size_t)sk * L::stage_bytes;
       const float* Fk = reinterpret_cast<const float*>(stg);
-      const float* Fn = reinterpret_cast<const float*>(stages + (size_t)((q + 1) % S) * L::stage_bytes);
+      const float* Fn = reinterpret_cast<const float*>(stages + (size_t)sn * L::stage_bytes);
+      const float* slots = reinterpret_cast<const float*>(stg + L::field_bytes + L::mat_bytes);
       const bool active = k >= z0;
       const bool zslab = k < zs_lo || k >= zs_hi;
       const bool gen_h = w_slab || zslab;                  // warp-uniform
       bool gen_e = gen_h || w_pec || k == 0 || (w_src && ((src_planes >> p) & 1u));
-      const unsigned mm = (!halo && active) ? *reinterpret_cast<const unsigned short*>(stg + L::field_bytes + 2 * tid) : 0u;
-      if (GAIN && G.gain) gen_e = gen_e || __any_sync(0xffffffffu, ((mm >> 6) | (mm >> 14)) & 1u);
+      unsigned mm[RY];
+      bool t_gain = false;
+#pragma unroll
+      for (int r = 0; r < RY; ++r) {
+        mm[r] = (!halo && active) ? *reinterpret_cast<const unsigned short*>(stg + L::field_bytes + 2 * cell[r]) : 0u;
+        t_gain = t_gain || ((((mm[r] >> 6) | (mm[r] >> 14)) & 1u) != 0u);
+      }
+      if (GAIN && G.gain) gen_e = gen_e || __any_sync(0xffffffffu, t_gain);
       Plane pl;
       if (gen_h || gen_e) pl = make_plane(G, k);
       const float* cz = cfz + 6 * p;
 
-      // CPML memory of this pair fetched ahead
-      float2 pre[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
-      float2 preE[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
-      int pa = -1;
-      if (gen_h) {
-        pa = valid ? (zslab ? 2 : col_axis) : -1;
-        if (pa >= 0) {
-          const float* slots = reinterpret_cast<const float*>(stg + L::field_bytes + L::mat_bytes);
-          pre[0] = ld2(slots + sbase);
-          pre[1] = ld2(slots + sstride + sbase);
-          if (!halo) {
-            preE[0] = ld2(slots + 2 * NC + sbase);
-            preE[1] = ld2(slots + 3 * NC + sbase);
+      float2 hx[RY], hy[RY], hz[RY];
+      float2 eox[RY], eoy[RY], eoz[RY];  // E^n of the pair, kept for the E update
+      float2 preE[RY][2];
+      int pa[RY];
+#pragma unroll
+      for (int r = 0; r < RY; ++r) {
+        hx[r] = hy[r] = hz[r] = make_float2(0.0f, 0.0f);
+        eox[r] = eoy[r] = eoz[r] = make_float2(0.0f, 0.0f);
+        preE[r][0] = preE[r][1] = make_float2(0.0f, 0.0f);
+        pa[r] = -1;
+        if (r >= nrows || !ok || !valid[r]) continue;
+        if (gen_h) {
+          // CPML memory of this pair fetched ahead
+          float2 pre[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+          pa[r] = zslab ? 2 : col_axis[r];
+          if (pa[r] >= 0) {
+            pre[0] = ld2(slots + sbase[r]);
+            pre[1] = ld2(slots + sstride + sbase[r]);
+            if (!halo) {
+              preE[r][0] = ld2(slots + 2 * NC + sbase[r]);
+              preE[r][1] = ld2(slots + 3 * NC + sbase[r]);
+            }
           }
+          pair_h<true>(G, pc[r], pl, sel, !halo && active, Fk, Fn, o[r], PL, BXT, cfx, xcol, cfy + 6 * yrow[r], cz,
+                       pa[r], pre, ncH, eox[r], eoy[r], eoz[r], hx[r], hy[r], hz[r]);
+        } else {
+          pair_h<false>(G, pc[r], pl, sel, false, Fk, Fn, o[r], PL, BXT, cfx, xcol, cfy, cz, -1, nullptr, ncH, eox[r],
+                        eoy[r], eoz[r], hx[r], hy[r], hz[r]);
         }
+        if (!pc[r].own1) hx[r].y = hy[r].y = hz[r].y = 0.0f;
       }
-
-      float2 hx = make_float2(0.0f, 0.0f), hy = hx, hz = hx;
-      if (ok && valid) {
-        if (gen_h)
-          pair_h<true>(G, pc, pl, sel, !halo && active, Fk, Fn, o, PL, BXT, cfx, xcol, cfy + 6 * yrow, cz, pa, pre,
-                       ncH, hx, hy, hz);
-        else
-          pair_h<false>(G, pc, pl, sel, false, Fk, Fn, o, PL, BXT, cfx, xcol, cfy, cz, -1, pre, ncH, hx, hy, hz);
-        if (!pc.own1) hx.y = hy.y = hz.y = 0.0f;
-      }
-      if (halo && lane >= 16) {
-        if (lane - 16 < OY) {
-          sHx[hcol + 1] = hx.y;
-          sHy[hcol + 1] = hy.y;
-          sHz[hcol + 1] = hz.y;
+      if (halo) {
+        if (lane < 16) {
+          st2(sHx + hcol[0], hx[0]);
+          st2(sHy + hcol[0], hy[0]);
+          st2(sHz + hcol[0], hz[0]);
+        } else if (lane - 16 < OY) {
+          sHx[hcol[0] + 1] = hx[0].y;
+          sHy[hcol[0] + 1] = hy[0].y;
+          sHz[hcol[0] + 1] = hz[0].y;
         }
       } else {
-        st2(sHx + hcol, hx);
-        st2(sHy + hcol, hy);
-        st2(sHz + hcol, hz);
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+          st2(sHx + hcol[r], hx[r]);
+          st2(sHy + hcol[r], hy[r]);
+          st2(sHz + hcol[r], hz[r]);
+        }
       }
       // the output tile buffer must have been read by the previous plane's store
       if (producer) bulk_wait_read0();
@@ -557,76 +625,87 @@ __global__ void __launch_bounds__(PairLayout<OY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 
         }
         return;
       }
+      // nothing reads the fields of plane p's stage after this barrier: refill
+      // it with plane p + S while the owners update E
+      if (producer && p + S < NP) {
+        fence_proxy_async_smem();
+        issue(sk, kstart + p + S);
+      }
 
       if (active && !halo) {
-        float2 enx = make_float2(0.0f, 0.0f), eny = enx, enz = enx;
-        if (valid) {
-          const int oh = hcol;
-          const float2 ex = ld2(Fk + o), ey = ld2(Fk + PL + o), ez = ld2(Fk + 2 * PL + o);
-          float2 dyHz = sub2(hz, ld2(sHz + oh - HW));
-          float2 dzHy = sub2(hy, hPy);
-          float2 dzHx = sub2(hx, hPx);
-          float2 dxHz = sub2(hz, make_float2(sHz[oh - 1], hz.x));
-          float2 dxHy = sub2(hy, make_float2(sHy[oh - 1], hy.x));
-          float2 dyHx = sub2(hx, ld2(sHx + oh - HW));
-          if (gen_h && (pc.sx0 >= 0 || pc.sx1 >= 0 || pc.sy >= 0 || pl.sz >= 0))
-            pair_cpml<0>(G, pc, pl, sel, true, cfx, xcol, cfy + 6 * yrow, cz, pa, preE, dxHz, dxHy, dyHx, dyHz,
-                         dzHy, dzHx);
-          const float2 curlx = sub2(dyHz, dzHy);
-          const float2 curly = sub2(dzHx, dxHz);
-          const float2 curlz = sub2(dxHy, dyHx);
-          const unsigned m0 = mm & 0xffu, m1 = mm >> 8;
-          const float4 c0 = ctab[m0 & 63u], c1 = ctab[m1 & 63u];
-          enx = fma2(make_float2(c0.x, c1.x), curlx, ex);
-          eny = fma2(make_float2(c0.y, c1.y), curly, ey);
-          enz = fma2(make_float2(c0.z, c1.z), curlz, ez);
-          if (gen_e) {
-            const bool pec = pc.i0 == 0 || pc.j == 0 || pl.pecz;
-            const bool gainpair = GAIN && G.gain && (((m0 | m1) >> 6) & 1);
-            if (src0 | src1 | pec | gainpair) {
-              const long long cidx = cbase + (long long)k * pstride;
-              float ec[3] = {ex.x, ey.x, ez.x}, en[3] = {enx.x, eny.x, enz.x};
-              node_extras<GAIN>(G, sg, pc.i0, pc.j, pl, sel, n, cidx, m0, src0, ec, en);
-              enx.x = en[0];
-              eny.x = en[1];
-              enz.x = en[2];
-              if (pc.own1) {
-                float ec1[3] = {ex.y, ey.y, ez.y}, en1[3] = {enx.y, eny.y, enz.y};
-                node_extras<GAIN>(G, sg, pc.i0 + 1, pc.j, pl, sel, n, cidx + 1, m1, src1, ec1, en1);
-                enx.y = en1[0];
-                eny.y = en1[1];
-                enz.y = en1[2];
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+          float2 enx = make_float2(0.0f, 0.0f), eny = enx, enz = enx;
+          if (valid[r]) {
+            const int oh = hcol[r];
+            const float2 ex = eox[r], ey = eoy[r], ez = eoz[r];
+            // H of the row below: this thread's previous row when it has one
+            const float2 hzJ = (r > 0) ? hz[r - 1] : ld2(sHz + oh - HW);
+            const float2 hxJ = (r > 0) ? hx[r - 1] : ld2(sHx + oh - HW);
+            float2 dyHz = sub2(hz[r], hzJ);
+            float2 dzHy = sub2(hy[r], hPy[r]);
+            float2 dzHx = sub2(hx[r], hPx[r]);
+            float2 dxHz = sub2(hz[r], make_float2(sHz[oh - 1], hz[r].x));
+            float2 dxHy = sub2(hy[r], make_float2(sHy[oh - 1], hy[r].x));
+            float2 dyHx = sub2(hx[r], hxJ);
+            if (gen_h && (pc[r].sx0 >= 0 || pc[r].sx1 >= 0 || pc[r].sy >= 0 || pl.sz >= 0))
+              pair_cpml<0>(G, pc[r], pl, sel, true, cfx, xcol, cfy + 6 * yrow[r], cz, pa[r], preE[r], dxHz, dxHy,
+                           dyHx, dyHz, dzHy, dzHx);
+            const float2 curlx = sub2(dyHz, dzHy);
+            const float2 curly = sub2(dzHx, dxHz);
+            const float2 curlz = sub2(dxHy, dyHx);
+            const unsigned m0 = mm[r] & 0xffu, m1 = mm[r] >> 8;
+            const float4 c0 = ctab[m0 & 63u], c1 = ctab[m1 & 63u];
+            enx = fma2(make_float2(c0.x, c1.x), curlx, ex);
+            eny = fma2(make_float2(c0.y, c1.y), curly, ey);
+            enz = fma2(make_float2(c0.z, c1.z), curlz, ez);
+            if (gen_e) {
+              const bool pec = pc[r].i0 == 0 || pc[r].j == 0 || pl.pecz;
+              const bool gainpair = GAIN && G.gain && (((m0 | m1) >> 6) & 1);
+              if (src0[r] | src1[r] | pec | gainpair) {
+                const long long cidx = (long long)pc[r].j * px + pc[r].i0 + (long long)k * pstride;
+                float ec[3] = {ex.x, ey.x, ez.x}, en[3] = {enx.x, eny.x, enz.x};
+                node_extras<GAIN>(G, sg, pc[r].i0, pc[r].j, pl, sel, n, cidx, m0, src0[r], ec, en);
+                enx.x = en[0];
+                eny.x = en[1];
+                enz.x = en[2];
+                if (pc[r].own1) {
+                  float ec1[3] = {ex.y, ey.y, ez.y}, en1[3] = {enx.y, eny.y, enz.y};
+                  node_extras<GAIN>(G, sg, pc[r].i0 + 1, pc[r].j, pl, sel, n, cidx + 1, m1, src1[r], ec1, en1);
+                  enx.y = en1[0];
+                  eny.y = en1[1];
+                  enz.y = en1[2];
+                }
               }
             }
+            // a node past the grid edge stores zeros: the bulk store's bounds
+            // check works on 16-byte units, so it can land in the row padding
+            if (!pc[r].own1) enx.y = eny.y = enz.y = 0.0f;
           }
-          // a node past the grid edge stores zeros: the bulk store's bounds
-          // check works on 16-byte units, so it can land in the row padding
-          if (!pc.own1) enx.y = eny.y = enz.y = 0.0f;
+          const int oc = 2 * cell[r];
+          st2(out + oc, enx);
+          st2(out + OPL + oc, eny);
+          st2(out + 2 * OPL + oc, enz);
+          st2(out + 3 * OPL + oc, hx[r]);
+          st2(out + 4 * OPL + oc, hy[r]);
+          st2(out + 5 * OPL + oc, hz[r]);
         }
-        st2(out + 2 * tid, enx);
-        st2(out + OPL + 2 * tid, eny);
-        st2(out + 2 * OPL + 2 * tid, enz);
-        st2(out + 3 * OPL + 2 * tid, hx);
-        st2(out + 4 * OPL + 2 * tid, hy);
-        st2(out + 5 * OPL + 2 * tid, hz);
         fence_proxy_async_smem();
       }
-      hPx = hx;
-      hPy = hy;
-      __syncthreads();
-      if (producer) {
-        if (active) {
-          // E^{n+1} and H~^{n+1/2} of the owned tile (clipped at the grid edge) to set (n+1)&1
-          tma_store_4d(smap, out, x0, y0, k, (sel ^ 1) * 6);
-          bulk_commit();
-        }
-        // stage of plane p is free: refill it with plane p + S
-        if (p + S < NP) {
-          fence_proxy_async_smem();
-          issue(q + S, kstart + p + S);
-        }
+#pragma unroll
+      for (int r = 0; r < RY; ++r) {
+        hPx[r] = hx[r];
+        hPy[r] = hy[r];
       }
-      issue_psi(kstart + p + S, (int)(q % S));
+      __syncthreads();
+      if (producer && active) {
+        // E^{n+1} and H~^{n+1/2} of the owned tile (clipped at the grid edge) to set (n+1)&1
+        tma_store_4d(smap, out, x0, y0, k, (sel ^ 1) * 6);
+        bulk_commit();
+      }
+      issue_psi(kstart + p + S, sk);
+      sk = sn;
+      sn = sn + 1 == S ? 0 : sn + 1;
     }
     ld = q0 + (unsigned)NP;
   }
@@ -634,16 +713,19 @@ __global__ void __launch_bounds__(PairLayout<OY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 
   if (producer) bulk_wait0();
 }
 
+// Rows of node pairs per owner thread for a tile of oy rows.
+constexpr int pair_rows(int oy) { return oy == 16 ? FDTD_PAIR_RY : 1; }
+
 int step_pair_blocks_per_sm(bool gain, int oy) {
   const size_t smem = step_pair_smem_bytes(oy);
   const void* f;
   int threads;
   if (oy == 8) {
-    f = gain ? (const void*)k_step_pair<true, 8> : (const void*)k_step_pair<false, 8>;
-    threads = PairLayout<8>::NT;
+    f = gain ? (const void*)k_step_pair<true, 8, pair_rows(8)> : (const void*)k_step_pair<false, 8, pair_rows(8)>;
+    threads = PairThreads<8, pair_rows(8)>::NT;
   } else {
-    f = gain ? (const void*)k_step_pair<true, 16> : (const void*)k_step_pair<false, 16>;
-    threads = PairLayout<16>::NT;
+    f = gain ? (const void*)k_step_pair<true, 16, pair_rows(16)> : (const void*)k_step_pair<false, 16, pair_rows(16)>;
+    threads = PairThreads<16, pair_rows(16)>::NT;
   }
   cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
@@ -660,13 +742,13 @@ cudaError_t launch_step_pair(const StepGrid<float>* grids, const TmaGrid* maps, 
   const int blocks = (grid_blocks > 0 && grid_blocks < nitems) ? grid_blocks : nitems;
   const size_t smem = step_pair_smem_bytes(oy);
   if (oy == 8) {
-    auto f = gain ? k_step_pair<true, 8> : k_step_pair<false, 8>;
+    auto f = gain ? k_step_pair<true, 8, pair_rows(8)> : k_step_pair<false, 8, pair_rows(8)>;
     cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    f<<<blocks, PairLayout<8>::NT, smem, st>>>(grids, maps, items, nitems, offset);
+    f<<<blocks, PairThreads<8, pair_rows(8)>::NT, smem, st>>>(grids, maps, items, nitems, offset);
   } else {
-    auto f = gain ? k_step_pair<true, 16> : k_step_pair<false, 16>;
+    auto f = gain ? k_step_pair<true, 16, pair_rows(16)> : k_step_pair<false, 16, pair_rows(16)>;
     cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    f<<<blocks, PairLayout<16>::NT, smem, st>>>(grids, maps, items, nitems, offset);
+    f<<<blocks, PairThreads<16, pair_rows(16)>::NT, smem, st>>>(grids, maps, items, nitems, offset);
   }
   return cudaGetLastError();
 }
