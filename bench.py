@@ -18,6 +18,7 @@ bounded sample of the same workload, on the host cores, rank 0 only.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -261,6 +262,19 @@ def run_gpu(args, rank, world, dist):
         "clocks": ck,
     }
     if rank == 0:
+        if world == 1 and not args.no_serve:
+            result["serve"] = serve_stream(capacity_mcell=0.6 * value)
+        if len(specs) > 1 and specs[0].precision == "f32":
+            # FP32 batched vs plain single-run FP64 GPU path, realizations/hour
+            steps_run = 20000  # steps per realization of the batched workload
+            rph32 = len(specs) / (ms_max / args.steps * 1e-3 * steps_run) * 3600.0
+            rph64, nsamp = fp64_plain_rate(specs, steps_run)
+            result["vs_fp64_plain"] = {
+                "fp32_batched_realizations_per_hour": round(rph32, 2),
+                "fp64_plain_realizations_per_hour": round(rph64, 2), "factor": round(rph32 / rph64, 2),
+                "steps_per_realization": steps_run,
+                "note": f"FP64 path: each realization stepped alone (automatic kernel), mean of the first {nsamp}; "
+                        "accuracy of both against the FP64 oracle is asserted by the parity tests"}
         result["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(result))
     if batch is not None:
@@ -314,6 +328,70 @@ def run_e2e(args, specs, rank, dist):
             "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": round(d2h / args.steps, 1),
             "includes": "grid creation from host sphere lists, device rasterization, set-up, steps "
                         "(CUDA-graph replays for batches), probe and flux series read back to the host"}
+
+
+# ----------------------------------------------------------------------------- serving
+def serve_stream(capacity_mcell: float, count: int = 48, load: float = 0.7, seed: int = 5000):
+    """Served request stream (the served-workload generator scaled to run in
+    about 15 s): Poisson arrivals of passive and lasing runs with grid edge
+    64..160 (CPML included) and 2000..8000 steps, the arrival rate set so the
+    offered load is `load` of `capacity_mcell`; every run is submitted at its
+    arrival time to one server (150 GB budget, continuous batching).
+    Latency = completion - submission, on the server's clock."""
+    from paper_0802_3775_gb300.serve import Server
+
+    stream = inputs.request_stream(count, rate_hz=1.0, seed=seed, n_range=(64, 160), steps_range=(2000, 8000))
+    work = [s.cells * s.steps for _, s in stream]
+    rate = load * capacity_mcell * 1e6 / (sum(work) / len(work))
+    srv = Server(hbm_budget_bytes=150 << 30, max_slots=64, steps_per_chunk=500)
+    t0 = time.perf_counter()
+    tickets = []
+    for t_arr, spec in stream:
+        t_sub = t_arr / rate
+        now = time.perf_counter() - t0
+        if t_sub > now:
+            time.sleep(t_sub - now)
+        tickets.append(srv.submit(spec, steps=spec.steps))
+    lat = []
+    for t in tickets:
+        r = srv.wait(t)
+        lat.append(r.done_s - r.submit_s)
+        srv.release(t)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat.sort()
+    pick = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]
+    return {"requests": count, "offered_load": load, "arrival_rate_hz": round(rate, 3),
+            "p50_s": round(pick(0.50), 3), "p99_s": round(pick(0.99), 3), "max_s": round(lat[-1], 3),
+            "realizations_per_hour": round(count / wall * 3600.0, 1),
+            "mcell_updates_per_s": round(sum(work) / wall / 1e6, 1), "failed": st["failed"],
+            "stream": "Poisson arrivals, grid edge 64..160 incl. CPML, 2000..8000 steps, half passive half "
+                      "lasing (served-workload generator scaled down), 150 GB budget, 64 slots, 500-step chunks"}
+
+
+def fp64_plain_rate(specs, steps_run: int, steps: int = 60, sample: int = 4):
+    """Realizations/hour of the plain single-run FP64 GPU path on the first
+    `sample` realizations of the workload (each stepped alone, `steps` timed
+    steps, extrapolated to `steps_run` steps per realization)."""
+    import torch
+
+    from paper_0802_3775_gb300.fdtd import Grid
+
+    secs = []
+    for s in specs[:sample]:
+        s64 = dataclasses.replace(s, precision="f64")
+        g = Grid.from_spec(s64, record_capacity=steps + 16)
+        g.step(3)
+        g.sync()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step(steps)
+        g.sync()
+        secs.append((time.perf_counter() - t0) / steps * steps_run)
+        g.close()
+    per = sum(secs) / len(secs)
+    return 3600.0 / per, len(secs)
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -395,6 +473,7 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma", "pair"],
                     help="step kernel (default: the library's automatic choice)")
     ap.add_argument("--by", type=int, default=0, help="tile rows of the step kernel (0: library default)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served request stream")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
