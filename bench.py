@@ -150,6 +150,19 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+# ----------------------------------------------------------------------------- ranks
+def rank_max(x: float, dist, device: str = "cuda") -> float:
+    """Maximum of a per-rank time over all ranks (the job is as slow as its
+    slowest replica); x itself when running alone."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def configure_grid(args, g):
     if args.kernel != "auto":
@@ -217,11 +230,7 @@ def run_gpu(args, rank, world, dist):
     kname = {1: "k_step", 2: "k_step_tma", 3: "k_step_pair"}[kind]
     stepper.set_timing(False)
     stepper.sync()
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = rank_max(ms, dist)
     cells = sum(s.cells for s in specs)
     value = cells * args.steps * world / (ms_max * 1e-3) / 1e6
 
@@ -236,7 +245,11 @@ def run_gpu(args, rank, world, dist):
     prof = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
     if os.path.exists(prof):
         with open(prof) as f:
-            traffic = json.load(f).get("dram_bytes_per_launch")
+            rec = json.load(f)
+        # DRAM bytes of one launch from an ncu capture of this workload, when
+        # it was taken on the kernel this run uses
+        if rec.get("kernel") == kname and rec.get("tile") == [32 if kind > 1 else None, rows]:
+            traffic = rec.get("dram_bytes_per_launch")
 
     # end to end through the public API with host inputs and host results
     e2e = run_e2e(args, specs, rank, dist)
@@ -317,11 +330,7 @@ def run_e2e(args, specs, rank, dist):
         d2h += fl.nbytes + pr.nbytes // (2 if s.precision == "f32" else 1)
         g.close()
     torch.cuda.synchronize()
-    t = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = rank_max(time.perf_counter() - t0, dist)
     world = dist.get_world_size() if dist is not None else 1
     cells = sum(s.cells for s in specs)
     return {"value": round(cells * args.steps * world / t / 1e6, 1), "unit": "Mcell-updates/s",
