@@ -397,6 +397,22 @@ struct GridImpl final : GridBase {
 
   // Relative cost of a work item: planes (plus the recomputed plane below)
   // times a factor for each absorbing slab the tile's columns or planes cross.
+  // Paired kernel: relative cost per plane of a tile's nodes (measured on the
+  // 184^3 grid: tiles crossing an x slab 2.3x, a y slab 1.6x an interior
+  // tile; a z-slab plane 2.25x an interior plane).
+  double pair_tile_cost(int x0, int y0, int ox, int oy) const {
+    auto crosses = [](int a0, int a1, int n, int L0, int L1) { return (L0 > 0 && a0 < L0) || (L1 > 0 && a1 > n - L1); };
+    const bool sx = crosses(x0 - 2, x0 + ox, desc.nx, desc.npml[0], desc.npml[1]);
+    const bool sy = crosses(y0 - 1, y0 + oy, desc.ny, desc.npml[2], desc.npml[3]);
+    return 1.0 + 1.3 * sx + 0.6 * sy;
+  }
+  double pair_item_cost(const int4& it, int ox, int oy) const {
+    const int z0 = it.w & 0xffff, z1 = (it.w >> 16) & 0xffff, kstart = z0 > 0 ? z0 - 1 : z0;
+    int slab_planes = 0;
+    for (int k = kstart; k < z1; ++k) slab_planes += (k < desc.npml[4] || k >= desc.nz - desc.npml[5]);
+    return pair_tile_cost(it.y, it.z, ox, oy) * ((z1 - kstart) + 1.25 * slab_planes);
+  }
+
   double item_cost(const int4& it, int ox, int oy) const {
     const int x0 = it.y, y0 = it.z, z0 = it.w & 0xffff, z1 = (it.w >> 16) & 0xffff;
     auto crosses = [](int a0, int a1, int n, int L0, int L1) { return (L0 > 0 && a0 < L0) || (L1 > 0 && a1 > n - L1); };
@@ -444,32 +460,52 @@ struct GridImpl final : GridBase {
     }
     depth = std::min(depth, desc.nz);
     if (use_tma) depth = std::min(depth, kTmaZMax - 1);  // the item's planes' coefficients fit in shared memory
-    // Issue order.  Paired kernel: the tiles of one z-range run together, so
-    // the halo rows and columns that neighbouring tiles share are read from
-    // DRAM once and then hit L2; z-ranges crossing an absorbing slab (costlier
-    // per plane) go first, and within a range the slab-crossing tiles lead.
-    // Other kernels: costliest items first over the whole launch (measured
-    // faster for them).  Either way the interior items fill the tail.
     std::vector<std::pair<double, int4>> work;
-    for (int z0 = 0; z0 < desc.nz; z0 += depth) {
-      const int z1 = std::min(desc.nz, z0 + depth);
+    if (use_pair && zdepth <= 0) {
+      // Paired kernel, automatic depth: every tile cuts z at the slab edges
+      // and takes z-ranges whose length falls with the tile's and the
+      // segment's cost per plane, so the items run about equally long; the
+      // costliest go first, and items of equal cost in z order (neighbouring
+      // tiles of one z-range run together: their shared halo rows and
+      // columns are read from DRAM once and then hit L2).
+      const int cuts[4] = {0, std::min(desc.npml[4], desc.nz), std::max(desc.nz - desc.npml[5], std::min(desc.npml[4], desc.nz)), desc.nz};
       for (int ty = 0; ty < tny; ++ty)
         for (int tx = 0; tx < tnx; ++tx) {
-          const int4 it = make_int4(0, tx * ox, ty * oy, z0 | (z1 << 16));
-          work.push_back({item_cost(it, ox, oy), it});
+          const double ct = pair_tile_cost(tx * ox, ty * oy, ox, oy);
+          for (int seg = 0; seg < 3; ++seg) {
+            const double cs = ct * (seg == 1 ? 1.0 : 2.25);
+            const int d = std::max(4, std::min(depth, (int)std::lround(depth / cs)));
+            for (int z0 = cuts[seg]; z0 < cuts[seg + 1]; z0 += d) {
+              const int z1 = std::min(cuts[seg + 1], z0 + d);
+              const int4 it = make_int4(0, tx * ox, ty * oy, z0 | (z1 << 16));
+              work.push_back({pair_item_cost(it, ox, oy), it});
+            }
+          }
         }
+      auto bucket = [](double c) { return (int)std::floor(std::log(c) / std::log(1.2)); };
+      std::stable_sort(work.begin(), work.end(), [&](const std::pair<double, int4>& a, const std::pair<double, int4>& b) {
+        const int ba = bucket(a.first), bb = bucket(b.first);
+        if (ba != bb) return ba > bb;
+        const int za = a.second.w & 0xffff, zb = b.second.w & 0xffff;
+        if (za != zb) return za < zb;
+        if (a.second.z != b.second.z) return a.second.z < b.second.z;
+        return a.second.y < b.second.y;
+      });
+    } else {
+      // Costliest items first over the whole launch (measured faster for the
+      // single-node kernels); items of equal cost in z order.
+      for (int z0 = 0; z0 < desc.nz; z0 += depth) {
+        const int z1 = std::min(desc.nz, z0 + depth);
+        for (int ty = 0; ty < tny; ++ty)
+          for (int tx = 0; tx < tnx; ++tx) {
+            const int4 it = make_int4(0, tx * ox, ty * oy, z0 | (z1 << 16));
+            work.push_back({item_cost(it, ox, oy), it});
+          }
+      }
+      std::stable_sort(work.begin(), work.end(), [](const std::pair<double, int4>& a, const std::pair<double, int4>& b) {
+        return a.first > b.first;
+      });
     }
-    std::vector<double> range_cost((desc.nz + depth - 1) / depth, 0.0);
-    for (auto& w : work) {
-      double& c = range_cost[(w.second.w & 0xffff) / depth];
-      c = std::max(c, w.first);
-    }
-    const bool grouped = use_pair;
-    std::stable_sort(work.begin(), work.end(), [&](const std::pair<double, int4>& a, const std::pair<double, int4>& b) {
-      const int ra = (a.second.w & 0xffff) / depth, rb = (b.second.w & 0xffff) / depth;
-      if (grouped && ra != rb) return range_cost[ra] > range_cost[rb];
-      return a.first > b.first;
-    });
     for (auto& w : work) items.push_back(w.second);
     oitems.clear();
     if (og.nprobe) oitems.push_back(make_int4(0, -1, 0, 1));

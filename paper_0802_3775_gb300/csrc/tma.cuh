@@ -58,13 +58,26 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// try_wait that lets the hardware suspend the thread for up to `ns`
+// nanoseconds while the phase is incomplete (instead of spinning).
+__device__ __forceinline__ bool mbar_try_wait_for(uint64_t* bar, unsigned parity, unsigned ns) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Wait for phase `parity` of an mbarrier, giving up after about 2 s.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (;;) {
-    for (int r = 0; r < 64; ++r)
-      if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_for(bar, parity, 100000u)) return true;  // suspended up to 0.1 ms per try
     if (global_ns() - t0 > 2000000000ull) return false;
   }
 }
