@@ -65,7 +65,9 @@ enum { FDTD_SRC_POINT = 0, FDTD_SRC_SHEET = 1 };
 typedef struct fdtd_grid fdtd_grid;
 
 /* Device allocator.  alloc returns device memory of `bytes` usable on
- * `stream` or NULL; free releases it.  ctx is passed through. */
+ * `stream`, aligned to 256 bytes, or NULL (a block that is not 256-byte
+ * aligned is freed again and the call that needed it fails with E_NOMEM);
+ * free releases it.  ctx is passed through. */
 typedef struct fdtd_allocator {
   void* (*alloc)(size_t bytes, void* stream, void* ctx);
   void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);

@@ -52,6 +52,12 @@ void* DeviceMemory::get(size_t bytes) {
     cudaGetLastError();
     p = nullptr;
   }
+  if (p && (reinterpret_cast<uintptr_t>(p) & 255u)) {
+    // the kernels move 8- and 16-byte words and TMA boxes: 256-byte alignment required
+    if (alloc.free) alloc.free(p, bytes, stream, alloc.ctx);
+    else cudaFree(p);
+    return nullptr;
+  }
   if (p) blocks.push_back({p, bytes});
   return p;
 }
@@ -222,14 +228,17 @@ struct GridImpl final : GridBase {
     og.err = d_err;
     og.dx2_over_eta0 = dx * dx / eta0();
 
-    // CPML memory: per axis with a slab, 2 E-side arrays and 2x2 H-side arrays
+    // CPML memory: per axis with a slab, 2 E-side arrays and 2x2 H-side arrays,
+    // each starting on a 128-byte boundary (node pairs move as 8-byte words)
     const int n3[3] = {desc.nx, desc.ny, desc.nz};
     psi_words = 0;
     size_t slab[3] = {0, 0, 0};
     for (int d = 0; d < 3; ++d) {
       sg.Sd[d] = desc.npml[2 * d] + desc.npml[2 * d + 1];
       if (sg.Sd[d]) {
-        slab[d] = (size_t)sg.Sd[d] * ((size_t)nc / n3[d]);
+        const size_t words = (size_t)sg.Sd[d] * ((size_t)nc / n3[d]);
+        const size_t unit = 128 / sizeof(T);
+        slab[d] = (words + unit - 1) / unit * unit;
         psi_words += 6 * slab[d];
       }
     }

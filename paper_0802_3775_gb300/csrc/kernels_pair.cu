@@ -124,6 +124,22 @@ __device__ __forceinline__ void make_pair_col(const StepGrid<float>& G, int i0, 
 // place when `wr`).  d[a][s]: the difference that psi slot s of axis a
 // modifies.  pa: axis whose old memory is in `pre` (-1: none); pre[s] holds
 // slot s of the pair (node 0 in .x, node 1 in .y).
+// Old CPML memory of both nodes at psi index pi (node 1 at pi + 1, read only
+// when `own1`); one 64-bit load when pi is even (both arrays are 8-byte
+// aligned and both nodes present).
+__device__ __forceinline__ float2 psi_pair(const float* a, int pi, bool own1) {
+  if (own1 && !(pi & 1)) return ld2(a + pi);
+  return make_float2(a[pi], own1 ? a[pi + 1] : 0.0f);
+}
+__device__ __forceinline__ void psi_store(float* a, int pi, bool own1, float2 v) {
+  if (own1 && !(pi & 1)) {
+    st2(a + pi, v);
+  } else {
+    a[pi] = v.x;
+    if (own1) a[pi + 1] = v.y;
+  }
+}
+
 template <int H>
 __device__ __forceinline__ void pair_cpml(const StepGrid<float>& G, const PairCol& c, const Plane& pl, int sel,
                                           bool wr, const float* cfx, int xcol, const float* cfy, const float* cfz,
@@ -132,7 +148,24 @@ __device__ __forceinline__ void pair_cpml(const StepGrid<float>& G, const PairCo
   // psi arrays: H side reads set sel, writes set sel^1; E side in place
   auto rd = [&](int a, int s) -> const float* { return H ? G.psiH[sel][a][s] : G.psiE[a][s]; };
   auto wt = [&](int a, int s) -> float* { return wr ? (H ? G.psiH[sel ^ 1][a][s] : G.psiE[a][s]) : (float*)nullptr; };
-  if (c.sx0 >= 0 || c.sx1 >= 0) {
+  constexpr int HW = PairLayout<8>::HW;
+  if (c.sx0 >= 0 && c.sx1 >= 0) {
+    // both nodes in the slab: consecutive memory and coefficient entries
+    const int pi = pl.px_plane + c.px0;
+    const float2 ik = ld2(cfx + (3 * H + 0) * HW + xcol), b = ld2(cfx + (3 * H + 1) * HW + xcol),
+                 cc = ld2(cfx + (3 * H + 2) * HW + xcol);
+    const float2 s0 = pa == 0 ? pre[0] : psi_pair(rd(0, 0), pi, true);
+    const float2 s1 = pa == 0 ? pre[1] : psi_pair(rd(0, 1), pi, true);
+    const float2 p0 = fma2(b, s0, mul2(cc, dxA));
+    const float2 p1 = fma2(b, s1, mul2(cc, dxB));
+    if (wr) {
+      psi_store(wt(0, 0), pi, true, p0);
+      psi_store(wt(0, 1), pi, true, p1);
+    }
+    dxA = fma2(ik, dxA, p0);
+    dxB = fma2(ik, dxB, p1);
+  } else if (c.sx0 >= 0 || c.sx1 >= 0) {
+    // one node in the slab (slab edge at an odd index, or the halo column)
     float* o0 = wt(0, 0);
     float* o1 = wt(0, 1);
 #pragma unroll
@@ -140,9 +173,9 @@ __device__ __forceinline__ void pair_cpml(const StepGrid<float>& G, const PairCo
       const int sx = e ? c.sx1 : c.sx0;
       if (sx < 0) continue;
       const int pi = pl.px_plane + (e ? c.px1 : c.px0);
-      const float ik = cfx[(3 * H + 0) * PairLayout<8>::HW + xcol + e];
-      const float b = cfx[(3 * H + 1) * PairLayout<8>::HW + xcol + e];
-      const float cc = cfx[(3 * H + 2) * PairLayout<8>::HW + xcol + e];
+      const float ik = cfx[(3 * H + 0) * HW + xcol + e];
+      const float b = cfx[(3 * H + 1) * HW + xcol + e];
+      const float cc = cfx[(3 * H + 2) * HW + xcol + e];
       const float s0 = pa == 0 ? (e ? pre[0].y : pre[0].x) : rd(0, 0)[pi];
       const float s1 = pa == 0 ? (e ? pre[1].y : pre[1].x) : rd(0, 1)[pi];
       float& A = e ? dxA.y : dxA.x;
@@ -154,27 +187,13 @@ __device__ __forceinline__ void pair_cpml(const StepGrid<float>& G, const PairCo
   // y and z: the two nodes share the coefficients
   auto both = [&](int a, int pi, const float* cf, float2& A, float2& B) {
     const float2 ik = bc2(cf[3 * H + 0]), b = bc2(cf[3 * H + 1]), cc = bc2(cf[3 * H + 2]);
-    float2 s0, s1;
-    if (pa == a) {
-      s0 = pre[0];
-      s1 = pre[1];
-    } else {
-      const float* r0 = rd(a, 0);
-      const float* r1 = rd(a, 1);
-      s0 = make_float2(r0[pi], c.own1 ? r0[pi + 1] : 0.0f);
-      s1 = make_float2(r1[pi], c.own1 ? r1[pi + 1] : 0.0f);
-    }
+    const float2 s0 = pa == a ? pre[0] : psi_pair(rd(a, 0), pi, c.own1);
+    const float2 s1 = pa == a ? pre[1] : psi_pair(rd(a, 1), pi, c.own1);
     const float2 p0 = fma2(b, s0, mul2(cc, A));
     const float2 p1 = fma2(b, s1, mul2(cc, B));
-    float* o0 = wt(a, 0);
-    float* o1 = wt(a, 1);
-    if (o0) {
-      o0[pi] = p0.x;
-      o1[pi] = p1.x;
-      if (c.own1) {
-        o0[pi + 1] = p0.y;
-        o1[pi + 1] = p1.y;
-      }
+    if (wr) {
+      psi_store(wt(a, 0), pi, c.own1, p0);
+      psi_store(wt(a, 1), pi, c.own1, p1);
     }
     A = fma2(ik, A, p0);
     B = fma2(ik, B, p1);
@@ -457,24 +476,31 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
       for (int r = 0; r < RY; ++r) {
         if (!(valid[r] && plane < z1 && (zs || col_axis[r] >= 0))) continue;
         const int a = zs ? 2 : col_axis[r];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          int pi;
-          if (a == 2) {
-            if (e == 1 && !pc[r].own1) continue;
-            pi = sz * ny * nx + pc[r].pz0 + e;
-          } else if (a == 0) {
-            if ((e ? pc[r].sx1 : pc[r].sx0) < 0) continue;
-            pi = plane * ny * G.Sd[0] + (e ? pc[r].px1 : pc[r].px0);
-          } else {
-            if (e == 1 && !pc[r].own1) continue;
-            pi = plane * G.Sd[1] * nx + pc[r].py0 + e;
-          }
-          cp_async_elem(slots + sbase[r] + e, G.psiH[sel][a][0] + pi);
-          cp_async_elem(slots + sstride + sbase[r] + e, G.psiH[sel][a][1] + pi);
+        // psi index of node 0; node 1 follows at +1 whenever it is fetched too
+        const int pi0 = a == 2 ? sz * ny * nx + pc[r].pz0
+                               : (a == 0 ? plane * ny * G.Sd[0] + (pc[r].sx0 >= 0 ? pc[r].px0 : pc[r].px1 - 1)
+                                         : plane * G.Sd[1] * nx + pc[r].py0);
+        const bool has0 = a != 0 || pc[r].sx0 >= 0;
+        const bool has1 = a == 0 ? pc[r].sx1 >= 0 : pc[r].own1;
+        if (has0 && has1 && !(pi0 & 1)) {
+          // both nodes, 8-byte aligned: one 8-byte copy per array
+          cp_async_pair(slots + sbase[r], G.psiH[sel][a][0] + pi0);
+          cp_async_pair(slots + sstride + sbase[r], G.psiH[sel][a][1] + pi0);
           if (eside) {
-            cp_async_elem(slots + 2 * NC + sbase[r] + e, G.psiE[a][0] + pi);
-            cp_async_elem(slots + 3 * NC + sbase[r] + e, G.psiE[a][1] + pi);
+            cp_async_pair(slots + 2 * NC + sbase[r], G.psiE[a][0] + pi0);
+            cp_async_pair(slots + 3 * NC + sbase[r], G.psiE[a][1] + pi0);
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            if (!(e ? has1 : has0)) continue;
+            const int pi = pi0 + e;
+            cp_async_elem(slots + sbase[r] + e, G.psiH[sel][a][0] + pi);
+            cp_async_elem(slots + sstride + sbase[r] + e, G.psiH[sel][a][1] + pi);
+            if (eside) {
+              cp_async_elem(slots + 2 * NC + sbase[r] + e, G.psiE[a][0] + pi);
+              cp_async_elem(slots + 3 * NC + sbase[r] + e, G.psiE[a][1] + pi);
+            }
           }
         }
       }

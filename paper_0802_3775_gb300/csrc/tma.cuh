@@ -113,6 +113,10 @@ __device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc) {
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
 }
+// 8-byte copy of two consecutive binary32 words (both addresses 8-byte aligned).
+__device__ __forceinline__ void cp_async_pair(float* smem_dst, const float* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
