@@ -201,6 +201,10 @@ def run_gpu(args, rank, world, dist):
         stepper = batch
     else:
         stepper = grids[0]
+    tune = None
+    if not args.no_autotune and args.kernel == "auto" and not args.by:
+        # launch shape picked by timing the candidates on this workload (state restored)
+        tune = stepper.autotune(trial_steps=10 if batch is None else 4)
     stepper.step(args.warmup)
     stepper.sync()
 
@@ -248,7 +252,8 @@ def run_gpu(args, rank, world, dist):
             rec = json.load(f)
         # DRAM bytes of one launch from an ncu capture of this workload, when
         # it was taken on the kernel this run uses
-        if rec.get("kernel") == kname and rec.get("tile") == [32 if kind > 1 else None, rows]:
+        zd = tune["zdepth"] if tune else 0
+        if rec.get("kernel") == kname and rec.get("tile") == [32 if kind > 1 else None, rows] and rec.get("zdepth") == zd:
             traffic = rec.get("dram_bytes_per_launch")
 
     # end to end through the public API with host inputs and host results
@@ -264,7 +269,10 @@ def run_gpu(args, rank, world, dist):
                    "cells_per_gpu": cells, "l2": "state larger than L2 (%.0f MB per GPU)" %
                    (sum(s.cells for s in specs) * (49 if specs[0].precision == "f32" else 97) / 1e6),
                    "parallelism": f"replicas x{world} (independent realizations)",
-                   "launch": "direct launches with per-launch events in the timed region"},
+                   "launch": "direct launches with per-launch events in the timed region",
+                   "launch_shape": ({"kernel": tune["kernel"], "by": tune["by"], "zdepth": tune["zdepth"],
+                                     "grid_blocks": tune["grid_blocks"], "autotuned_over": tune["candidates"]}
+                                    if tune else "library default")},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "kernel": kname, "tile": [32 if kind > 1 else None, rows],
@@ -483,6 +491,7 @@ def main():
                     help="step kernel (default: the library's automatic choice)")
     ap.add_argument("--by", type=int, default=0, help="tile rows of the step kernel (0: library default)")
     ap.add_argument("--no-serve", action="store_true", help="skip the served request stream")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shape")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

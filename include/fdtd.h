@@ -217,6 +217,25 @@ int fdtd_set_kernel(fdtd_grid* g, int32_t kind);
  * Valid after the first step (or a batch build); E_STATE before. */
 int fdtd_kernel_in_use(fdtd_grid* g, int32_t* kind, int32_t* rows);
 
+/* Launch-shape autotuner (no counterpart in the paper: it serves the
+ * stepping of many realizations).  Times each candidate launch shape (step
+ * kernel, tile rows, z-range depth, and for batches the persistent grid) for
+ * trial_steps steps after two warm-up steps, starting every trial from the
+ * current state and restoring the state afterwards (fields, CPML and gain
+ * memory, recorder rings, step counters), then keeps the fastest shape.  The
+ * candidates perform identical arithmetic, so no result changes.  Needs free
+ * device memory for one copy of the state (plain cudaMalloc, not the grid's
+ * allocator; E_NOMEM otherwise).  out (nullable) receives the choice. */
+typedef struct fdtd_tune_result {
+  int32_t kernel;       /* fdtd_set_kernel kind (0 = automatic)             */
+  int32_t bx, by;       /* launch shape (by 0 = the kernel's default rows)  */
+  int32_t zdepth;       /* planes per work item (0 = automatic)            */
+  int32_t grid_blocks;  /* persistent blocks (0 = one block per work item)  */
+  int32_t candidates;   /* shapes timed                                     */
+  double ms_per_step;   /* time of one step with the chosen shape           */
+} fdtd_tune_result;
+int fdtd_autotune(fdtd_grid* g, int32_t trial_steps, fdtd_tune_result* out);
+
 /* Per-launch timing of the step kernel: while on, every step-kernel launch
  * is bracketed by a pair of CUDA events on the grid's stream.
  * fdtd_kernel_time synchronizes and returns the summed duration (ms) and the
@@ -286,6 +305,8 @@ int fdtd_batch_step_n(fdtd_batch* b, int64_t n);
 int fdtd_batch_sync(fdtd_batch* b);
 int fdtd_batch_set_timing(fdtd_batch* b, int32_t on);
 int fdtd_batch_kernel_time(fdtd_batch* b, double* ms, int64_t* launches);
+/* As fdtd_autotune, over the batch's launch shapes, restoring every member. */
+int fdtd_batch_autotune(fdtd_batch* b, int32_t trial_steps, fdtd_tune_result* out);
 
 /* ---------------------------------------------------------------- serving
  * A request server keeps runs (disorder realizations, pulse or lasing runs of

@@ -58,6 +58,11 @@ class Allocator(C.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("bx", C.c_int32), ("by", C.c_int32), ("zdepth", C.c_int32),
+                ("grid_blocks", C.c_int32), ("candidates", C.c_int32), ("ms_per_step", C.c_double)]
+
+
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 SIGNATURES = {
@@ -74,6 +79,8 @@ SIGNATURES = {
     "fdtd_set_launch": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
     "fdtd_set_kernel": [_P, C.c_int32],
     "fdtd_kernel_in_use": [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+    "fdtd_autotune": [_P, C.c_int32, C.POINTER(TuneResult)],
+    "fdtd_batch_autotune": [_P, C.c_int32, C.POINTER(TuneResult)],
     "fdtd_step_n": [_P, C.c_int64],
     "fdtd_sync": [_P],
     "fdtd_steps_done": [_P, C.POINTER(C.c_int64)],
@@ -273,6 +280,13 @@ class Grid:
         kinds = {"auto": 0, "plain": 1, "tma": 2, "pair": 3}
         check(self._lib.fdtd_set_kernel(self.h, int(kinds.get(kind, kind))))
 
+    def autotune(self, trial_steps=10):
+        """Time the candidate launch shapes from the current state (restored
+        after every trial) and keep the fastest; returns the choice."""
+        r = TuneResult()
+        check(self._lib.fdtd_autotune(self.h, int(trial_steps), C.byref(r)))
+        return {k: getattr(r, k) for k, _ in TuneResult._fields_}
+
     def kernel_in_use(self):
         """(kind, rows): the step kernel of the grid's launches (1 plain, 2 TMA,
         3 paired) and the rows of its tile; valid after the first step."""
@@ -404,6 +418,12 @@ class Batch:
 
     def set_graph(self, steps_per_graph):
         check(self._lib.fdtd_batch_set_graph(self.h, int(steps_per_graph)))
+
+    def autotune(self, trial_steps=5):
+        """As Grid.autotune over the batch's launch shapes (every member restored)."""
+        r = TuneResult()
+        check(self._lib.fdtd_batch_autotune(self.h, int(trial_steps), C.byref(r)))
+        return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
     def step(self, n=1):
         check(self._lib.fdtd_batch_step_n(self.h, int(n)))
