@@ -25,6 +25,7 @@ import scipy.stats
 from oracle import C0, EPS0, HBAR, Oracle
 from oracle import gain as G
 from oracle.philox import gain_noise, philox4x32_10
+from paper_0802_3775_gb300 import inputs
 
 GAIN_BYTE = np.uint8(0b1101010)  # all three E components class 2, gain bit set
 
@@ -203,3 +204,42 @@ def test_noise_kick_statistics_in_gain_cells():
     xi = gain_noise(99, 0, np.arange(120))
     got = o.P.transpose(0, 3, 2, 1).reshape(3, -1)
     np.testing.assert_allclose(got, 1e-6 * xi, rtol=1e-15, atol=0)
+
+
+def test_energy_bookkeeping_field_plus_upper_population_is_conserved():
+    """Closed PEC box, every cell a gain cell, relaxation and pump off (rates
+    ~1e-6 /s), an inverted initial population: the discrete field energy
+    W^n = 1/2 eps0 dx^3 (sum eps_r E^n.E^n + sum H~^{n+1/2}.H~^{n-1/2}) plus
+    hbar w_a dx^3 sum N2^n is conserved to rounding, because the field's work
+    on the polarization, -(E^{n+1}+E^n)/2 . (P~^{n+1}-P~^n), is exactly the
+    energy the rate equations hand to level 2 (paper, Sec. "Sample and
+    numerical approach": energy exchange between field and medium)."""
+    shape = (7, 8, 6)
+    o = Oracle(shape, 12, courant=0.5, eps=(1.0, 2.5, 2.25))
+    mat = inputs.random_material(shape, seed=21, classes=(1, 2)) | np.uint8(64)
+    o.set_material(mat)
+    n_total, fa = 1e24, 0.8
+    omega_a = 2.0 * math.pi * fa * C0 / o.a
+    o.set_gain(n_total=n_total, fa_hat=fa, dw_rel=0.02, tau32=1e6, tau21=1e6, tau10=1e6, pump=0.0,
+               kappa=G.default_kappa(omega_a, 1e-9), noise_amp=0.0, init="ground")
+    o.dN[0] -= 0.4 * n_total   # 40 % of the atoms moved from level 0 to level 2: inverted
+    o.dN[2] += 0.4 * n_total
+    rng = np.random.Generator(np.random.PCG64(22))
+    o.E[:] = 1e7 * rng.normal(size=o.E.shape)   # strong enough that the exchange shows in N2 at FP64
+    o.E[1][0] = o.E[2][0] = 0.0
+    o.E[0][:, 0] = o.E[2][:, 0] = 0.0
+    o.E[0][:, :, 0] = o.E[1][:, :, 0] = 0.0
+    dv = o.dx ** 3
+    C, Wf = [], []
+    for n in range(1500):
+        E_n, H_before = o.E.copy(), o.H.copy()
+        N2 = float(np.sum(o.populations()[2]))
+        o.step(1)
+        W = 0.5 * EPS0 * dv * (float(np.sum(o.eps_E * E_n * E_n)) + float(np.sum(o.H * H_before)))
+        Wf.append(W)
+        C.append(W + HBAR * o.gain["omega_a"] * dv * N2)
+    C, Wf = np.asarray(C), np.asarray(Wf)
+    moved = np.max(np.abs(Wf - Wf[0]))
+    assert moved > 1e-5 * abs(C[0])                       # the field gained energy from level 2
+    assert np.max(np.abs(C - C[0])) <= 1e-14 * abs(C[0])  # ... exactly what level 2 lost
+    assert np.max(np.abs(C - C[0])) <= 1e-9 * moved
