@@ -243,3 +243,31 @@ def test_energy_bookkeeping_field_plus_upper_population_is_conserved():
     assert moved > 1e-5 * abs(C[0])                       # the field gained energy from level 2
     assert np.max(np.abs(C - C[0])) <= 1e-14 * abs(C[0])  # ... exactly what level 2 lost
     assert np.max(np.abs(C - C[0])) <= 1e-9 * moved
+
+
+@pytest.mark.parametrize("steps_per_period", [20, 40, 80])
+def test_polarization_recurrence_against_the_damped_oscillator(steps_per_period):
+    """The P~ recurrence with constant drive: its characteristic roots give the
+    damped oscillator's decay rate dw/2 and frequency sqrt(w_a^2 - dw^2/4) to
+    second order in dt, and its fixed point is the static response
+    kappa (N1-N2) E / (eps0 w_a^2) exactly (paper, Sec. "Sample and numerical
+    approach": Lorentz polarization driven by the population difference)."""
+    omega_a, domega, kappa = 2 * math.pi * 5e14, 0.2 * 2 * math.pi * 5e14, 3.0e-5
+    dt = 2 * math.pi / omega_a / steps_per_period
+    a1, a2, a3 = G.polarization_coefficients(omega_a, domega, kappa, dt)
+    lam = np.roots([1.0, -a1, a2])
+    decay = -math.log(abs(lam[0])) / dt
+    freq = abs(np.angle(lam[0])) / dt
+    w_d = math.sqrt(omega_a ** 2 - domega ** 2 / 4)
+    h = omega_a * dt
+    assert abs(decay / (domega / 2) - 1) < 0.5 * h * h
+    assert abs(freq / w_d - 1) < 0.5 * h * h
+    # fixed point of the driven recurrence
+    dn, E = 2.5e23, 7.0
+    P_star = a3 * dn * E / (1.0 - a1 + a2)
+    assert abs(P_star / (kappa * dn * E / (EPS0 * omega_a ** 2)) - 1) < 1e-12
+    # the recurrence itself converges to it
+    p_prev = p = 0.0
+    for _ in range(200 * steps_per_period):
+        p, p_prev = a1 * p - a2 * p_prev + a3 * dn * E, p
+    assert abs(p / P_star - 1) < 1e-9
