@@ -236,10 +236,11 @@ typedef struct fdtd_tune_result {
 } fdtd_tune_result;
 int fdtd_autotune(fdtd_grid* g, int32_t trial_steps, fdtd_tune_result* out);
 
-/* Per-launch timing of the step kernel: while on, every step-kernel launch
- * is bracketed by a pair of CUDA events on the grid's stream.
- * fdtd_kernel_time synchronizes and returns the summed duration (ms) and the
- * number of step-kernel launches since timing was switched on. */
+/* Per-launch timing of the step kernel: on = 0 switches it off; on = k >= 1
+ * brackets every k-th step-kernel launch (the first, the (k+1)-th, ...) by a
+ * pair of CUDA events on the grid's stream (k > 1 keeps the event overhead
+ * off most launches).  fdtd_kernel_time synchronizes and returns the summed
+ * duration (ms) of the bracketed launches and their number. */
 int fdtd_set_timing(fdtd_grid* g, int32_t on);
 int fdtd_kernel_time(fdtd_grid* g, double* ms, int64_t* launches);
 

@@ -348,8 +348,11 @@ int fdtd_set_timing(fdtd_grid* g, int32_t on) {
     CHECK_GRID(g);
     cudaError_t e = cudaStreamSynchronize(G->stream);
     if (e != cudaSuccess) return fdtd::cuda_error(e, "sync");
+    if (on < 0) return set_error(FDTD_E_INVAL, "timing: 0 (off) or a launch stride >= 1");
     G->timer.collect();
     G->timer.on = on != 0;
+    G->timer.stride = on > 0 ? on : 1;
+    G->timer.seen = 0;
     G->timer.ms = 0.0;
     G->timer.launches = 0;
     return FDTD_OK;
@@ -558,8 +561,11 @@ int fdtd_batch_set_timing(fdtd_batch* b, int32_t on) {
     CHECK_BATCH(b);
     cudaError_t e = cudaStreamSynchronize(B->stream);
     if (e != cudaSuccess) return fdtd::cuda_error(e, "sync");
+    if (on < 0) return set_error(FDTD_E_INVAL, "timing: 0 (off) or a launch stride >= 1");
     B->timer.collect();
     B->timer.on = on != 0;
+    B->timer.stride = on > 0 ? on : 1;
+    B->timer.seen = 0;
     B->timer.ms = 0.0;
     B->timer.launches = 0;
     return FDTD_OK;

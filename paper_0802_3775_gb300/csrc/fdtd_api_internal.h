@@ -29,6 +29,8 @@ struct DeviceMemory {
 // Event pairs bracketing kernel launches (optional per-launch timing).
 struct LaunchTimer {
   bool on = false;
+  int stride = 1;       // bracket every stride-th launch
+  long long seen = 0;   // launches since timing was switched on
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
   size_t used = 0;
   double ms = 0.0;
@@ -42,6 +44,7 @@ struct LaunchTimer {
   // events for the next launch (nullptr pair when off)
   std::pair<cudaEvent_t, cudaEvent_t> next() {
     if (!on) return {nullptr, nullptr};
+    if ((seen++ % stride) != 0) return {nullptr, nullptr};
     if (used == pool.size()) {
       cudaEvent_t a, b;
       if (cudaEventCreate(&a) != cudaSuccess) return {nullptr, nullptr};

@@ -310,8 +310,9 @@ class Grid:
         check(self._lib.fdtd_steps_done(self.h, C.byref(n)))
         return n.value
 
-    def set_timing(self, on=True):
-        check(self._lib.fdtd_set_timing(self.h, int(bool(on))))
+    def set_timing(self, on=True, every=1):
+        """Bracket every `every`-th step-kernel launch with CUDA events (off: on=False)."""
+        check(self._lib.fdtd_set_timing(self.h, int(every) if on else 0))
 
     def kernel_time(self):
         """(summed step-kernel milliseconds, launches) since timing was switched on."""
@@ -431,8 +432,9 @@ class Batch:
     def sync(self):
         check(self._lib.fdtd_batch_sync(self.h))
 
-    def set_timing(self, on=True):
-        check(self._lib.fdtd_batch_set_timing(self.h, int(bool(on))))
+    def set_timing(self, on=True, every=1):
+        """Bracket every `every`-th step-kernel launch with CUDA events (off: on=False)."""
+        check(self._lib.fdtd_batch_set_timing(self.h, int(every) if on else 0))
 
     def kernel_time(self):
         ms = C.c_double()
