@@ -6,8 +6,7 @@
 // (tile plus a one-node halo, x padded by one 16-byte unit each side) and the
 // tile's material bytes arrive in shared memory by two TMA bulk-tensor copies
 // into a 3-stage mbarrier pipeline; CPML memory of the planes ahead is fetched
-// per thread with cp.async; the new E and H of a plane leave by one TMA
-// bulk-tensor store.  What differs:
+// per thread with cp.async.  What differs:
 //   - 16 x OY owner threads, each owning the node pair (x0 + 2 tx, x0 + 2 tx + 1):
 //     the pair's values travel as 64-bit shared-memory words and every
 //     difference, curl and update of the interior cell is one f32x2 add, sub,
@@ -16,7 +15,12 @@
 //     column (OY pairs, the x0-1 node kept) while the owners compute their
 //     own H, and issues the TMA copies, so no owner warp carries halo work;
 //   - the material classes of both nodes index a 64-entry table of
-//     (S/eps_x, S/eps_y, S/eps_z) built once per grid record.
+//     (S/eps_x, S/eps_y, S/eps_z) built once per grid record;
+//   - the new E and H of a pair leave by 8-byte stores straight from
+//     registers (a half-warp writes one 128-byte row segment), and H of a
+//     plane goes to one of two shared buffers, so one block barrier per plane
+//     suffices (measured: as fast as a TMA store of an output tile, without
+//     its 12 KB of shared memory and its second barrier).
 // Every operation is the one the scalar kernels perform on that node, in the
 // same order and rounding (f32x2 lanes round like the scalar instruction), so
 // the results equal theirs bit for bit.
@@ -86,11 +90,12 @@ struct PairLayout {
   // CPML memory fetched ahead: 4 slots per owned node, 2 per halo node
   static constexpr size_t psi_bytes = align128((size_t)(4 * NC + 2 * NHC) * sizeof(float));
   static constexpr size_t stage_bytes = field_bytes + mat_bytes + psi_bytes;
-  static constexpr size_t out_off = stage_off + (size_t)kTmaStages * stage_bytes;
-  static constexpr size_t h_off = out_off + align128((size_t)6 * OPL * sizeof(float));
+  // H of the plane (row 0 = y0-1, column 1 = x0-1), two buffers: plane p uses p & 1
+  static constexpr size_t hbuf_bytes = align128((size_t)3 * HPL * sizeof(float));
+  static constexpr size_t h_off = stage_off + (size_t)kTmaStages * stage_bytes;
   // CPML grading coefficients: x as [h*3+q][HW column], y as [row][h*3+q], z as [plane][h*3+q]
   static constexpr int CXN = 6 * HW, CYN = 6 * (OY + 1), CZN = 6 * kTmaZMax;
-  static constexpr size_t coef_off = h_off + align128((size_t)3 * HPL * sizeof(float));
+  static constexpr size_t coef_off = h_off + 2 * hbuf_bytes;
   static constexpr size_t total = coef_off + (size_t)(CXN + CYN + CZN) * sizeof(float) + 128;
 };
 
@@ -327,7 +332,7 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
                 const int4* __restrict__ items, int nitems, int offset) {
   using L = PairLayout<OY>;
   constexpr int S = kTmaStages;
-  constexpr int AX = L::AX, BXT = L::BXT, PL = L::PL, HW = L::HW, OPL = L::OPL, NC = L::NC;
+  constexpr int AX = L::AX, BXT = L::BXT, PL = L::PL, HW = L::HW, NC = L::NC;
   constexpr int NTO = PairThreads<OY, RY>::NTO, NT = PairThreads<OY, RY>::NT;
   constexpr unsigned TX_BYTES = (unsigned)(6 * PL * sizeof(float) + L::OX * OY);
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -337,10 +342,6 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::bar_off);
   float4* ctab = reinterpret_cast<float4*>(smem + L::ctab_off);
   unsigned char* stages = smem + L::stage_off;
-  float* out = reinterpret_cast<float*>(smem + L::out_off);
-  float* sHx = reinterpret_cast<float*>(smem + L::h_off);
-  float* sHy = sHx + L::HPL;
-  float* sHz = sHy + L::HPL;
   float* cfx = reinterpret_cast<float*>(smem + L::coef_off);
   float* cfy = cfx + L::CXN;
   float* cfz = cfy + L::CYN;
@@ -385,7 +386,6 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
     const int sel = (int)(n & 1);
     const CUtensorMap* fmap = &maps[item.x].fields;
     const CUtensorMap* mmap = &maps[item.x].mat;
-    const CUtensorMap* smap = &maps[item.x].store;
     const unsigned q0 = ld;
 
     auto issue = [&](int s, int plane) {
@@ -398,7 +398,6 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
       if (fresh) {
         tensormap_acquire(fmap);
         tensormap_acquire(mmap);
-        tensormap_acquire(smap);
       }
       fence_proxy_async_smem();
       for (int p = 0; p < S && p < NP; ++p) issue((int)((q0 + p) % S), kstart + p);
@@ -569,6 +568,9 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
     };
     for (int p = 0; p < NP - 1; ++p) {
       const int k = kstart + p;
+      float* sHx = reinterpret_cast<float*>(smem + L::h_off + (p & 1) * L::hbuf_bytes);
+      float* sHy = sHx + L::HPL;
+      float* sHz = sHy + L::HPL;
       if (p == 0) wait_stage(sk);
       wait_stage(sn);
       cp_async_wait<S - 1>();  // this thread's CPML memory of plane p
@@ -641,14 +643,9 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
           st2(sHz + hcol[r], hz[r]);
         }
       }
-      // the output tile buffer must have been read by the previous plane's store
-      if (producer) bulk_wait_read0();
       if (__syncthreads_or(!ok)) {
         cp_async_wait<0>();
-        if (producer) {
-          atomicOr(G.err, 2);
-          bulk_wait0();
-        }
+        if (producer) atomicOr(G.err, 2);
         return;
       }
       // nothing reads the fields of plane p's stage after this barrier: refill
@@ -708,27 +705,37 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
             // check works on 16-byte units, so it can land in the row padding
             if (!pc[r].own1) enx.y = eny.y = enz.y = 0.0f;
           }
-          const int oc = 2 * cell[r];
-          st2(out + oc, enx);
-          st2(out + OPL + oc, eny);
-          st2(out + 2 * OPL + oc, enz);
-          st2(out + 3 * OPL + oc, hx[r]);
-          st2(out + 4 * OPL + oc, hy[r]);
-          st2(out + 5 * OPL + oc, hz[r]);
+          // E^{n+1} and H~^{n+1/2} of the pair straight to set (n+1)&1: 8-byte
+          // stores, a warp's half-row one 128-byte segment (px is even)
+          if (valid[r]) {
+            const long long cidx = (long long)pc[r].j * px + pc[r].i0 + (long long)k * pstride;
+            float* const* Fo = G.F[sel ^ 1];
+            if (pc[r].own1) {
+              st2(Fo[0] + cidx, enx);
+              st2(Fo[1] + cidx, eny);
+              st2(Fo[2] + cidx, enz);
+              st2(Fo[3] + cidx, hx[r]);
+              st2(Fo[4] + cidx, hy[r]);
+              st2(Fo[5] + cidx, hz[r]);
+            } else {
+              Fo[0][cidx] = enx.x;
+              Fo[1][cidx] = eny.x;
+              Fo[2][cidx] = enz.x;
+              Fo[3][cidx] = hx[r].x;
+              Fo[4][cidx] = hy[r].x;
+              Fo[5][cidx] = hz[r].x;
+            }
+          }
         }
-        fence_proxy_async_smem();
       }
 #pragma unroll
       for (int r = 0; r < RY; ++r) {
         hPx[r] = hx[r];
         hPy[r] = hy[r];
       }
-      __syncthreads();
-      if (producer && active) {
-        // E^{n+1} and H~^{n+1/2} of the owned tile (clipped at the grid edge) to set (n+1)&1
-        tma_store_4d(smap, out, x0, y0, k, (sel ^ 1) * 6);
-        bulk_commit();
-      }
+      // no second barrier: the next plane writes the other H buffer, and the
+      // barrier after its H update orders this plane's E reads before the
+      // buffer is written again
       issue_psi(kstart + p + S, sk);
       sk = sn;
       sn = sn + 1 == S ? 0 : sn + 1;
@@ -736,7 +743,6 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
     ld = q0 + (unsigned)NP;
   }
   cp_async_wait<0>();
-  if (producer) bulk_wait0();
 }
 
 // Rows of node pairs per owner thread for a tile of oy rows.
