@@ -254,7 +254,6 @@ struct TmaLayout {
   static constexpr int PL = BXT * BYT;            // elements of one component plane in a stage
   static constexpr int HW = kTmaOX + 1;           // row length of the H plane buffer
   static constexpr int HPL = (OY + 1) * HW;
-  static constexpr int OPL = kTmaOX * OY;         // elements of one component of the output tile
   static constexpr size_t sg_off = align128(sizeof(StepGrid<T>));
   static constexpr size_t bar_off = sg_off + align128(kMaxSrc * sizeof(double));
   static constexpr size_t stage_off = bar_off + 128;
@@ -265,12 +264,13 @@ struct TmaLayout {
   // CPML memory fetched ahead per thread: 4 slots per owned node, 2 per halo node
   static constexpr size_t psi_bytes = align128((size_t)(4 * NT + 2 * NH) * sizeof(T));
   static constexpr size_t stage_bytes = field_bytes + mat_bytes + psi_bytes;
-  static constexpr size_t out_off = stage_off + (size_t)kTmaStages * stage_bytes;
-  static constexpr size_t h_off = out_off + align128((size_t)6 * OPL * sizeof(T));
+  // H of the plane, two buffers (plane p uses p & 1)
+  static constexpr size_t hbuf_bytes = align128((size_t)3 * HPL * sizeof(T));
+  static constexpr size_t h_off = stage_off + (size_t)kTmaStages * stage_bytes;
   // CPML grading coefficients of the item: (OX + 1) columns, (OY + 1) rows
   // (the -x / -y halo first) and up to kTmaZMax planes, 6 values each
   static constexpr int CXN = (kTmaOX + 1) * 6, CYN = (OY + 1) * 6, CZN = kTmaZMax * 6;
-  static constexpr size_t coef_off = h_off + align128((size_t)3 * HPL * sizeof(T));
+  static constexpr size_t coef_off = h_off + 2 * hbuf_bytes;
   static constexpr size_t total = coef_off + (size_t)(CXN + CYN + CZN) * sizeof(T) + 128;  // + base alignment slack
 };
 
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
   using L = TmaLayout<T, OY>;
   constexpr int OX = kTmaOX;
   constexpr int S = kTmaStages;
-  constexpr int AX = L::AX, BXT = L::BXT, PL = L::PL, HW = L::HW, HPL = L::HPL, OPL = L::OPL;
+  constexpr int AX = L::AX, BXT = L::BXT, PL = L::PL, HW = L::HW, HPL = L::HPL;
   constexpr unsigned TX_BYTES = (unsigned)(6 * PL * sizeof(T) + OX * OY);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // TMA sources and destinations need 128-byte alignment: align the dynamic base explicitly
@@ -301,10 +301,6 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
   double* sg = reinterpret_cast<double*>(smem + L::sg_off);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::bar_off);
   unsigned char* stages = smem + L::stage_off;
-  T* out = reinterpret_cast<T*>(smem + L::out_off);
-  T* sHx = reinterpret_cast<T*>(smem + L::h_off);
-  T* sHy = sHx + HPL;
-  T* sHz = sHy + HPL;
   T* cfx = reinterpret_cast<T*>(smem + L::coef_off);
   T* cfy = cfx + L::CXN;
   T* cfz = cfy + L::CYN;
@@ -339,7 +335,6 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
     const int sel = (int)(n & 1);
     const CUtensorMap* fmap = &maps[item.x].fields;
     const CUtensorMap* mmap = &maps[item.x].mat;
-    const CUtensorMap* smap = &maps[item.x].store;
     const unsigned q0 = ld;
 
     auto issue = [&](unsigned q, int plane) {
@@ -353,7 +348,6 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
       if (fresh) {
         tensormap_acquire(fmap);
         tensormap_acquire(mmap);
-        tensormap_acquire(smap);
       }
       fence_proxy_async_smem();
       for (int p = 0; p < S && p < NP; ++p) issue(q0 + p, kstart + p);
@@ -445,6 +439,9 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
     for (int p = 0; p < NP - 1; ++p) {
       const int k = kstart + p;
       const unsigned q = q0 + p;
+      T* sHx = reinterpret_cast<T*>(smem + L::h_off + (p & 1) * L::hbuf_bytes);  // H of this plane
+      T* sHy = sHx + HPL;
+      T* sHz = sHy + HPL;
       if (p == 0) ok = ok && mbar_wait(&full[q % S], (q / S) & 1);
       ok = ok && mbar_wait(&full[(q + 1) % S], ((q + 1) / S) & 1);
       cp_async_wait<S - 1>();  // this thread's CPML memory of plane p
@@ -489,6 +486,7 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
 
       T hx = T(0), hy = T(0), hz = T(0);
       const CoefShared<T> ocf{cfx + 6 * (tx + 1), cfy + 6 * (ty + 1), cz};
+      const T eox = Fk[oe], eoy = Fk[PL + oe], eoz = Fk[2 * PL + oe];  // E^n of the own node, for the E update
       if (ok && own) h_at(col, ocf, oe, active, hx, hy, hz, &pre);
       sHx[oh] = hx;
       sHy[oh] = hy;
@@ -511,52 +509,40 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
         sHy[slot] = b;
         sHz[slot] = c;
       }
-      // the output tile buffer must have been read by the previous plane's store
-      if (tid == 0) bulk_wait_read0();
       if (__syncthreads_or(!ok)) {
         cp_async_wait<0>();
-        if (tid == 0) {
-          atomicOr(G.err, 2);
-          bulk_wait0();
-        }
+        if (tid == 0) atomicOr(G.err, 2);
         return;
       }
-
-      if (active) {
-        T enx = T(0), eny = T(0), enz = T(0);
-        if (own)
-          e_node<T, GAIN>(G, sg, col, pl, sel, n, cidx, m, gcell, gs, ocf, hz - sHz[oh - HW], hy - hPy, hx - hPx,
-                          hz - sHz[oh - 1], hy - sHy[oh - 1], hx - sHx[oh - HW], Fk[oe], Fk[PL + oe],
-                          Fk[2 * PL + oe], enx, eny, enz, &pre);
-        out[tid] = enx;
-        out[OPL + tid] = eny;
-        out[2 * OPL + tid] = enz;
-        out[3 * OPL + tid] = hx;
-        out[4 * OPL + tid] = hy;
-        out[5 * OPL + tid] = hz;
+      // nothing reads the fields of plane p's stage after this barrier: refill it
+      if (tid == 0 && p + S < NP) {
         fence_proxy_async_smem();
+        issue(q + S, kstart + p + S);
+      }
+
+      if (active && own) {
+        T enx, eny, enz;
+        e_node<T, GAIN>(G, sg, col, pl, sel, n, cidx, m, gcell, gs, ocf, hz - sHz[oh - HW], hy - hPy, hx - hPx,
+                        hz - sHz[oh - 1], hy - sHy[oh - 1], hx - sHx[oh - HW], eox, eoy, eoz, enx, eny, enz, &pre);
+        // E^{n+1} and H~^{n+1/2} straight to set (n+1)&1 (a warp row: one contiguous segment)
+        T* const* Fo = G.F[sel ^ 1];
+        Fo[0][cidx] = enx;
+        Fo[1][cidx] = eny;
+        Fo[2][cidx] = enz;
+        Fo[3][cidx] = hx;
+        Fo[4][cidx] = hy;
+        Fo[5][cidx] = hz;
       }
       hPx = hx;
       hPy = hy;
-      __syncthreads();
-      if (tid == 0) {
-        if (active) {
-          // E^{n+1} and H~^{n+1/2} of the owned tile (clipped at the grid edge) to set (n+1)&1
-          tma_store_4d(smap, out, x0, y0, k, (sel ^ 1) * 6);
-          bulk_commit();
-        }
-        // stage of plane p is free: refill it with plane p + S
-        if (p + S < NP) {
-          fence_proxy_async_smem();
-          issue(q + S, kstart + p + S);
-        }
-      }
+      // no second barrier: the next plane writes the other H buffer, and the
+      // barrier after its H update orders this plane's E reads before the
+      // buffer is written again
       issue_psi(kstart + p + S, (int)(q % S));
     }
     ld = q0 + (unsigned)NP;
   }
   cp_async_wait<0>();
-  if (tid == 0) bulk_wait0();
 }
 
 template <typename T>
