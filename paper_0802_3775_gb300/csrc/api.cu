@@ -545,11 +545,6 @@ struct GridImpl final : GridBase {
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(FDTD_E_CUDA, "tensor map (material) encode failed: %d", (int)r);
-    const cuuint32_t sbox[4] = {(cuuint32_t)kTmaOX, (cuuint32_t)tile_oy, 1, 6};
-    r = enc(&h.store, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
-            (void*)d_F, fdim, fstr, sbox, one, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return set_error(FDTD_E_CUDA, "tensor map (store) encode failed: %d", (int)r);
     cudaError_t e = cudaMemcpyAsync(d_tma, &h, sizeof(h), cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return cuda_error(e, "upload tensor maps");
     return FDTD_OK;

@@ -100,13 +100,11 @@ struct ObsGrid {
 };
 
 // TMA descriptors of one grid: all twelve field arrays as one 4D tensor
-// (x, y, z, array) read with a box of (32 + 2 pad) x (tile rows + 2) x 1 x 6
-// and written with a box of 32 x rows x 1 x 6, and the material bytes as a
-// 3D tensor read with a box of 32 x rows x 1.
+// (x, y, z, array) read with a box of (32 + 2 pad) x (tile rows + 2) x 1 x 6,
+// and the material bytes as a 3D tensor read with a box of 32 x rows x 1.
 struct alignas(128) TmaGrid {
   CUtensorMap fields;
   CUtensorMap mat;
-  CUtensorMap store;
 };
 
 // Work items of the step kernel: (grid, x0, y0, z0 | z1 << 16).

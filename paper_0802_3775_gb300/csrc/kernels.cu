@@ -5,12 +5,14 @@
 //             tile marches in z; each plane of all six fields (tile plus a
 //             one-node halo, x padded to 16-byte alignment) and the tile's
 //             material bytes arrive in shared memory by two TMA bulk-tensor
-//             copies into a 4-stage mbarrier pipeline, so three planes are in
-//             flight while one is computed.  H on the -x / -y halo is
-//             recomputed so no block needs a neighbour's output of the same
-//             step; fields and H-side CPML memory are double-buffered (read
-//             set n&1, write set (n+1)&1); E-side CPML memory and gain state
-//             are updated in place by the owning thread.
+//             copies into a 3-stage mbarrier pipeline (the current plane, the
+//             next one, one in flight).  H on the -x / -y halo is recomputed
+//             so no block needs a neighbour's output of the same step; fields
+//             and H-side CPML memory are double-buffered (read set n&1, write
+//             set (n+1)&1); E-side CPML memory and gain state are updated in
+//             place by the owning thread; new values are stored from
+//             registers; H of a plane goes to one of two shared buffers, so
+//             one block barrier per plane suffices.
 // k_step      the same step with plain loads and register prefetch of the
 //             next plane; any boundary, including periodic axes.
 // k_observe   probes (E^{n+1}) and Poynting flux T^n per plane with a

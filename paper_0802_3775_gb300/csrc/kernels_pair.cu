@@ -701,8 +701,7 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
                 }
               }
             }
-            // a node past the grid edge stores zeros: the bulk store's bounds
-            // check works on 16-byte units, so it can land in the row padding
+            // a node past the grid edge is never stored (its lane holds zeros)
             if (!pc[r].own1) enx.y = eny.y = enz.y = 0.0f;
           }
           // E^{n+1} and H~^{n+1/2} of the pair straight to set (n+1)&1: 8-byte

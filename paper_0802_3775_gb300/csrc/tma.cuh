@@ -1,5 +1,5 @@
 // Shared-memory staging helpers of the TMA step kernels: mbarriers with a
-// bounded wait, TMA bulk-tensor loads and stores, per-thread cp.async copies,
+// bounded wait, TMA bulk-tensor loads, per-thread cp.async copies,
 // proxy fences, and the copy of a grid record into shared memory.
 #pragma once
 #include <cuda.h>
@@ -99,12 +99,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0, int c1, int c2, int c3) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(map), "r"(c0),
-      "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(src))
-      : "memory");
-}
 
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc) {
@@ -123,8 +117,5 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 }  // namespace fdtd
