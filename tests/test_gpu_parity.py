@@ -269,17 +269,63 @@ def test_fp32_gain_short_run():
 
 
 def test_full_size_planewave_grid_few_steps():
-    """184^3 FP32 disordered-opal grid in its default launch shape: 4 steps from
-    seeded random fields, every cell compared with the oracle."""
+    """184^3 FP32 disordered-opal grid in the launch shape the benchmark times
+    (autotuned from the same state): 4 steps from seeded random fields, every
+    cell compared with the oracle."""
     spec = inputs.opal_planewave_f32(ncell=8, res=20, npml=12, sigma=0.06, realization=1)
     g = gpu_grid(spec)
     o = oracle_grid(spec, coef32=True)
     F = inputs.random_fields(spec.shape, seed=5, scale=1.0)
     g.write_fields(F)
     o.set_fields_memory_order(F.astype(np.float32).astype(np.float64))
+    g.autotune(trial_steps=3)
     g.step(4)
     o.step(4)
     assert _fields_gpu_vs_oracle(g, o) <= 1e-6
+
+
+def test_full_size_lasing_grid_few_steps():
+    """140^3 FP32 Maxwell-Bloch lasing grid (gain in the spheres, pump, noise)
+    in the autotuned launch shape: 3 steps from seeded random fields, every
+    cell's fields and population deviations compared with the oracle."""
+    spec = inputs.opal_lasing_f32(ncell=6, res=20, npml=10, sigma=0.05, pump=1e10, realization=1)
+    g = gpu_grid(spec)
+    o = oracle_grid(spec, coef32=True)
+    F = inputs.random_fields(spec.shape, seed=6, scale=1.0e4)
+    g.write_fields(F)
+    o.set_fields_memory_order(F.astype(np.float32).astype(np.float64))
+    g.autotune(trial_steps=3)
+    g.step(3)
+    o.step(3)
+    assert _fields_gpu_vs_oracle(g, o) <= 1e-5
+    assert rel_l2(g.read_gain(0), o.P.transpose(0, 3, 2, 1)) <= 1e-5
+    assert rel_l2(g.read_gain(3), o.dN[1:].transpose(0, 3, 2, 1)) <= 1e-6
+
+
+def test_full_size_batch_sampled_members():
+    """The 64-realization mixed batch stepped together in its autotuned shape:
+    a passive and a lasing member (from seeded random fields) against the
+    oracle, every cell, after 2 steps."""
+    from paper_0802_3775_gb300.fdtd import Batch
+    specs = inputs.mixed_batch(64, seed=4000, steps=40)
+    grids = [gpu_grid(s, record_capacity=64) for s in specs]
+    picks = [0, 1]
+    oracles = {}
+    for q in picks:
+        F = inputs.random_fields(specs[q].shape, seed=70 + q, scale=1.0e3)
+        grids[q].write_fields(F)
+        oracles[q] = oracle_grid(specs[q], coef32=True)
+        oracles[q].set_fields_memory_order(F.astype(np.float32).astype(np.float64))
+    b = Batch(grids)
+    b.autotune(trial_steps=2)
+    b.step(2)
+    b.sync()
+    for q in picks:
+        oracles[q].step(2)
+        assert _fields_gpu_vs_oracle(grids[q], oracles[q]) <= 1e-5
+    b.close()
+    for g in grids:
+        g.close()
 
 
 def test_checkpoint_restart_is_bitwise():
