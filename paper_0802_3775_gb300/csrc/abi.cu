@@ -585,7 +585,7 @@ int fdtd_batch_kernel_time(fdtd_batch* b, double* ms, int64_t* launches) {
   });
 }
 
-static const char kMagic[8] = {'F', 'D', 'T', 'D', 'C', 'K', 'P', '1'};
+static const char kMagic[8] = {'F', 'D', 'T', 'D', 'C', 'K', 'P', '2'};
 
 int fdtd_save_state(fdtd_grid* g, const char* path) {
   return guarded([&]() -> int {

@@ -326,17 +326,16 @@ struct GridImpl final : GridBase {
       for (int j = 0; j < 3; ++j) sg.D[k][j] = (T)(dt * (B[k + 1][j + 1] - B[k + 1][0]));
       sg.w[k] = (T)B[k + 1][4];
     }
-    // state: P (2 slots x 3), dN (3), compensation (3, binary32 only)
-    const size_t nw = (sizeof(T) == 4 ? 12 : 9);
+    // state: P (2 slots x 3), dN (3), compensation (3, binary32 only), in
+    // records of 32 x-adjacent nodes (rows padded to whole records)
+    sg.gxb = (desc.nx + 31) / 32;
+    const long long nslots = (long long)sg.gxb * 32 * desc.ny * desc.nz;
     if (!d_gain) {
-      gain_words = nw * (size_t)nstore;
+      gain_words = (size_t)GainWords<T>::NW * (size_t)nslots;
       d_gain = (T*)mem.get(sizeof(T) * gain_words);
       if (!d_gain) return set_error(FDTD_E_NOMEM, "device allocation failed (gain state)");
     }
-    for (int s = 0; s < 2; ++s)
-      for (int c = 0; c < 3; ++c) sg.P[s][c] = d_gain + (size_t)(s * 3 + c) * nstore;
-    for (int c = 0; c < 3; ++c) sg.dN[c] = d_gain + (size_t)(6 + c) * nstore;
-    for (int c = 0; c < 3; ++c) sg.cmp[c] = sizeof(T) == 4 ? d_gain + (size_t)(9 + c) * nstore : nullptr;
+    sg.gst = d_gain;
     sg.gain = 1;
     T d1 = 0, d2 = 0, d3 = 0;
     if (p.init == FDTD_INIT_GROUND) {
@@ -344,7 +343,7 @@ struct GridImpl final : GridBase {
       d2 = (T)(-neq[2] / p.n_total);
       d3 = (T)(-neq[3] / p.n_total);
     }
-    cudaError_t e = launch_gain_init<T>(&sg, nstore, d1, d2, d3, stream);
+    cudaError_t e = launch_gain_init<T>(&sg, nslots, d1, d2, d3, stream);
     if (e != cudaSuccess) return cuda_error(e, "gain init");
     return FDTD_OK;
   }
@@ -652,6 +651,25 @@ struct GridImpl final : GridBase {
     return copy_out(sg.F[sel][comp], out);
   }
 
+  // word w of every node's gain state -> double[nz][ny][nx] on the host (one
+  // strided copy: each 32-node record contributes its run of word w)
+  int gain_word_out(int w, double* out) {
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "sync");
+    const size_t run = sizeof(T) * 32;
+    const size_t nruns = (size_t)sg.gxb * desc.ny * desc.nz;
+    std::vector<T> h(nruns * 32);
+    if ((e = cudaMemcpy2D(h.data(), run, d_gain + (size_t)32 * w, run * GainWords<T>::NW, run, nruns,
+                          cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_error(e, "read gain state");
+    const size_t rowp = (size_t)sg.gxb * 32;
+    for (long long k = 0; k < desc.nz; ++k)
+      for (long long j = 0; j < desc.ny; ++j)
+        for (long long i = 0; i < desc.nx; ++i)
+          out[(k * desc.ny + j) * desc.nx + i] = (double)h[(size_t)(k * desc.ny + j) * rowp + (size_t)i];
+    return FDTD_OK;
+  }
+
   // device array in the pitched layout -> double[nz][ny][nx] on the host
   int copy_out(const T* src, double* out) {
     cudaError_t e;
@@ -680,13 +698,14 @@ struct GridImpl final : GridBase {
     if (what == 0 || what == 1) {
       const int slot = (int)((steps + (what == 1 ? 1 : 0)) & 1);
       for (int c = 0; c < 3; ++c)
-        if ((r = copy_out(sg.P[slot][c], out + (size_t)c * ncell)) != FDTD_OK) return r;
+        if ((r = gain_word_out((slot ? GainWords<T>::P1 : GainWords<T>::P0) + c, out + (size_t)c * ncell)) != FDTD_OK)
+          return r;
       return FDTD_OK;
     }
     std::vector<uint8_t> m((size_t)ncell);
     if ((r = get_material(m.data())) != FDTD_OK) return r;
     for (int c = 0; c < 3; ++c) {
-      if ((r = copy_out(sg.dN[c], out + (size_t)c * ncell)) != FDTD_OK) return r;
+      if ((r = gain_word_out(GainWords<T>::DN + c, out + (size_t)c * ncell)) != FDTD_OK) return r;
       for (long long q = 0; q < ncell; ++q) {
         double& v = out[(size_t)c * ncell + q];
         if (!((m[q] >> 6) & 1)) v = 0.0;

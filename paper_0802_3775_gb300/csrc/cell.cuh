@@ -44,7 +44,13 @@ __device__ __forceinline__ uint4 noise_bits(unsigned long long seed, long long c
 }
 
 // Three N(0,1) deviates for (seed, cell, step): Box-Muller on the uniforms
-// u = ((x >> 9) + 0.5) 2^-23 (exact in binary32).
+// u = ((x >> 9) + 0.5) 2^-23 (exact in binary32).  Binary32 runs take the
+// special-function-unit forms of log, sin and cos (__logf, __sincosf,
+// __cosf; documented bounds: absolute error 2^-21.41 for log on [0.5, 2] and
+// for sin and cos on [-pi, pi], 3 ulp for log elsewhere), with the angle
+// 2 pi u moved to [-pi, pi) by the exact shift u - 1/2 (cos and sin change
+// sign).  A deviate then differs from the binary64 Box-Muller value of the
+// same uniforms by about 1e-6 relative (larger only where rho is tiny).
 __device__ __forceinline__ void gain_normals(unsigned long long seed, long long cell, long long step, float& a,
                                              float& b, float& c) {
   const uint4 x = noise_bits(seed, cell, step);
@@ -52,12 +58,13 @@ __device__ __forceinline__ void gain_normals(unsigned long long seed, long long 
   const float u1 = ((float)(x.y >> 9) + 0.5f) * 0x1p-23f;
   const float u2 = ((float)(x.z >> 9) + 0.5f) * 0x1p-23f;
   const float u3 = ((float)(x.w >> 9) + 0.5f) * 0x1p-23f;
-  const float rho = sqrtf(-2.0f * logf(u0));
+  constexpr float kTwoPi = 6.28318530717958648f;
+  const float rho = sqrtf(-2.0f * __logf(u0));
   float s, co;
-  sincospif(2.0f * u1, &s, &co);
-  a = rho * co;
-  b = rho * s;
-  c = sqrtf(-2.0f * logf(u2)) * cospif(2.0f * u3);
+  __sincosf(kTwoPi * (u1 - 0.5f), &s, &co);
+  a = -(rho * co);
+  b = -(rho * s);
+  c = -(sqrtf(-2.0f * __logf(u2)) * __cosf(kTwoPi * (u3 - 0.5f)));
 }
 
 __device__ __forceinline__ void gain_normals(unsigned long long seed, long long cell, long long step, double& a,
@@ -266,21 +273,35 @@ struct GainState {
   T pnx, pny, pnz, pmx, pmy, pmz, d1, d2, d3, c1, c2, c3;
 };
 
+// Index of word 0 of node (i, j, k)'s gain state.  The state of the 32
+// nodes i = 32 b .. 32 b + 31 of a row lies in one record of NW runs of 32
+// values (word w of node i at +32 w), so a warp reads or writes each word of
+// a row segment as one contiguous 128-byte (binary32) line, and the words of
+// a node sit at fixed offsets from one address.
 template <typename T>
-__device__ __forceinline__ void load_gain(const StepGrid<T>& G, int sel, long long cidx, GainState<T>& s) {
-  s.pnx = G.P[sel][0][cidx];
-  s.pny = G.P[sel][1][cidx];
-  s.pnz = G.P[sel][2][cidx];
-  s.pmx = G.P[sel ^ 1][0][cidx];
-  s.pmy = G.P[sel ^ 1][1][cidx];
-  s.pmz = G.P[sel ^ 1][2][cidx];
-  s.d1 = G.dN[0][cidx];
-  s.d2 = G.dN[1][cidx];
-  s.d3 = G.dN[2][cidx];
+__device__ __forceinline__ long long gain_base(const StepGrid<T>& G, int i, int j, int k) {
+  return (((long long)k * G.ny + j) * G.gxb + (i >> 5)) * (GainWords<T>::NW * 32) + (i & 31);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_gain(const StepGrid<T>& G, int sel, long long gidx, GainState<T>& s) {
+  using W = GainWords<T>;
+  const T* g = G.gst + gidx;
+  const T* pn = g + 32 * (sel ? W::P1 : W::P0);
+  const T* pm = g + 32 * (sel ? W::P0 : W::P1);
+  s.pnx = pn[0];
+  s.pny = pn[32];
+  s.pnz = pn[64];
+  s.pmx = pm[0];
+  s.pmy = pm[32];
+  s.pmz = pm[64];
+  s.d1 = g[32 * W::DN];
+  s.d2 = g[32 * W::DN + 32];
+  s.d3 = g[32 * W::DN + 64];
   if (sizeof(T) == 4) {
-    s.c1 = G.cmp[0][cidx];
-    s.c2 = G.cmp[1][cidx];
-    s.c3 = G.cmp[2][cidx];
+    s.c1 = g[32 * W::CMP];
+    s.c2 = g[32 * W::CMP + 32];
+    s.c3 = g[32 * W::CMP + 64];
   } else {
     s.c1 = s.c2 = s.c3 = T(0);
   }
@@ -335,10 +356,11 @@ __device__ __forceinline__ void source_drive(const StepGrid<T>& G, const double*
 // E^{n+1} at node (c.i, c.j, p.k) from the six backward differences of
 // H~^{n+1/2}, with the CPML (E-side memory updated in place), the soft
 // sources, the gain polarization current and populations (state `gs` of a
-// gain cell), and the PEC hold of tangential E on index-0 planes.
+// gain cell, loaded from and stored back to gain_base index `gidx`), and the
+// PEC hold of tangential E on index-0 planes.
 template <typename T, bool GAIN, typename CF>
 __device__ __forceinline__ void e_node(const StepGrid<T>& G, const double* sg, const Column& c, const Plane& p,
-                                       int sel, long long n, long long cidx, unsigned m, bool gcell,
+                                       int sel, long long n, long long gidx, unsigned m, bool gcell,
                                        const GainState<T>& gs, const CF& cf, T dyHz, T dzHy, T dzHx, T dxHz, T dxHy,
                                        T dyHx, T eCx, T eCy, T eCz, T& enx, T& eny, T& enz,
                                        const PsiPre<T>* pre = nullptr) {
@@ -394,9 +416,10 @@ __device__ __forceinline__ void e_node(const StepGrid<T>& G, const double* sg, c
     dPx = Pnx - gs.pnx;
     dPy = Pny - gs.pny;
     dPz = Pnz - gs.pnz;
-    G.P[sel ^ 1][0][cidx] = Pnx;
-    G.P[sel ^ 1][1][cidx] = Pny;
-    G.P[sel ^ 1][2][cidx] = Pnz;
+    T* pm = G.gst + gidx + 32 * (sel ? GainWords<T>::P0 : GainWords<T>::P1);  // receives P~^{n+1}
+    pm[0] = Pnx;
+    pm[32] = Pny;
+    pm[64] = Pnz;
   }
 
   enx = fmad(-G.cP[clx], dPx + srcx, fmad(G.cE[clx], curlx, eCx));
@@ -416,16 +439,18 @@ __device__ __forceinline__ void e_node(const StepGrid<T>& G, const double* sg, c
       // compensated (Kahan) accumulation of the population deviations
       const T y1 = inc1 - gs.c1, y2 = inc2 - gs.c2, y3 = inc3 - gs.c3;
       const T t1 = gs.d1 + y1, t2 = gs.d2 + y2, t3 = gs.d3 + y3;
-      G.cmp[0][cidx] = (t1 - gs.d1) - y1;
-      G.cmp[1][cidx] = (t2 - gs.d2) - y2;
-      G.cmp[2][cidx] = (t3 - gs.d3) - y3;
-      G.dN[0][cidx] = t1;
-      G.dN[1][cidx] = t2;
-      G.dN[2][cidx] = t3;
+      T* g = G.gst + gidx;
+      g[32 * GainWords<T>::CMP] = (t1 - gs.d1) - y1;
+      g[32 * GainWords<T>::CMP + 32] = (t2 - gs.d2) - y2;
+      g[32 * GainWords<T>::CMP + 64] = (t3 - gs.d3) - y3;
+      g[32 * GainWords<T>::DN] = t1;
+      g[32 * GainWords<T>::DN + 32] = t2;
+      g[32 * GainWords<T>::DN + 64] = t3;
     } else {
-      G.dN[0][cidx] = gs.d1 + inc1;
-      G.dN[1][cidx] = gs.d2 + inc2;
-      G.dN[2][cidx] = gs.d3 + inc3;
+      T* g = G.gst + gidx;
+      g[32 * GainWords<T>::DN] = gs.d1 + inc1;
+      g[32 * GainWords<T>::DN + 32] = gs.d2 + inc2;
+      g[32 * GainWords<T>::DN + 64] = gs.d3 + inc3;
     }
   }
 }

@@ -44,6 +44,14 @@ struct SrcDev {
   double t0;         // envelope centre in steps
 };
 
+// Words of a node's gain state: P~ in two time slots (x, y, z each), dN~1..3,
+// and in binary32 runs three compensation words of the dN~ sums.
+template <typename T>
+struct GainWords {
+  static constexpr int NW = sizeof(T) == 4 ? 12 : 9;
+  static constexpr int P0 = 0, P1 = 3, DN = 6, CMP = 9;  // first word of each group
+};
+
 // Per-grid record read by the step kernel.  Lives in device memory (a table
 // of them for a batched launch); each block copies its grid's record into
 // shared memory.
@@ -65,10 +73,10 @@ struct StepGrid {
   const T* prof[3][2][3];  // [axis][0 E-node (integer), 1 H-node (half-integer)][1/kappa, b, c]
   T cH;                 // S
   T cE[3], cP[3];       // S/eps_r and 1/eps_r per material class
-  // gain medium (normalized populations N~ = N / n_total)
-  T* P[2][3];           // P~ time slots: P^n in slot n&1
-  T* dN[3];             // dN~1..3 (dN~0 = -sum)
-  T* cmp[3];            // compensation words (binary32 runs only)
+  // gain medium (normalized populations N~ = N / n_total): the state words
+  // of each run of 32 x-adjacent nodes of a row lie together (see gain_base)
+  T* gst;               // gain state: P~ slot 0 and 1 (slot n&1 holds P^n), dN~1..3, compensation words
+  int gxb;              // 32-node blocks per row of the gain state (ceil(nx / 32))
   T a1, a2, a3, n12eq, q, noise;
   T D[3][3], w[3];
   unsigned long long seed;
@@ -152,7 +160,7 @@ cudaError_t launch_rasterize(uint8_t* mat, int nx, int ny, int nz, int px, const
 
 // Gain initialization: P slots zero, dN~ = init - N~eq in gain cells.
 template <typename T>
-cudaError_t launch_gain_init(const StepGrid<T>* g_host_copy, long long nstore, T d1, T d2, T d3, cudaStream_t st);
+cudaError_t launch_gain_init(const StepGrid<T>* g_host_copy, long long nslots, T d1, T d2, T d3, cudaStream_t st);
 
 // Field energy sum (eps_r E^2 + H~^2) over the cells in FP64; result in out[0].
 template <typename T>

@@ -204,9 +204,10 @@ __global__ void __launch_bounds__(512) k_step(const StepGrid<T>* __restrict__ gr
       if (owner && active) {
         const bool gcell = GAIN && G.gain && ((m >> 6) & 1);
         GainState<T> gs{};
-        if (GAIN && gcell) load_gain(G, sel, cidx, gs);
+        const long long gidx = GAIN ? gain_base(G, iw, jw, kw) : 0;
+        if (GAIN && gcell) load_gain(G, sel, gidx, gs);
         T enx, eny, enz;
-        e_node<T, GAIN>(G, sg, col, pl, sel, n, cidx, m, gcell, gs, CoefGlobal<T>{&G, col.i, col.j, pl.k}, hz - sHz[tid - bx], hy - hPy, hx - hPx,
+        e_node<T, GAIN>(G, sg, col, pl, sel, n, gidx, m, gcell, gs, CoefGlobal<T>{&G, col.i, col.j, pl.k}, hz - sHz[tid - bx], hy - hPy, hx - hPx,
                         hz - sHz[tid - 1], hy - sHy[tid - 1], hx - sHx[tid - bx], eCx, eCy, eCz, enx, eny, enz);
         G.F[sel ^ 1][0][cidx] = enx;
         G.F[sel ^ 1][1][cidx] = eny;
@@ -366,6 +367,9 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
     make_column(G, own ? i : 0, own ? j : 0, col, true);
     const long long cbase = (long long)j * px + i;
     const long long pstride = (long long)px * ny;
+    // gain state of the own node in plane 0 and the stride between planes
+    const long long gbase = GAIN ? gain_base(G, own ? i : 0, own ? j : 0, 0) : 0;
+    const long long gplane = (long long)ny * G.gxb * (GainWords<T>::NW * 32);
     // halo node of this thread, if any: -y row (ty == 0) or -x column (ty == 1, tx < OY)
     const bool hrow = (ty == 0) && y0 > 0 && i < nx;
     const bool hcolm = (ty == 1) && tx < OY && x0 > 0 && y0 + tx < ny;
@@ -463,7 +467,7 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
       if (ok && own && active) {
         m = Mk[tid];
         gcell = GAIN && G.gain && ((m >> 6) & 1);
-        if (GAIN && gcell) load_gain(G, sel, cidx, gs);
+        if (GAIN && gcell) load_gain(G, sel, gbase + (long long)k * gplane, gs);
       }
       PsiPre<T> pre;
       pre.axis = own ? (pl.sz >= 0 ? 2 : col_axis) : -1;
@@ -524,7 +528,8 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
 
       if (active && own) {
         T enx, eny, enz;
-        e_node<T, GAIN>(G, sg, col, pl, sel, n, cidx, m, gcell, gs, ocf, hz - sHz[oh - HW], hy - hPy, hx - hPx,
+        e_node<T, GAIN>(G, sg, col, pl, sel, n, gbase + (long long)k * gplane, m, gcell, gs, ocf, hz - sHz[oh - HW],
+                        hy - hPy, hx - hPx,
                         hz - sHz[oh - 1], hy - sHy[oh - 1], hx - sHx[oh - HW], eox, eoy, eoz, enx, eny, enz, &pre);
         // E^{n+1} and H~^{n+1/2} straight to set (n+1)&1 (a warp row: one contiguous segment)
         T* const* Fo = G.F[sel ^ 1];
@@ -822,26 +827,32 @@ cudaError_t launch_rasterize(uint8_t* mat, int nx, int ny, int nz, int px, const
 // =====================================================================
 // Gain initialization and conversions
 // =====================================================================
+// One thread per node slot of the gain state (rows padded to 32-node
+// blocks): both P~ slots and the compensation words zero, dN~ = (d1, d2, d3)
+// in gain cells and 0 elsewhere (padding slots included).
 template <typename T>
-__global__ void k_gain_init(StepGrid<T> G, long long nstore, T d1, T d2, T d3) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nstore) return;
-  const bool g = (G.mat[c] >> 6) & 1;
-  for (int s = 0; s < 2; ++s)
-    for (int q = 0; q < 3; ++q) G.P[s][q][c] = T(0);
-  G.dN[0][c] = g ? d1 : T(0);
-  G.dN[1][c] = g ? d2 : T(0);
-  G.dN[2][c] = g ? d3 : T(0);
-  if (G.cmp[0]) {
-    G.cmp[0][c] = T(0);
-    G.cmp[1][c] = T(0);
-    G.cmp[2][c] = T(0);
+__global__ void k_gain_init(StepGrid<T> G, long long nslots, T d1, T d2, T d3) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nslots) return;
+  const long long rb = t >> 5;  // 32-node block of a row
+  const int lane = (int)(t & 31);
+  const int i = (int)(rb % G.gxb) * 32 + lane;
+  const long long row = rb / G.gxb;
+  const int j = (int)(row % G.ny), k = (int)(row / G.ny);
+  const bool g = i < G.nx && ((G.mat[((long long)k * G.ny + j) * G.px + i] >> 6) & 1);
+  using W = GainWords<T>;
+  T* w = G.gst + rb * (W::NW * 32) + lane;
+  for (int q = 0; q < W::NW; ++q) w[32 * q] = T(0);
+  if (g) {
+    w[32 * W::DN] = d1;
+    w[32 * W::DN + 32] = d2;
+    w[32 * W::DN + 64] = d3;
   }
 }
 
 template <typename T>
-cudaError_t launch_gain_init(const StepGrid<T>* g, long long nstore, T d1, T d2, T d3, cudaStream_t st) {
-  k_gain_init<T><<<(unsigned)((nstore + 255) / 256), 256, 0, st>>>(*g, nstore, d1, d2, d3);
+cudaError_t launch_gain_init(const StepGrid<T>* g, long long nslots, T d1, T d2, T d3, cudaStream_t st) {
+  k_gain_init<T><<<(unsigned)((nslots + 255) / 256), 256, 0, st>>>(*g, nslots, d1, d2, d3);
   return cudaGetLastError();
 }
 

@@ -52,6 +52,11 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
   return upk2(r);
 }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(r);
+}
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) {
   unsigned long long r;
   asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
@@ -231,68 +236,132 @@ __device__ __forceinline__ void pair_h(const StepGrid<float>& G, const PairCol& 
   hz = fma2(ncH, sub2(dxEy, dyEx), ld2(Fk + 5 * PL + o));
 }
 
-// Sources, gain and PEC of one node of the pair (the general part of the E
-// update, scalar): `en` holds fmad(cE, curl, E^n) on entry.
+// Sources, gain and PEC of the node pair (the general part of the E update):
+// (enx, eny, enz) hold fmad(cE, curl, E^n) of both nodes on entry.  The gain
+// state of both nodes is read and written as 8-byte words (node 0 at gain
+// index g0, even; node 1 at g0 + 1 in the same 32-node record), and the
+// polarization and population updates of both nodes run as f32x2 operations
+// in the scalar kernels' order; a node that is not a gain cell (or is off the
+// grid) keeps its state and gets no polarization current.
 template <bool GAIN>
-__device__ __forceinline__ void node_extras(const StepGrid<float>& G, const double* sg, int i, int j,
-                                            const Plane& pl, int sel, long long n, long long cidx, unsigned m,
-                                            unsigned srcmask, const float ec[3], float en[3]) {
-  float src[3] = {0.0f, 0.0f, 0.0f};
-  if (srcmask) {
-    Column c;
-    c.i = i;
-    c.j = j;
-    c.src = srcmask;
-    source_drive(G, sg, c, pl, src[0], src[1], src[2]);
+__device__ __forceinline__ void pair_extras(const StepGrid<float>& G, const double* sg, const PairCol& c,
+                                            const Plane& pl, int sel, long long n, long long g0, unsigned m0,
+                                            unsigned m1, unsigned s0, unsigned s1, float2 ex, float2 ey, float2 ez,
+                                            float2& enx, float2& eny, float2& enz) {
+  using W = GainWords<float>;
+  const bool ga = GAIN && G.gain && ((m0 >> 6) & 1);
+  const bool gb = GAIN && G.gain && c.own1 && ((m1 >> 6) & 1);
+  float2 srx = make_float2(0.0f, 0.0f), sry = srx, srz = srx;
+  if (s0 | s1) {
+    Column col;
+    col.j = c.j;
+    if (s0) {
+      col.i = c.i0;
+      col.src = s0;
+      source_drive(G, sg, col, pl, srx.x, sry.x, srz.x);
+    }
+    if (s1) {
+      col.i = c.i0 + 1;
+      col.src = s1;
+      source_drive(G, sg, col, pl, srx.y, sry.y, srz.y);
+    }
   }
-  const bool gcell = GAIN && G.gain && ((m >> 6) & 1);
-  float dP[3] = {0.0f, 0.0f, 0.0f};
-  GainState<float> gs{};
-  if (GAIN && gcell) {
-    load_gain(G, sel, cidx, gs);
-    const float dn12 = G.n12eq + (gs.d1 - gs.d2);
-    const float drive = G.a3 * dn12;
-    const float a1 = G.a1, a2 = G.a2;
-    float Pn[3];
-    Pn[0] = fmad(drive, ec[0], fmad(a1, gs.pnx, -(a2 * gs.pmx)));
-    Pn[1] = fmad(drive, ec[1], fmad(a1, gs.pny, -(a2 * gs.pmy)));
-    Pn[2] = fmad(drive, ec[2], fmad(a1, gs.pnz, -(a2 * gs.pmz)));
+  float2 dPx = make_float2(0.0f, 0.0f), dPy = dPx, dPz = dPx;
+  float2 d1, d2;
+  float* gw = G.gst + g0;
+  if (GAIN && (ga || gb)) {
+    float* pmw = gw + 32 * (sel ? W::P0 : W::P1);  // P~^{n-1}, receives P~^{n+1}
+    const float* pnw = gw + 32 * (sel ? W::P1 : W::P0);
+    const float2 pnx = ld2(pnw), pny = ld2(pnw + 32), pnz = ld2(pnw + 64);
+    const float2 pmx = ld2(pmw), pmy = ld2(pmw + 32), pmz = ld2(pmw + 64);
+    d1 = ld2(gw + 32 * W::DN);
+    d2 = ld2(gw + 32 * W::DN + 32);
+    const float2 drive = mul2(bc2(G.a3), add2(bc2(G.n12eq), sub2(d1, d2)));
+    const float2 a1 = bc2(G.a1), na2 = bc2(-G.a2);
+    float2 Px = fma2(drive, ex, fma2(a1, pnx, mul2(na2, pmx)));
+    float2 Py = fma2(drive, ey, fma2(a1, pny, mul2(na2, pmy)));
+    float2 Pz = fma2(drive, ez, fma2(a1, pnz, mul2(na2, pmz)));
     if (G.noise != 0.0f) {
       float xa, xb, xc;
-      const long long lcell = ((long long)pl.k * G.ny + j) * G.nx + i;
-      gain_normals(G.seed, lcell, n, xa, xb, xc);
-      Pn[0] = fmad(G.noise, xa, Pn[0]);
-      Pn[1] = fmad(G.noise, xb, Pn[1]);
-      Pn[2] = fmad(G.noise, xc, Pn[2]);
+      const long long lcell = ((long long)pl.k * G.ny + c.j) * G.nx + c.i0;
+      if (ga) {
+        gain_normals(G.seed, lcell, n, xa, xb, xc);
+        Px.x = fmad(G.noise, xa, Px.x);
+        Py.x = fmad(G.noise, xb, Py.x);
+        Pz.x = fmad(G.noise, xc, Pz.x);
+      }
+      if (gb) {
+        gain_normals(G.seed, lcell + 1, n, xa, xb, xc);
+        Px.y = fmad(G.noise, xa, Px.y);
+        Py.y = fmad(G.noise, xb, Py.y);
+        Pz.y = fmad(G.noise, xc, Pz.y);
+      }
     }
-    dP[0] = Pn[0] - gs.pnx;
-    dP[1] = Pn[1] - gs.pny;
-    dP[2] = Pn[2] - gs.pnz;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) G.P[sel ^ 1][q][cidx] = Pn[q];
+    dPx = sub2(Px, pnx);
+    dPy = sub2(Py, pny);
+    dPz = sub2(Pz, pnz);
+    if (ga && gb) {
+      st2(pmw, Px);
+      st2(pmw + 32, Py);
+      st2(pmw + 64, Pz);
+    } else if (ga) {
+      pmw[0] = Px.x;
+      pmw[32] = Py.x;
+      pmw[64] = Pz.x;
+      dPx.y = dPy.y = dPz.y = 0.0f;
+    } else {
+      pmw[1] = Px.y;
+      pmw[33] = Py.y;
+      pmw[65] = Pz.y;
+      dPx.x = dPy.x = dPz.x = 0.0f;
+    }
   }
-  if (srcmask || (GAIN && gcell)) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) en[q] = fmad(-G.cP[(m >> (2 * q)) & 3], dP[q] + src[q], en[q]);
+  if (s0 | s1 | ga | gb) {
+    // -1/eps of each node's component classes; a lane with neither a source
+    // nor gain adds fma(-1/eps, +0, e) = e
+    const float2 cx = make_float2(-G.cP[m0 & 3], -G.cP[m1 & 3]);
+    const float2 cy = make_float2(-G.cP[(m0 >> 2) & 3], -G.cP[(m1 >> 2) & 3]);
+    const float2 cz = make_float2(-G.cP[(m0 >> 4) & 3], -G.cP[(m1 >> 4) & 3]);
+    enx = fma2(cx, add2(dPx, srx), enx);
+    eny = fma2(cy, add2(dPy, sry), eny);
+    enz = fma2(cz, add2(dPz, srz), enz);
   }
-  if (j == 0 || pl.pecz) en[0] = 0.0f;
-  if (i == 0 || pl.pecz) en[1] = 0.0f;
-  if (i == 0 || j == 0) en[2] = 0.0f;
-  if (GAIN && gcell) {
-    const float hx_ = 0.5f * (en[0] + ec[0]), hy_ = 0.5f * (en[1] + ec[1]), hz_ = 0.5f * (en[2] + ec[2]);
-    const float r = G.q * fmad(hz_, dP[2], fmad(hy_, dP[1], hx_ * dP[0]));
-    const float inc1 = fmad(G.w[0], r, fmad(G.D[0][2], gs.d3, fmad(G.D[0][1], gs.d2, G.D[0][0] * gs.d1)));
-    const float inc2 = fmad(G.w[1], r, fmad(G.D[1][2], gs.d3, fmad(G.D[1][1], gs.d2, G.D[1][0] * gs.d1)));
-    const float inc3 = fmad(G.w[2], r, fmad(G.D[2][2], gs.d3, fmad(G.D[2][1], gs.d2, G.D[2][0] * gs.d1)));
+  if (c.j == 0 || pl.pecz) enx = make_float2(0.0f, 0.0f);
+  if (c.i0 == 0) eny.x = 0.0f;
+  if (pl.pecz) eny = make_float2(0.0f, 0.0f);
+  if (c.i0 == 0) enz.x = 0.0f;
+  if (c.j == 0) enz = make_float2(0.0f, 0.0f);
+  if (GAIN && (ga || gb)) {
+    const float2 d3 = ld2(gw + 32 * W::DN + 64);
+    const float2 k1 = ld2(gw + 32 * W::CMP), k2 = ld2(gw + 32 * W::CMP + 32), k3 = ld2(gw + 32 * W::CMP + 64);
+    const float2 half = bc2(0.5f);
+    const float2 hx_ = mul2(half, add2(enx, ex)), hy_ = mul2(half, add2(eny, ey)), hz_ = mul2(half, add2(enz, ez));
+    const float2 r = mul2(bc2(G.q), fma2(hz_, dPz, fma2(hy_, dPy, mul2(hx_, dPx))));
+    const float2 inc1 = fma2(bc2(G.w[0]), r, fma2(bc2(G.D[0][2]), d3, fma2(bc2(G.D[0][1]), d2, mul2(bc2(G.D[0][0]), d1))));
+    const float2 inc2 = fma2(bc2(G.w[1]), r, fma2(bc2(G.D[1][2]), d3, fma2(bc2(G.D[1][1]), d2, mul2(bc2(G.D[1][0]), d1))));
+    const float2 inc3 = fma2(bc2(G.w[2]), r, fma2(bc2(G.D[2][2]), d3, fma2(bc2(G.D[2][1]), d2, mul2(bc2(G.D[2][0]), d1))));
     // compensated (Kahan) accumulation of the population deviations
-    const float y1 = inc1 - gs.c1, y2 = inc2 - gs.c2, y3 = inc3 - gs.c3;
-    const float t1 = gs.d1 + y1, t2 = gs.d2 + y2, t3 = gs.d3 + y3;
-    G.cmp[0][cidx] = (t1 - gs.d1) - y1;
-    G.cmp[1][cidx] = (t2 - gs.d2) - y2;
-    G.cmp[2][cidx] = (t3 - gs.d3) - y3;
-    G.dN[0][cidx] = t1;
-    G.dN[1][cidx] = t2;
-    G.dN[2][cidx] = t3;
+    const float2 y1 = sub2(inc1, k1), y2 = sub2(inc2, k2), y3 = sub2(inc3, k3);
+    const float2 t1 = add2(d1, y1), t2 = add2(d2, y2), t3 = add2(d3, y3);
+    const float2 n1 = sub2(sub2(t1, d1), y1), n2 = sub2(sub2(t2, d2), y2), n3 = sub2(sub2(t3, d3), y3);
+    float* dw = gw + 32 * W::DN;
+    float* kw = gw + 32 * W::CMP;
+    if (ga && gb) {
+      st2(kw, n1);
+      st2(kw + 32, n2);
+      st2(kw + 64, n3);
+      st2(dw, t1);
+      st2(dw + 32, t2);
+      st2(dw + 64, t3);
+    } else {
+      const int e = ga ? 0 : 1;
+      kw[e] = ga ? n1.x : n1.y;
+      kw[e + 32] = ga ? n2.x : n2.y;
+      kw[e + 64] = ga ? n3.x : n3.y;
+      dw[e] = ga ? t1.x : t1.y;
+      dw[e + 32] = ga ? t2.x : t2.y;
+      dw[e + 64] = ga ? t3.x : t3.y;
+    }
   }
 }
 
@@ -458,6 +527,11 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
     const int sstride = halo ? L::NHC : NC;
     const int xcol = hcol[0] - (hcol[0] / HW) * HW;  // column of node 0 in the x coefficient rows
     const long long pstride = (long long)px * ny;
+    // gain state of node 0 of each owned pair in plane 0, and the stride between planes
+    long long gbase[RY];
+#pragma unroll
+    for (int r = 0; r < RY; ++r) gbase[r] = (GAIN && !halo && valid[r]) ? gain_base(G, pc[r].i0, pc[r].j, 0) : 0;
+    const long long gplane = (long long)ny * G.gxb * (GainWords<float>::NW * 32);
 
     // slab axis whose CPML memory is fetched ahead: z for the planes of a z
     // slab, else x for pairs in an x slab, else y
@@ -685,21 +759,9 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
             if (gen_e) {
               const bool pec = pc[r].i0 == 0 || pc[r].j == 0 || pl.pecz;
               const bool gainpair = GAIN && G.gain && (((m0 | m1) >> 6) & 1);
-              if (src0[r] | src1[r] | pec | gainpair) {
-                const long long cidx = (long long)pc[r].j * px + pc[r].i0 + (long long)k * pstride;
-                float ec[3] = {ex.x, ey.x, ez.x}, en[3] = {enx.x, eny.x, enz.x};
-                node_extras<GAIN>(G, sg, pc[r].i0, pc[r].j, pl, sel, n, cidx, m0, src0[r], ec, en);
-                enx.x = en[0];
-                eny.x = en[1];
-                enz.x = en[2];
-                if (pc[r].own1) {
-                  float ec1[3] = {ex.y, ey.y, ez.y}, en1[3] = {enx.y, eny.y, enz.y};
-                  node_extras<GAIN>(G, sg, pc[r].i0 + 1, pc[r].j, pl, sel, n, cidx + 1, m1, src1[r], ec1, en1);
-                  enx.y = en1[0];
-                  eny.y = en1[1];
-                  enz.y = en1[2];
-                }
-              }
+              if (src0[r] | src1[r] | pec | gainpair)
+                pair_extras<GAIN>(G, sg, pc[r], pl, sel, n, GAIN ? gbase[r] + (long long)k * gplane : 0, m0, m1,
+                                  src0[r], src1[r], ex, ey, ez, enx, eny, enz);
             }
             // a node past the grid edge is never stored (its lane holds zeros)
             if (!pc[r].own1) enx.y = eny.y = enz.y = 0.0f;

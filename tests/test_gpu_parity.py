@@ -254,6 +254,32 @@ def test_fp64_gain_with_noise_matches_oracle():
     assert rel_l2(N, o.populations()[1:].transpose(0, 3, 2, 1)) <= 1e-14
 
 
+@pytest.mark.parametrize("kernel", ["tma", "pair", "plain"])
+def test_fp32_noise_kick_matches_oracle_deviates(kernel):
+    """One step from zero fields and steady populations leaves P~^1 =
+    noise_amp xi in every gain cell (xi: Box-Muller deviates of the Philox
+    stream), which isolates the binary32 deviates (special-function-unit log,
+    sin and cos) from the oracle's binary64 ones of the same counters: about
+    1e-6 relative, up to sqrt(2 x 2^-21.41) absolute where rho is tiny."""
+    gain = inputs.GainSpec(n_total=1e24, fa_hat=0.8, dw_rel=0.02, tau32=100e-15, tau21=1e-9, tau10=100e-15,
+                           pump=5e11, noise_amp=1e-3, init="steady")
+    spec = small_opal(n_cells=3, res=8, npml=5, precision="f32", source="dipole", gain=gain)
+    g = gpu_grid(spec)
+    g.set_kernel(kernel)
+    o = oracle_grid(spec, coef32=True)
+    g.step(1)
+    o.step(1)
+    P = g.read_gain(0)
+    Po = o.P.transpose(0, 3, 2, 1)
+    gcell = np.broadcast_to(o.gain_cell.transpose(2, 1, 0)[None], P.shape)
+    assert gcell.sum() > 1000
+    assert np.all(P[~gcell] == 0.0)
+    xi, xo = P[gcell] / 1e-3, Po[gcell] / 1e-3
+    assert rel_l2(xi, xo) <= 1e-5
+    assert np.max(np.abs(xi - xo)) <= 1.5e-3
+    assert abs(np.mean(xi)) < 0.02 and abs(np.std(xi) - 1.0) < 0.02
+
+
 def test_fp32_gain_short_run():
     gain = inputs.GainSpec(n_total=1e24, fa_hat=0.8, dw_rel=0.02, tau32=100e-15, tau21=1e-9, tau10=100e-15,
                            pump=5e11, noise_amp=1e-3, init="ground")
