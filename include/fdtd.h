@@ -194,8 +194,9 @@ int fdtd_step_n(fdtd_grid* g, int64_t n);
  * default tile), z-ranges of `zdepth` planes per work item (0: chosen from
  * the grid size; the TMA kernels cap it at 31), and grid_blocks > 0 makes the
  * launch persistent with that many blocks looping over the work items (0: one
- * block per item).  Results do not depend on the shape.  Needs bx, by >= 2,
- * bx*by a multiple of 32, <= 512. */
+ * block per item, except the paired kernel, which then runs one wave of
+ * resident blocks and fetches each block's next item ahead).  Results do not
+ * depend on the shape.  Needs bx, by >= 2, bx*by a multiple of 32, <= 512. */
 int fdtd_set_launch(fdtd_grid* g, int32_t bx, int32_t by, int32_t zdepth, int32_t grid_blocks);
 
 /* Step-kernel variant: 0 = automatic (the paired kernel for binary32 and
@@ -230,7 +231,7 @@ typedef struct fdtd_tune_result {
   int32_t kernel;       /* fdtd_set_kernel kind (0 = automatic)             */
   int32_t bx, by;       /* launch shape (by 0 = the kernel's default rows)  */
   int32_t zdepth;       /* planes per work item (0 = automatic)            */
-  int32_t grid_blocks;  /* persistent blocks (0 = one block per work item)  */
+  int32_t grid_blocks;  /* persistent blocks (0 = the kernel's default)     */
   int32_t candidates;   /* shapes timed                                     */
   double ms_per_step;   /* time of one step with the chosen shape           */
 } fdtd_tune_result;

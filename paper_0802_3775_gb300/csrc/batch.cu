@@ -155,8 +155,11 @@ struct BatchImpl final : BatchBase {
     const auto ev = timed ? timer.next() : std::pair<cudaEvent_t, cudaEvent_t>{nullptr, nullptr};
     if (ev.first) cudaEventRecord(ev.first, stream);
     if (pair)
+      // one block per item unless set: the members' items differ in cost,
+      // and the hardware's block dispatch balances them better than a
+      // persistent grid's fixed stride (measured)
       e = launch_step_pair(reinterpret_cast<const StepGrid<float>*>(d_sg), d_tma, d_items, (int)items.size(), offset,
-                           oy, gain, grid_blocks, stream);
+                           oy, gain, grid_blocks > 0 ? grid_blocks : (int)items.size(), stream);
     else if (tma)
       e = launch_step_tma<T>(d_sg, d_tma, d_items, (int)items.size(), offset, oy, gain, grid_blocks, stream);
     else

@@ -419,8 +419,14 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
     // grading coefficients of the columns, rows and planes this item touches
     // (joined to the first plane's copy group; visible after the barrier below)
     {
-      const bool any_slab = G.Sd[0] || G.Sd[1] || G.Sd[2];
-      for (int e = tid; any_slab && e < L::CXN + L::CYN + 6 * (NP - 1); e += OX * OY) {
+      // only the axes whose slabs the item's columns (x0-1 .. x0+31), rows
+      // (y0-1 .. y0+OY-1) or planes (kstart .. z1-1) reach: no other entry is read
+      const bool tsx = G.Sd[0] && (x0 - 1 < G.L[0] || x0 + OX - 1 >= nx - G.L[1]);
+      const bool tsy = G.Sd[1] && (y0 - 1 < G.L[2] || y0 + OY - 1 >= ny - G.L[3]);
+      const bool tsz = G.Sd[2] && (kstart < G.L[4] || z1 - 1 >= G.nz - G.L[5]);
+      const int e0 = tsx ? 0 : (tsy ? L::CXN : L::CXN + L::CYN);
+      const int e1 = tsz ? L::CXN + L::CYN + 6 * (NP - 1) : (tsy ? L::CXN + L::CYN : (tsx ? L::CXN : 0));
+      for (int e = e0 + tid; e < e1; e += OX * OY) {
         int a, pos;
         T* dst;
         if (e < L::CXN) {
@@ -432,7 +438,8 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
         }
         const int hq = e % 6;  // CXN and CYN are multiples of 6
         const int lim = a == 0 ? nx : (a == 1 ? ny : G.nz);
-        if (G.Sd[a] && pos >= 0 && pos < lim) cp_async_elem(dst, G.prof[a][hq / 3][hq % 3] + pos);
+        const bool t = a == 0 ? tsx : (a == 1 ? tsy : tsz);
+        if (t && pos >= 0 && pos < lim) cp_async_elem(dst, G.prof[a][hq / 3][hq % 3] + pos);
       }
     }
     for (int p = 0; p < S; ++p) issue_psi(kstart + p, (int)((q0 + p) % S));

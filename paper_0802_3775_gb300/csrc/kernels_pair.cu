@@ -101,7 +101,10 @@ struct PairLayout {
   // CPML grading coefficients: x as [h*3+q][HW column], y as [row][h*3+q], z as [plane][h*3+q]
   static constexpr int CXN = 6 * HW, CYN = 6 * (OY + 1), CZN = 6 * kTmaZMax;
   static constexpr size_t coef_off = h_off + 2 * hbuf_bytes;
-  static constexpr size_t total = coef_off + (size_t)(CXN + CYN + CZN) * sizeof(float) + 128;
+  // the block's first kItemCache work items (a persistent block takes every gridDim-th item)
+  static constexpr int kItemCache = 32;
+  static constexpr size_t items_off = align128(coef_off + (size_t)(CXN + CYN + CZN) * sizeof(float));
+  static constexpr size_t total = items_off + kItemCache * sizeof(int4) + 128;
 };
 
 size_t step_pair_smem_bytes(int oy) { return oy == 8 ? PairLayout<8>::total : PairLayout<16>::total; }
@@ -380,6 +383,17 @@ __device__ __forceinline__ unsigned node_sources(const StepGrid<float>& G, int i
   return m;
 }
 
+// The next work item's planes that the producer fetches while the current
+// item finishes (kept in shared memory: only the producer reads or writes it).
+struct PairNext {
+  const CUtensorMap* fmap;
+  const CUtensorMap* mmap;
+  int x0, y0, kstart, sel;
+  int cnt;  // planes of the next item to issue from the current item's last refills (0..S-1)
+};
+
+static_assert(sizeof(PairNext) <= 64, "PairNext lives in the 128-byte barrier area after the stage barriers");
+
 #ifndef FDTD_PAIR_MIN_BLOCKS
 #define FDTD_PAIR_MIN_BLOCKS 2
 #endif
@@ -409,11 +423,13 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
   StepGrid<float>& G = *reinterpret_cast<StepGrid<float>*>(smem);
   double* sg = reinterpret_cast<double*>(smem + L::sg_off);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::bar_off);
+  PairNext& nxt = *reinterpret_cast<PairNext*>(smem + L::bar_off + 64);
   float4* ctab = reinterpret_cast<float4*>(smem + L::ctab_off);
   unsigned char* stages = smem + L::stage_off;
   float* cfx = reinterpret_cast<float*>(smem + L::coef_off);
   float* cfy = cfx + L::CXN;
   float* cfz = cfy + L::CYN;
+  int4* sitems = reinterpret_cast<int4*>(smem + L::items_off);
   const int tid = threadIdx.x;
   const bool halo = tid >= NTO;       // the last warp
   const int lane = tid & 31;
@@ -425,13 +441,16 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
     for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
     fence_mbar_init();
   }
+  if (tid < L::kItemCache && (int)blockIdx.x + tid * (int)gridDim.x < nitems)
+    sitems[tid] = items[blockIdx.x + tid * gridDim.x];
   __syncthreads();
 
-  unsigned ld = 0;     // plane loads issued by this block so far (same value in every thread)
+  unsigned ld = 0;     // planes of the items before this one (same value in every thread)
   unsigned phase = 0;  // bit s: parity of the next completion of stage s's barrier
+  int pf = 0;          // producer: planes of this item already issued by the previous item
   int cur = -1;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const int4 item = items[it];
+  for (int it = blockIdx.x, r = 0; it < nitems; it += gridDim.x, ++r) {
+    const int4 item = r < L::kItemCache ? sitems[r] : items[it];
     __syncthreads();
     const bool fresh = item.x != cur;
     if (fresh) {
@@ -469,9 +488,35 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
         tensormap_acquire(mmap);
       }
       fence_proxy_async_smem();
-      for (int p = 0; p < S && p < NP; ++p) issue((int)((q0 + p) % S), kstart + p);
+      for (int p = pf; p < S && p < NP; ++p) issue((int)((q0 + p) % S), kstart + p);
+      pf = 0;
+      // the next item of this block: its first planes are issued into the
+      // stages that this item's last planes free (same grid step, so the
+      // planes it reads are not written by this launch)
+      nxt.cnt = 0;
+      const int nit = it + (int)gridDim.x;
+      if (nit < nitems && NP >= S) {
+        const int4 ni = r + 1 < L::kItemCache ? sitems[r + 1] : items[nit];
+        // the same grid's step and limit are in the block's record
+        const StepGrid<float>* ng = grids + ni.x;
+        const long long nn = ni.x == item.x ? n : ng->step + offset;
+        if (nn < (ni.x == item.x ? G.step_end : ng->step_end)) {
+          const int nz0 = ni.w & 0xffff, nz1 = (ni.w >> 16) & 0xffff;
+          const int nks = nz0 > 0 ? nz0 - 1 : nz0;
+          nxt.fmap = &maps[ni.x].fields;
+          nxt.mmap = &maps[ni.x].mat;
+          if (ni.x != item.x) {
+            tensormap_acquire(nxt.fmap);
+            tensormap_acquire(nxt.mmap);
+          }
+          nxt.x0 = ni.y;
+          nxt.y0 = ni.z;
+          nxt.kstart = nks;
+          nxt.sel = (int)(nn & 1);
+          nxt.cnt = min(S - 1, nz1 - nks + 1);
+        }
+      }
     }
-    ld = q0 + (unsigned)(NP < S ? NP : S);
 
     // this thread's node pairs: RY owned rows (i0, j), or one on the halo row / column
     bool valid[RY];   // node 0 of the pair is a grid node whose H this thread provides
@@ -583,8 +628,14 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
     // grading coefficients of the columns, rows and planes this item touches
     // (joined to the first plane's copy group; visible after the barrier below)
     {
-      const bool any_slab = G.Sd[0] || G.Sd[1] || G.Sd[2];
-      for (int e = tid; any_slab && e < L::CXN + L::CYN + 6 * (NP - 1); e += NT) {
+      // only the axes whose slabs the item's columns (x0-2 .. x0+31), rows
+      // (y0-1 .. y0+OY-1) or planes (kstart .. z1-1) reach: no other entry is read
+      const bool tsx = G.Sd[0] && (x0 - 2 < G.L[0] || x0 + L::OX - 1 >= nx - G.L[1]);
+      const bool tsy = G.Sd[1] && (y0 - 1 < G.L[2] || y0 + OY - 1 >= ny - G.L[3]);
+      const bool tsz = G.Sd[2] && (kstart < G.L[4] || z1 - 1 >= G.nz - G.L[5]);
+      const int e0 = tsx ? 0 : (tsy ? L::CXN : L::CXN + L::CYN);
+      const int e1 = tsz ? L::CXN + L::CYN + 6 * (NP - 1) : (tsy ? L::CXN + L::CYN : (tsx ? L::CXN : 0));
+      for (int e = e0 + tid; e < e1; e += NT) {
         int a, pos, hq;
         float* dst;
         if (e < L::CXN) {
@@ -600,7 +651,8 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
           a = 2; pos = kstart + rr / 6; dst = cfz + rr;
         }
         const int lim = a == 0 ? nx : (a == 1 ? ny : G.nz);
-        if (G.Sd[a] && pos >= 0 && pos < lim) cp_async_elem(dst, G.prof[a][hq / 3][hq % 3] + pos);
+        const bool t = a == 0 ? tsx : (a == 1 ? tsy : tsz);
+        if (t && pos >= 0 && pos < lim) cp_async_elem(dst, G.prof[a][hq / 3][hq % 3] + pos);
       }
     }
     for (int p = 0; p < S; ++p) issue_psi(kstart + p, (int)((q0 + p) % S));
@@ -723,10 +775,20 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
         return;
       }
       // nothing reads the fields of plane p's stage after this barrier: refill
-      // it with plane p + S while the owners update E
-      if (producer && p + S < NP) {
-        fence_proxy_async_smem();
-        issue(sk, kstart + p + S);
+      // it with plane p + S (or a first plane of the block's next item) while
+      // the owners update E
+      if (producer) {
+        if (p + S < NP) {
+          fence_proxy_async_smem();
+          issue(sk, kstart + p + S);
+        } else if (p + S - NP < nxt.cnt) {
+          fence_proxy_async_smem();
+          unsigned char* dst = stages + (size_t)sk * L::stage_bytes;
+          mbar_arrive_expect_tx(&full[sk], TX_BYTES);
+          tma_load_4d(dst, nxt.fmap, nxt.x0 - AX, nxt.y0 - 1, nxt.kstart + p + S - NP, nxt.sel * 6, &full[sk]);
+          tma_load_3d(dst + L::field_bytes, nxt.mmap, nxt.x0, nxt.y0, nxt.kstart + p + S - NP, &full[sk]);
+          ++pf;
+        }
       }
 
       if (active && !halo) {
@@ -829,10 +891,30 @@ int step_pair_blocks_per_sm(bool gain, int oy) {
   return nb > 0 ? nb : 1;
 }
 
+// Resident blocks of the paired kernel on the whole GPU (per template; the
+// occupancy query runs once).
+static int pair_resident_blocks(bool gain, int oy) {
+  static int cache[2][2] = {{0, 0}, {0, 0}};
+  int& v = cache[gain ? 1 : 0][oy == 8 ? 1 : 0];
+  if (v == 0) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0) {
+      cudaGetLastError();
+      sms = 1;
+    }
+    v = step_pair_blocks_per_sm(gain, oy) * sms;
+  }
+  return v;
+}
+
 cudaError_t launch_step_pair(const StepGrid<float>* grids, const TmaGrid* maps, const int4* items, int nitems,
                              int offset, int oy, bool gain, int grid_blocks, cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
-  const int blocks = (grid_blocks > 0 && grid_blocks < nitems) ? grid_blocks : nitems;
+  // grid_blocks 0: persistent, one wave of resident blocks, each taking every
+  // gridDim-th item and fetching its next item's first planes ahead
+  const int want = grid_blocks > 0 ? grid_blocks : pair_resident_blocks(gain, oy);
+  const int blocks = want < nitems ? want : nitems;
   const size_t smem = step_pair_smem_bytes(oy);
   if (oy == 8) {
     auto f = gain ? k_step_pair<true, 8, pair_rows(8)> : k_step_pair<false, 8, pair_rows(8)>;
