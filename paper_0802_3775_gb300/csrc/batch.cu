@@ -1,7 +1,7 @@
 // Batched stepping of many grids of mixed size: every time step of every
-// member is one launch of the step kernel over the concatenated work items
-// (optionally persistent: a fixed number of blocks looping over the items),
-// followed by one observation launch; k steps can be captured into a CUDA
+// member is one launch of each step kernel in use over the concatenated work
+// items of its members (optionally persistent: a fixed number of blocks
+// looping over the items), followed by one observation launch; k steps can be captured into a CUDA
 // graph and replayed.  Members keep their own step counters and limits, so a
 // member that reaches its limit stops being updated while the others go on.
 //
@@ -25,25 +25,46 @@ namespace fdtd {
 
 template <typename T>
 struct BatchImpl final : BatchBase {
+  // Members stepped by one kernel: the paired kernel (kind 3), the TMA
+  // kernel (2) or the plain-load kernel (1), each with one tile shape.
+  struct Group {
+    bool gain = false;
+    int oy = 8;  // tile rows (TMA kernels) or rows of the plain kernel's tile less its halo row
+    std::vector<int4> items;
+    int4* d_items = nullptr;
+  };
   StepGrid<T>* d_sg = nullptr;
   ObsGrid<T>* d_og = nullptr;
   TmaGrid* d_tma = nullptr;
-  int4* d_items = nullptr;
   int4* d_oitems = nullptr;
-  std::vector<int4> items, oitems;
-  bool gain = false;
-  bool pair = false;  // every member on the paired binary32 kernel
-  int oy = 8;
+  std::vector<int4> oitems;
+  Group groups[4];  // by kernel kind (index 0 unused)
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
   int graph_built_for = 0;
+  // second stream for the TMA group when the paired group runs too: the two
+  // launches of a step overlap (one kernel's blocks fill the SMs that the
+  // other's tail leaves idle)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 
   ~BatchImpl() override {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
+    if (side) {
+      cudaStreamSynchronize(side);
+      cudaStreamDestroy(side);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
   }
 
-  // Records of every member in the batch's own tables, items re-indexed.
+  static int kind_of(const GridBase* g) { return g->uses_pair() ? 3 : (g->uses_tma() ? 2 : 1); }
+
+  // Records of every member in the batch's own tables, items re-indexed and
+  // grouped by the members' kernels (kernel 0: each member's automatic
+  // choice, so passive binary32 members take the paired kernel and gain
+  // members the TMA kernel, one launch each per time step).
   int build() override {
     const int ng = (int)grids.size();
     cudaError_t e;
@@ -51,7 +72,6 @@ struct BatchImpl final : BatchBase {
     for (GridBase* g : grids) {
       if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) return cuda_error(e, "sync member");
     }
-    gain = false;
     for (GridBase* g : grids) {
       g->kernel_kind = kernel_kind;
       g->bx = bx;
@@ -61,35 +81,41 @@ struct BatchImpl final : BatchBase {
       int r = g->finalized ? g->replan() : g->finalize();
       if (r != FDTD_OK) return r;
       g->finalized = true;
-      gain = gain || g->has_gain();
     }
-    // one launch serves all members: they must agree on the kernel and the
-    // tile; members that differ fall back to the most general kernel used
-    for (int round = 0; round < 3; ++round) {
-      int lo = 3, hi = 1;
-      for (GridBase* g : grids) {
-        const int v = g->uses_pair() ? 3 : (g->uses_tma() ? 2 : 1);
-        lo = std::min(lo, v);
-        hi = std::max(hi, v);
-      }
-      bool rows_agree = true;
-      for (GridBase* g : grids) rows_agree = rows_agree && g->tile_rows() == grids[0]->tile_rows();
-      if (lo == hi && rows_agree) break;
-      const int to = (lo == hi) ? 1 : lo;
-      for (GridBase* g : grids) {
-        g->kernel_kind = to;
+    // one launch per kernel serves its members: they must share the tile;
+    // a member whose rows differ from the first of its kernel's takes the
+    // plain-load kernel (whose tile the batch sets for all its members)
+    for (GridBase* g : grids) {
+      const int k = kind_of(g);
+      if (k == 1) continue;
+      const GridBase* first = nullptr;
+      for (GridBase* h : grids)
+        if (kind_of(h) == k) {
+          first = h;
+          break;
+        }
+      if (g->tile_rows() != first->tile_rows()) {
+        g->kernel_kind = 1;
         int r = g->replan();
         if (r != FDTD_OK) return r;
       }
     }
-    tma = !grids.empty() && grids[0]->uses_tma();
-    pair = !grids.empty() && grids[0]->uses_pair();
-    oy = grids.empty() ? 8 : grids[0]->tile_rows();
+    tma = false;
+    for (Group& gr : groups) {
+      gr.gain = false;
+      gr.items.clear();
+      gr.d_items = nullptr;
+    }
+    for (GridBase* g : grids) {
+      Group& gr = groups[kind_of(g)];
+      gr.gain = gr.gain || g->has_gain();
+      gr.oy = g->tile_rows();
+      tma = tma || g->uses_tma();
+    }
     std::vector<StepGrid<T>> hsg(ng);
     std::vector<ObsGrid<T>> hog(ng);
-    items.clear();
     oitems.clear();
-    std::vector<std::pair<double, int4>> ranked;
+    std::vector<std::pair<double, int4>> ranked[4];
     for (int q = 0; q < ng; ++q) {
       GridBase* g = grids[q];
       std::memcpy(&hsg[q], g->step_record(), sizeof(StepGrid<T>));
@@ -103,38 +129,50 @@ struct BatchImpl final : BatchBase {
       for (size_t r = 0; r < si.size(); ++r) {
         int4 it = si[r];
         it.x = q;
-        ranked.push_back({(double)r / (double)si.size(), it});
+        ranked[kind_of(g)].push_back({(double)r / (double)si.size(), it});
       }
       for (auto it : oi) {
         it.x = q;
         oitems.push_back(it);
       }
     }
-    std::stable_sort(ranked.begin(), ranked.end(),
-                     [](const std::pair<double, int4>& a, const std::pair<double, int4>& b) { return a.first < b.first; });
-    for (auto& w : ranked) items.push_back(w.second);
+    for (int k = 1; k <= 3; ++k) {
+      std::stable_sort(ranked[k].begin(), ranked[k].end(),
+                       [](const std::pair<double, int4>& a, const std::pair<double, int4>& b) { return a.first < b.first; });
+      for (auto& w : ranked[k]) groups[k].items.push_back(w.second);
+    }
     mem.release_all();
     d_sg = (StepGrid<T>*)mem.get(sizeof(StepGrid<T>) * ng);
     d_og = (ObsGrid<T>*)mem.get(sizeof(ObsGrid<T>) * ng);
     d_tma = tma ? (TmaGrid*)mem.get(sizeof(TmaGrid) * ng) : nullptr;
-    d_items = (int4*)mem.get(sizeof(int4) * std::max<size_t>(items.size(), 1));
     d_oitems = (int4*)mem.get(sizeof(int4) * std::max<size_t>(oitems.size(), 1));
-    if (!d_sg || !d_og || (tma && !d_tma) || !d_items || !d_oitems)
-      return set_error(FDTD_E_NOMEM, "device allocation failed (batch tables)");
+    bool ok = d_sg && d_og && (!tma || d_tma) && d_oitems;
+    for (int k = 1; k <= 3 && ok; ++k)
+      if (!groups[k].items.empty()) ok = (groups[k].d_items = (int4*)mem.get(sizeof(int4) * groups[k].items.size())) != nullptr;
+    if (!ok) return set_error(FDTD_E_NOMEM, "device allocation failed (batch tables)");
     if ((e = cudaMemcpyAsync(d_sg, hsg.data(), sizeof(StepGrid<T>) * ng, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(d_og, hog.data(), sizeof(ObsGrid<T>) * ng, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
       return cuda_error(e, "upload batch tables");
     if (tma)
       for (int q = 0; q < ng; ++q)
-        if ((e = cudaMemcpyAsync(d_tma + q, grids[q]->tma_device(), sizeof(TmaGrid), cudaMemcpyDeviceToDevice, stream)) != cudaSuccess)
+        if (grids[q]->uses_tma() &&
+            (e = cudaMemcpyAsync(d_tma + q, grids[q]->tma_device(), sizeof(TmaGrid), cudaMemcpyDeviceToDevice, stream)) != cudaSuccess)
           return cuda_error(e, "copy tensor maps");
-    if (!items.empty() &&
-        (e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
-      return cuda_error(e, "upload items");
+    for (int k = 1; k <= 3; ++k)
+      if (!groups[k].items.empty() &&
+          (e = cudaMemcpyAsync(groups[k].d_items, groups[k].items.data(), sizeof(int4) * groups[k].items.size(),
+                               cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return cuda_error(e, "upload items");
     if (!oitems.empty() &&
         (e = cudaMemcpyAsync(d_oitems, oitems.data(), sizeof(int4) * oitems.size(), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
       return cuda_error(e, "upload items");
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "build batch");
+    if (!groups[3].items.empty() && !groups[2].items.empty() && !side) {
+      if ((e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_error(e, "batch side stream");
+    }
     if (gexec) {
       cudaGraphExecDestroy(gexec);
       gexec = nullptr;
@@ -148,22 +186,38 @@ struct BatchImpl final : BatchBase {
     return FDTD_OK;
   }
 
-  size_t nitems() const override { return items.size(); }
+  size_t nitems() const override { return groups[1].items.size() + groups[2].items.size() + groups[3].items.size(); }
 
+  // One time step of every member: one launch per kernel group (paired,
+  // TMA, plain-load), then the observation launch.
   cudaError_t launch_one(int offset, bool timed) {
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
     const auto ev = timed ? timer.next() : std::pair<cudaEvent_t, cudaEvent_t>{nullptr, nullptr};
     if (ev.first) cudaEventRecord(ev.first, stream);
-    if (pair)
+    const Group& gp = groups[3];
+    const Group& gt = groups[2];
+    const bool two = side && !gp.items.empty() && !gt.items.empty();
+    if (two) {
+      if ((e = cudaEventRecord(fork, stream)) != cudaSuccess || (e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess)
+        return e;
+    }
+    if (!gp.items.empty())
       // one block per item unless set: the members' items differ in cost,
       // and the hardware's block dispatch balances them better than a
       // persistent grid's fixed stride (measured)
-      e = launch_step_pair(reinterpret_cast<const StepGrid<float>*>(d_sg), d_tma, d_items, (int)items.size(), offset,
-                           oy, gain, grid_blocks > 0 ? grid_blocks : (int)items.size(), stream);
-    else if (tma)
-      e = launch_step_tma<T>(d_sg, d_tma, d_items, (int)items.size(), offset, oy, gain, grid_blocks, stream);
-    else
-      e = launch_step<T>(d_sg, d_items, (int)items.size(), offset, bx, oy + 1, gain, grid_blocks, stream);
+      e = launch_step_pair(reinterpret_cast<const StepGrid<float>*>(d_sg), d_tma, gp.d_items, (int)gp.items.size(),
+                           offset, gp.oy, gp.gain, grid_blocks > 0 ? grid_blocks : (int)gp.items.size(), stream);
+    if (e == cudaSuccess && !gt.items.empty())
+      e = launch_step_tma<T>(d_sg, d_tma, gt.d_items, (int)gt.items.size(), offset, gt.oy, gt.gain, grid_blocks,
+                             two ? side : stream);
+    if (two) {
+      const cudaError_t e2 = cudaEventRecord(join, side);
+      const cudaError_t e3 = cudaStreamWaitEvent(stream, join, 0);
+      if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
+    }
+    const Group& gl = groups[1];
+    if (e == cudaSuccess && !gl.items.empty())
+      e = launch_step<T>(d_sg, gl.d_items, (int)gl.items.size(), offset, bx, gl.oy + 1, gl.gain, grid_blocks, stream);
     if (e != cudaSuccess) return e;
     if (ev.second) cudaEventRecord(ev.second, stream);
     if (!oitems.empty()) e = launch_observe<T>(d_og, d_oitems, (int)oitems.size(), offset, stream);

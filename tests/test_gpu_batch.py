@@ -31,8 +31,11 @@ def _state(g):
     return out
 
 
-@pytest.mark.parametrize("kernel,graph", [("tma", 0), ("tma", 7), ("plain", 0), ("plain", 5), ("pair", 0), ("pair", 7)])
+@pytest.mark.parametrize("kernel,graph", [("tma", 0), ("tma", 7), ("plain", 0), ("plain", 5), ("pair", 0), ("pair", 7),
+                                          ("auto", 0), ("auto", 7)])
 def test_batch_equals_members_alone(kernel, graph):
+    """kernel "auto": every member on its own automatic kernel (passive
+    binary32 members paired, gain members TMA), one launch per kernel."""
     from paper_0802_3775_gb300.fdtd import Batch, Grid
     specs = _members()
     alone = []
@@ -44,7 +47,7 @@ def test_batch_equals_members_alone(kernel, graph):
         g.close()
     grids = [Grid.from_spec(s) for s in specs]
     b = Batch(grids)
-    b.set_launch(kernel, 16 if kernel == "pair" else 8, 0, 0)
+    b.set_launch(kernel, {"pair": 16, "auto": 0}.get(kernel, 8), 0, 0)
     b.set_graph(graph)
     b.step(23)
     b.step(37)
