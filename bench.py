@@ -232,8 +232,12 @@ def run_gpu(args, rank, world, dist):
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     kernel = [stepper.kernel_time()]
-    kind, rows = grids[0].kernel_in_use()
-    kname = {1: "k_step", 2: "k_step_tma", 3: "k_step_pair"}[kind]
+    # step kernels in use (a batch launches one per kernel group each step)
+    names = {1: "k_step", 2: "k_step_tma", 3: "k_step_pair"}
+    in_use = sorted({g.kernel_in_use() for g in grids}, key=lambda kr: -kr[0])
+    kind, rows = in_use[0]
+    kname = " + ".join(names[k] for k, _ in in_use)
+    tiles = [[32 if k > 1 else None, r] for k, r in in_use]
     stepper.set_timing(False)
     stepper.sync()
     ms_max = rank_max(ms, dist)
@@ -255,13 +259,13 @@ def run_gpu(args, rank, world, dist):
         # DRAM bytes of one launch from an ncu capture of this workload, when
         # it was taken on the kernel this run uses
         zd = tune["zdepth"] if tune else 0
-        if rec.get("kernel") == kname and rec.get("tile") == [32 if kind > 1 else None, rows] and rec.get("zdepth") == zd:
+        if len(in_use) == 1 and rec.get("kernel") == kname and rec.get("tile") == tiles[0] and rec.get("zdepth") == zd:
             traffic = rec.get("dram_bytes_per_launch")
 
     # end to end through the public API with host inputs and host results
     e2e = run_e2e(args, specs, rank, dist)
 
-    launches = args.steps * 2 + 1
+    launches = args.steps * (len(in_use) + 1) + 1  # step kernel(s) and observation per step, one counter update
     result = {
         "metric": METRIC, "value": round(value, 1), "unit": "Mcell-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5),
@@ -271,13 +275,13 @@ def run_gpu(args, rank, world, dist):
                    "cells_per_gpu": cells, "l2": "state larger than L2 (%.0f MB per GPU)" %
                    (sum(s.cells for s in specs) * (49 if specs[0].precision == "f32" else 97) / 1e6),
                    "parallelism": f"replicas x{world} (independent realizations)",
-                   "launch": "direct launches; CUDA events around every 8th step-kernel launch of the timed region",
+                   "launch": "direct launches; CUDA events around the step-kernel launch(es) of every 8th time step of the timed region",
                    "launch_shape": ({"kernel": tune["kernel"], "by": tune["by"], "zdepth": tune["zdepth"],
                                      "grid_blocks": tune["grid_blocks"], "autotuned_over": tune["candidates"]}
                                     if tune else "library default")},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": kname, "tile": [32 if kind > 1 else None, rows],
+                     "kernel": kname, "tile": tiles[0] if len(tiles) == 1 else tiles,
                      "algorithmic_bytes_per_launch": bytes_step,
                      "mean_launch_ms": round(per_launch_ms, 5), "peak_source": f"{peak_kind} hbm_gbs"},
         "e2e": e2e,

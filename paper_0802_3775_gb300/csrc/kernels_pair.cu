@@ -441,6 +441,9 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
     for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
     fence_mbar_init();
   }
+  // the launch before this one (observation or step) has finished
+  grid_dependency_wait();
+  allow_dependents();
   if (tid < L::kItemCache && (int)blockIdx.x + tid * (int)gridDim.x < nitems)
     sitems[tid] = items[blockIdx.x + tid * gridDim.x];
   __syncthreads();
@@ -919,13 +922,13 @@ cudaError_t launch_step_pair(const StepGrid<float>* grids, const TmaGrid* maps, 
   if (oy == 8) {
     auto f = gain ? k_step_pair<true, 8, pair_rows(8)> : k_step_pair<false, 8, pair_rows(8)>;
     cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    f<<<blocks, PairThreads<8, pair_rows(8)>::NT, smem, st>>>(grids, maps, items, nitems, offset);
-  } else {
-    auto f = gain ? k_step_pair<true, 16, pair_rows(16)> : k_step_pair<false, 16, pair_rows(16)>;
-    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    f<<<blocks, PairThreads<16, pair_rows(16)>::NT, smem, st>>>(grids, maps, items, nitems, offset);
+    return launch_programmatic(f, dim3(blocks), dim3(PairThreads<8, pair_rows(8)>::NT), smem, st, grids, maps, items,
+                               nitems, offset);
   }
-  return cudaGetLastError();
+  auto f = gain ? k_step_pair<true, 16, pair_rows(16)> : k_step_pair<false, 16, pair_rows(16)>;
+  cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return launch_programmatic(f, dim3(blocks), dim3(PairThreads<16, pair_rows(16)>::NT), smem, st, grids, maps, items,
+                             nitems, offset);
 }
 
 }  // namespace fdtd
