@@ -76,7 +76,7 @@ WORKLOAD_TEXT = {
     "planewave64": "as planewave but FP64 (plain single-run FP64 GPU path)",
     "batch": "64 disorder realizations of mixed size (4^3..8^3 unit cells at 16..20 cells/a + 12-cell CPML, "
              "sigma U(0,10%)), even ones passive [111] plane-wave runs, odd ones four-level lasing runs, FP32, "
-             "all stepped together by one step-kernel launch per time step",
+             "all stepped together: per time step one launch of each step kernel in use over its members' work items",
 }
 
 

@@ -218,8 +218,8 @@ int fdtd_batch_autotune(fdtd_batch* b, int32_t trial_steps, fdtd_tune_result* ou
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaGetLastError();
     const bool gain = std::any_of(B->grids.begin(), B->grids.end(), [](GridBase* g) { return g->has_gain() != 0; });
-    std::vector<Candidate> cands = {{0, 32, 0, 0, 0},      {0, 32, 0, 24, 0}, {2, 32, 8, 0, 0}, {2, 32, 4, 0, 0},
-                                    {2, 32, 8, 8, 0},      {2, 32, 8, 0, 2 * sms}, {2, 32, 8, 24, 0}};
+    std::vector<Candidate> cands = {{0, 32, 0, 0, 0}, {0, 32, 0, 24, 0}, {0, 32, 0, 8, 0},      {2, 32, 8, 0, 0},
+                                    {2, 32, 4, 0, 0}, {2, 32, 8, 8, 0},  {2, 32, 8, 0, 2 * sms}, {2, 32, 8, 24, 0}};
     if (B->grids.front()->precision() == FDTD_FP32) {
       cands.push_back({3, 32, 16, 0, 0});
       cands.push_back({3, 32, 16, 8, 0});
