@@ -164,6 +164,7 @@ struct GridImpl final : GridBase {
   int4* d_oitems = nullptr;
   std::vector<int4> items, oitems;
   int* d_err = nullptr;
+  ObsOverlap obs;  // observation launches beside the step launches
   double* d_energy = nullptr;
   double* d_epart = nullptr;
   unsigned int* d_ecount = nullptr;
@@ -187,7 +188,7 @@ struct GridImpl final : GridBase {
     const long long nc = ncell;
     px = (desc.nx + 15) / 16 * 16;
     nstore = (long long)px * desc.ny * desc.nz;
-    d_F = (T*)mem.get(sizeof(T) * 12 * (size_t)nstore);
+    d_F = (T*)mem.get(sizeof(T) * 6 * kFieldSets * (size_t)nstore);
     uint8_t* mat = (uint8_t*)mem.get((size_t)nstore);
     d_tma = (TmaGrid*)mem.get(sizeof(TmaGrid));
     d_err = (int*)mem.get(sizeof(int) * 4);
@@ -199,7 +200,8 @@ struct GridImpl final : GridBase {
     if (!d_F || !mat || !d_tma || !d_err || !d_energy || !d_epart || !d_ecount || !d_sg || !d_og)
       return set_error(FDTD_E_NOMEM, "device allocation failed (%lld cells)", nc);
     cudaError_t e;
-    if ((e = cudaMemsetAsync(d_F, 0, sizeof(T) * 12 * (size_t)nstore, stream)) != cudaSuccess) return cuda_error(e, "memset fields");
+    if ((e = cudaMemsetAsync(d_F, 0, sizeof(T) * 6 * kFieldSets * (size_t)nstore, stream)) != cudaSuccess)
+      return cuda_error(e, "memset fields");
     // background class in every E node of the grid; the pitch padding stays 0
     if ((e = cudaMemsetAsync(mat, 0, (size_t)nstore, stream)) != cudaSuccess) return cuda_error(e, "memset material");
     if ((e = cudaMemset2DAsync(mat, px, 0x15, desc.nx, (size_t)desc.ny * desc.nz, stream)) != cudaSuccess)
@@ -215,12 +217,13 @@ struct GridImpl final : GridBase {
     sg.err = d_err;
     sg.per = (desc.periodic[0] ? 1 : 0) | (desc.periodic[1] ? 2 : 0) | (desc.periodic[2] ? 4 : 0);
     for (int q = 0; q < 6; ++q) sg.L[q] = desc.npml[q];
-    for (int s = 0; s < 2; ++s)
+    for (int s = 0; s < kFieldSets; ++s)
       for (int c = 0; c < 6; ++c) {
         sg.F[s][c] = d_F + (size_t)(s * 6 + c) * nstore;
         og.F[s][c] = sg.F[s][c];
       }
     sg.mat = mat;
+    sg.nsets = og.nsets = 2;  // three once the grid is frozen on the paired kernel
     sg.step = 0;
     sg.step_end = (long long)0x7fffffffffffffffLL;
     og.step = 0;
@@ -528,7 +531,7 @@ struct GridImpl final : GridBase {
     TmaGrid h;
     std::memset(&h, 0, sizeof(h));
     const int AX = 16 / (int)sizeof(T);
-    const cuuint64_t fdim[4] = {(cuuint64_t)desc.nx, (cuuint64_t)desc.ny, (cuuint64_t)desc.nz, 12};
+    const cuuint64_t fdim[4] = {(cuuint64_t)desc.nx, (cuuint64_t)desc.ny, (cuuint64_t)desc.nz, 6 * kFieldSets};
     const cuuint64_t fstr[3] = {(cuuint64_t)px * sizeof(T), (cuuint64_t)px * desc.ny * sizeof(T),
                                 (cuuint64_t)nstore * sizeof(T)};
     const cuuint32_t fbox[4] = {(cuuint32_t)(kTmaOX + 2 * AX), (cuuint32_t)(tile_oy + 2), 1, 6};
@@ -567,7 +570,11 @@ struct GridImpl final : GridBase {
       if ((e = cudaMemsetAsync(og.counters, 0, sizeof(unsigned) * kMaxFlux, stream)) != cudaSuccess)
         return cuda_error(e, "memset counters");
     }
-    return replan();
+    const int r = replan();
+    // a grid frozen on the paired kernel cycles through three field sets, so
+    // its observation can run beside the next step (set once, at step 0)
+    if (r == FDTD_OK && steps == 0) sg.nsets = og.nsets = use_pair ? 3 : 2;
+    return r == FDTD_OK ? upload_tables() : r;
   }
 
   size_t items_cap = 0, oitems_cap = 0;
@@ -617,9 +624,13 @@ struct GridImpl final : GridBase {
     }
     n = std::min(n, std::max(0LL, step_limit - steps));
     long long done = 0;
+    // observation beside the next step's launch (paired kernel), else in line
+    const bool beside = use_pair && sg.nsets == 3 && !oitems.empty();
+    if (beside && (e = obs.ensure()) != cudaSuccess) return cuda_error(e, "observation stream");
     while (done < n) {
       const int chunk = (int)std::min<long long>(n - done, 1 << 20);
       for (int s = 0; s < chunk; ++s) {
+        if (beside && (e = obs.before_step(stream, s)) != cudaSuccess) return cuda_error(e, "order");
         const auto ev = timer.next();
         if (ev.first) cudaEventRecord(ev.first, stream);
         if (use_pair)
@@ -635,9 +646,15 @@ struct GridImpl final : GridBase {
           if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "sync");
           timer.collect();
         }
-        if (!oitems.empty() && (e = launch_observe<T>(d_og, d_oitems, (int)oitems.size(), s, stream)) != cudaSuccess)
-          return cuda_error(e, "observe kernel");
+        if (beside)
+          e = obs.observe(stream, s, [&](cudaStream_t st) {
+            return launch_observe<T>(d_og, d_oitems, (int)oitems.size(), s, st);
+          });
+        else if (!oitems.empty())
+          e = launch_observe<T>(d_og, d_oitems, (int)oitems.size(), s, stream);
+        if (e != cudaSuccess) return cuda_error(e, "observe kernel");
       }
+      if (beside && (e = obs.join(stream, chunk)) != cudaSuccess) return cuda_error(e, "order");
       if ((e = launch_advance<T>(d_sg, d_og, 1, chunk, stream)) != cudaSuccess) return cuda_error(e, "advance");
       done += chunk;
       steps += chunk;
@@ -646,10 +663,7 @@ struct GridImpl final : GridBase {
     return FDTD_OK;
   }
 
-  int read_field(int comp, double* out) override {
-    const int sel = (int)(steps & 1);
-    return copy_out(sg.F[sel][comp], out);
-  }
+  int read_field(int comp, double* out) override { return copy_out(sg.F[steps % sg.nsets][comp], out); }
 
   // word w of every node's gain state -> double[nz][ny][nx] on the host (one
   // strided copy: each 32-node record contributes its run of word w)
@@ -686,7 +700,8 @@ struct GridImpl final : GridBase {
     std::vector<T> h((size_t)ncell);
     for (long long q = 0; q < ncell; ++q) h[q] = (T)in[q];
     cudaError_t e;
-    if ((e = cudaMemcpy2D(sg.F[0][comp], sizeof(T) * px, h.data(), sizeof(T) * desc.nx, sizeof(T) * desc.nx,
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "sync");
+    if ((e = cudaMemcpy2D(sg.F[steps % sg.nsets][comp], sizeof(T) * px, h.data(), sizeof(T) * desc.nx, sizeof(T) * desc.nx,
                           (size_t)desc.ny * desc.nz, cudaMemcpyHostToDevice)) != cudaSuccess)
       return cuda_error(e, "write");
     return FDTD_OK;
@@ -744,9 +759,8 @@ struct GridImpl final : GridBase {
   long long capacity() const override { return og.cap; }
 
   int energy(double* out) override {
-    const int sel = (int)(steps & 1);
     const T* F6[6];
-    for (int c = 0; c < 6; ++c) F6[c] = sg.F[sel][c];
+    for (int c = 0; c < 6; ++c) F6[c] = sg.F[steps % sg.nsets][c];
     cudaError_t e = launch_energy<T>(F6, d_mat, desc.eps[0], desc.eps[1], desc.eps[2], nstore, d_epart, d_ecount,
                                      d_energy, d_err, stream);
     if (e != cudaSuccess) return cuda_error(e, "energy kernel");
@@ -767,7 +781,7 @@ struct GridImpl final : GridBase {
   // state blobs for checkpointing: (device pointer, bytes)
   void state_blobs(std::vector<std::pair<void*, size_t>>& v) override {
     v.clear();
-    v.push_back({d_F, sizeof(T) * 12 * (size_t)nstore});
+    v.push_back({d_F, sizeof(T) * 6 * kFieldSets * (size_t)nstore});
     v.push_back({(void*)d_mat, (size_t)nstore});
     if (d_psi) v.push_back({d_psi, sizeof(T) * psi_words});
     if (d_gain) v.push_back({d_gain, sizeof(T) * gain_words});

@@ -47,6 +47,8 @@ struct BatchImpl final : BatchBase {
   // other's tail leaves idle)
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  ObsOverlap obs;  // observation launches beside the next step's launches
+  bool beside = false;  // every member on the paired kernel: observation on the side stream
 
   ~BatchImpl() override {
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -167,6 +169,9 @@ struct BatchImpl final : BatchBase {
         (e = cudaMemcpyAsync(d_oitems, oitems.data(), sizeof(int4) * oitems.size(), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
       return cuda_error(e, "upload items");
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "build batch");
+    beside = !oitems.empty() && groups[1].items.empty() && groups[2].items.empty();
+    for (int q = 0; q < ng; ++q) beside = beside && hsg[q].nsets == 3;  // three field sets in every member
+    if (beside && (e = obs.ensure()) != cudaSuccess) return cuda_error(e, "observation stream");
     if (!groups[3].items.empty() && !groups[2].items.empty() && !side) {
       if ((e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking)) != cudaSuccess ||
           (e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming)) != cudaSuccess ||
@@ -189,9 +194,10 @@ struct BatchImpl final : BatchBase {
   size_t nitems() const override { return groups[1].items.size() + groups[2].items.size() + groups[3].items.size(); }
 
   // One time step of every member: one launch per kernel group (paired,
-  // TMA, plain-load), then the observation launch.
+  // TMA, plain-load), then the observation launch on its own stream.
   cudaError_t launch_one(int offset, bool timed) {
     cudaError_t e = cudaSuccess;
+    if (beside && (e = obs.before_step(stream, offset)) != cudaSuccess) return e;
     const auto ev = timed ? timer.next() : std::pair<cudaEvent_t, cudaEvent_t>{nullptr, nullptr};
     if (ev.first) cudaEventRecord(ev.first, stream);
     const Group& gp = groups[3];
@@ -220,7 +226,12 @@ struct BatchImpl final : BatchBase {
       e = launch_step<T>(d_sg, gl.d_items, (int)gl.items.size(), offset, bx, gl.oy + 1, gl.gain, grid_blocks, stream);
     if (e != cudaSuccess) return e;
     if (ev.second) cudaEventRecord(ev.second, stream);
-    if (!oitems.empty()) e = launch_observe<T>(d_og, d_oitems, (int)oitems.size(), offset, stream);
+    if (beside)
+      e = obs.observe(stream, offset, [&](cudaStream_t st) {
+        return launch_observe<T>(d_og, d_oitems, (int)oitems.size(), offset, st);
+      });
+    else if (!oitems.empty())
+      e = launch_observe<T>(d_og, d_oitems, (int)oitems.size(), offset, stream);
     return e;
   }
 
@@ -241,6 +252,7 @@ struct BatchImpl final : BatchBase {
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       for (int s = 0; s < k && e == cudaSuccess; ++s) e = launch_one(s, false);
+      if (e == cudaSuccess && beside) e = obs.join(cs, k);
       if (e == cudaSuccess) e = launch_advance<T>(d_sg, d_og, (int)grids.size(), k, cs);
       cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
       if (e == cudaSuccess) e = e2;
@@ -282,6 +294,7 @@ struct BatchImpl final : BatchBase {
           timer.collect();
         }
       }
+      if (beside && (e = obs.join(stream, chunk)) != cudaSuccess) return cuda_error(e, "order");
       if ((e = launch_advance<T>(d_sg, d_og, (int)grids.size(), chunk, stream)) != cudaSuccess)
         return cuda_error(e, "advance");
       done += chunk;

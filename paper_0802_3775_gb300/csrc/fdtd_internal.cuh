@@ -21,6 +21,11 @@ constexpr int kEnergyBlocks = 256;
 constexpr int kTmaStages = FDTD_TMA_STAGES;  // planes resident or in flight per block (TMA step kernel)
 constexpr int kTmaOX = 32;        // owned tile width of the TMA step kernel
 constexpr int kTmaZMax = 32;      // planes of one TMA work item, its lower halo plane included
+// Field sets: a grid cycles through `nsets` (2 or 3) of the kFieldSets
+// allocated sets; set n % nsets holds E^n and H~^{n-1/2} and step n writes set
+// (n+1) % nsets.  With three, the observation of step n (sets n%3 and
+// (n+1)%3) can run while step n+1 writes the third set.
+constexpr int kFieldSets = 3;
 
 // Physical constants (CODATA; mu0 of the 2019 SI, hbar exact).
 constexpr double kC0 = 299792458.0;
@@ -66,7 +71,8 @@ struct StepGrid {
   int nsrc;
   long long step;       // steps completed before this launch sequence
   long long step_end;   // no update n >= step_end is performed
-  T* F[2][6];           // field sets (ping-pong): Ex Ey Ez Hx Hy Hz
+  T* F[kFieldSets][6];  // field sets (set n%nsets: E^n, H~^{n-1/2}): Ex Ey Ez Hx Hy Hz
+  int nsets;            // field sets in the cycle (2 or 3)
   const uint8_t* mat;   // material bytes
   T* psiE[3][2];        // E-curl CPML memory per axis, slot 0 -> comp (d+1)%3, 1 -> (d+2)%3
   T* psiH[2][3][2];     // H-curl CPML memory, ping-pong like the fields
@@ -94,7 +100,8 @@ struct ObsGrid {
   long long step_end;
   long long cap;        // recorder ring length (steps)
   double dx2_over_eta0; // dx^2 / eta0
-  const T* F[2][6];
+  const T* F[kFieldSets][6];
+  int nsets;
   int probe[kMaxProbes][3];
   T* probe_ring;        // [cap][nprobe][3]
   int flux_axis[kMaxFlux], flux_index[kMaxFlux];

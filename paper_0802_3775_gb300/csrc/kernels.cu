@@ -114,13 +114,14 @@ __global__ void __launch_bounds__(512) k_step(const StepGrid<T>* __restrict__ gr
     const bool vrow = yrow && vx && vyp;  // extra row node (i, j+1) exists
     const bool owner = tx > 0 && ty > 0 && i < nx && j < ny;
 
-    const int sel = (int)(n & 1);
-    const T* __restrict__ Ex = G.F[sel][0];
-    const T* __restrict__ Ey = G.F[sel][1];
-    const T* __restrict__ Ez = G.F[sel][2];
-    const T* __restrict__ Hx = G.F[sel][3];
-    const T* __restrict__ Hy = G.F[sel][4];
-    const T* __restrict__ Hz = G.F[sel][5];
+    const int sel = (int)(n & 1);                   // parity: CPML memory and gain slots
+    const int fs = (int)(n % G.nsets), fo = fs + 1 == G.nsets ? 0 : fs + 1;  // field sets read / written
+    const T* __restrict__ Ex = G.F[fs][0];
+    const T* __restrict__ Ey = G.F[fs][1];
+    const T* __restrict__ Ez = G.F[fs][2];
+    const T* __restrict__ Hx = G.F[fs][3];
+    const T* __restrict__ Hy = G.F[fs][4];
+    const T* __restrict__ Hz = G.F[fs][5];
 
     auto kwrap = [&](int k, bool& v) { return wrap_index(k, nz, perz, v); };
 
@@ -209,12 +210,12 @@ __global__ void __launch_bounds__(512) k_step(const StepGrid<T>* __restrict__ gr
         T enx, eny, enz;
         e_node<T, GAIN>(G, sg, col, pl, sel, n, gidx, m, gcell, gs, CoefGlobal<T>{&G, col.i, col.j, pl.k}, hz - sHz[tid - bx], hy - hPy, hx - hPx,
                         hz - sHz[tid - 1], hy - sHy[tid - 1], hx - sHx[tid - bx], eCx, eCy, eCz, enx, eny, enz);
-        G.F[sel ^ 1][0][cidx] = enx;
-        G.F[sel ^ 1][1][cidx] = eny;
-        G.F[sel ^ 1][2][cidx] = enz;
-        G.F[sel ^ 1][3][cidx] = hx;
-        G.F[sel ^ 1][4][cidx] = hy;
-        G.F[sel ^ 1][5][cidx] = hz;
+        G.F[fo][0][cidx] = enx;
+        G.F[fo][1][cidx] = eny;
+        G.F[fo][2][cidx] = enz;
+        G.F[fo][3][cidx] = hx;
+        G.F[fo][4][cidx] = hy;
+        G.F[fo][5][cidx] = hz;
       }
 
       hPx = hx;
@@ -338,7 +339,8 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
     const int x0 = item.y, y0 = item.z, z0 = item.w & 0xffff, z1 = (item.w >> 16) & 0xffff;
     const int kstart = z0 > 0 ? z0 - 1 : z0;
     const int NP = z1 - kstart + 1;  // planes kstart .. z1 (E of plane z1 feeds H of plane z1-1)
-    const int sel = (int)(n & 1);
+    const int sel = (int)(n & 1);                   // parity: CPML memory and gain slots
+    const int fs = (int)(n % G.nsets), fo = fs + 1 == G.nsets ? 0 : fs + 1;  // field sets read / written
     const CUtensorMap* fmap = &maps[item.x].fields;
     const CUtensorMap* mmap = &maps[item.x].mat;
     const unsigned q0 = ld;
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
       const int s = (int)(q % S);
       unsigned char* dst = stages + (size_t)s * L::stage_bytes;
       mbar_arrive_expect_tx(&full[s], TX_BYTES);
-      tma_load_4d(dst, fmap, x0 - AX, y0 - 1, plane, sel * 6, &full[s]);
+      tma_load_4d(dst, fmap, x0 - AX, y0 - 1, plane, fs * 6, &full[s]);
       tma_load_3d(dst + L::field_bytes, mmap, x0, y0, plane, &full[s]);
     };
     if (tid == 0) {
@@ -541,8 +543,8 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
         e_node<T, GAIN>(G, sg, col, pl, sel, n, gbase + (long long)k * gplane, m, gcell, gs, ocf, hz - sHz[oh - HW],
                         hy - hPy, hx - hPx,
                         hz - sHz[oh - 1], hy - sHy[oh - 1], hx - sHx[oh - HW], eox, eoy, eoz, enx, eny, enz, &pre);
-        // E^{n+1} and H~^{n+1/2} straight to set (n+1)&1 (a warp row: one contiguous segment)
-        T* const* Fo = G.F[sel ^ 1];
+        // E^{n+1} and H~^{n+1/2} straight to set (n+1)%3 (a warp row: one contiguous segment)
+        T* const* Fo = G.F[fo];
         Fo[0][cidx] = enx;
         Fo[1][cidx] = eny;
         Fo[2][cidx] = enz;
@@ -643,13 +645,13 @@ __global__ void __launch_bounds__(256) k_observe(const ObsGrid<T>* __restrict__ 
   const ObsGrid<T>& G = grids[it.x];
   const long long n = G.step + offset;
   if (n >= G.step_end) return;
-  const int sel = (int)(n & 1);
+  const int fs = (int)(n % G.nsets), fo = fs + 1 == G.nsets ? 0 : fs + 1;  // sets n and n+1
   const int px = G.px, ny = G.ny;
   const long long slot = n % G.cap;
   if (it.y < 0) {
     for (int q = threadIdx.x; q < G.nprobe * 3; q += blockDim.x) {
       const int p = q / 3, c = q % 3;
-      const T v = G.F[sel ^ 1][c][pidx3(G.probe[p][0], G.probe[p][1], G.probe[p][2], px, ny)];
+      const T v = G.F[fo][c][pidx3(G.probe[p][0], G.probe[p][1], G.probe[p][2], px, ny)];
       G.probe_ring[(slot * G.nprobe + p) * 3 + c] = v;
       if (!isfinite((double)v)) atomicOr(G.err, 1);
     }
@@ -662,12 +664,12 @@ __global__ void __launch_bounds__(256) k_observe(const ObsGrid<T>* __restrict__ 
   const int nu = G.flux_u1[f] - u0, nv = G.flux_v1[f] - v0;
   const long long total = (long long)nu * nv;
   const long long beg = total * part / nparts, end = total * (part + 1) / nparts;
-  const T* E1 = G.F[sel][d1];
-  const T* E2 = G.F[sel][d2];
-  const T* H1a = G.F[sel][3 + d1];
-  const T* H1b = G.F[sel ^ 1][3 + d1];
-  const T* H2a = G.F[sel][3 + d2];
-  const T* H2b = G.F[sel ^ 1][3 + d2];
+  const T* E1 = G.F[fs][d1];
+  const T* E2 = G.F[fs][d2];
+  const T* H1a = G.F[fs][3 + d1];
+  const T* H1b = G.F[fo][3 + d1];
+  const T* H2a = G.F[fs][3 + d2];
+  const T* H2b = G.F[fo][3 + d2];
   double acc = 0.0;
   for (long long q = beg + threadIdx.x; q < end; q += blockDim.x) {
     // consecutive threads take consecutive x (the fastest memory axis) when x is transverse

@@ -388,7 +388,7 @@ __device__ __forceinline__ unsigned node_sources(const StepGrid<float>& G, int i
 struct PairNext {
   const CUtensorMap* fmap;
   const CUtensorMap* mmap;
-  int x0, y0, kstart, sel;
+  int x0, y0, kstart, fs;  // fs: field set the next item reads
   int cnt;  // planes of the next item to issue from the current item's last refills (0..S-1)
 };
 
@@ -474,7 +474,8 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
     const int x0 = item.y, y0 = item.z, z0 = item.w & 0xffff, z1 = (item.w >> 16) & 0xffff;
     const int kstart = z0 > 0 ? z0 - 1 : z0;
     const int NP = z1 - kstart + 1;  // planes kstart .. z1 (E of plane z1 feeds H of plane z1-1)
-    const int sel = (int)(n & 1);
+    const int sel = (int)(n & 1);                   // parity: CPML memory and gain slots
+    const int fs = (int)(n % G.nsets), fo = fs + 1 == G.nsets ? 0 : fs + 1;  // field sets read / written
     const CUtensorMap* fmap = &maps[item.x].fields;
     const CUtensorMap* mmap = &maps[item.x].mat;
     const unsigned q0 = ld;
@@ -482,7 +483,7 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
     auto issue = [&](int s, int plane) {
       unsigned char* dst = stages + (size_t)s * L::stage_bytes;
       mbar_arrive_expect_tx(&full[s], TX_BYTES);
-      tma_load_4d(dst, fmap, x0 - AX, y0 - 1, plane, sel * 6, &full[s]);
+      tma_load_4d(dst, fmap, x0 - AX, y0 - 1, plane, fs * 6, &full[s]);
       tma_load_3d(dst + L::field_bytes, mmap, x0, y0, plane, &full[s]);
     };
     if (producer) {
@@ -515,7 +516,7 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
           nxt.x0 = ni.y;
           nxt.y0 = ni.z;
           nxt.kstart = nks;
-          nxt.sel = (int)(nn & 1);
+          nxt.fs = (int)(nn % (ni.x == item.x ? G.nsets : ng->nsets));
           nxt.cnt = min(S - 1, nz1 - nks + 1);
         }
       }
@@ -788,7 +789,7 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
           fence_proxy_async_smem();
           unsigned char* dst = stages + (size_t)sk * L::stage_bytes;
           mbar_arrive_expect_tx(&full[sk], TX_BYTES);
-          tma_load_4d(dst, nxt.fmap, nxt.x0 - AX, nxt.y0 - 1, nxt.kstart + p + S - NP, nxt.sel * 6, &full[sk]);
+          tma_load_4d(dst, nxt.fmap, nxt.x0 - AX, nxt.y0 - 1, nxt.kstart + p + S - NP, nxt.fs * 6, &full[sk]);
           tma_load_3d(dst + L::field_bytes, nxt.mmap, nxt.x0, nxt.y0, nxt.kstart + p + S - NP, &full[sk]);
           ++pf;
         }
@@ -831,11 +832,11 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
             // a node past the grid edge is never stored (its lane holds zeros)
             if (!pc[r].own1) enx.y = eny.y = enz.y = 0.0f;
           }
-          // E^{n+1} and H~^{n+1/2} of the pair straight to set (n+1)&1: 8-byte
+          // E^{n+1} and H~^{n+1/2} of the pair straight to set (n+1)%3: 8-byte
           // stores, a warp's half-row one 128-byte segment (px is even)
           if (valid[r]) {
             const long long cidx = (long long)pc[r].j * px + pc[r].i0 + (long long)k * pstride;
-            float* const* Fo = G.F[sel ^ 1];
+            float* const* Fo = G.F[fo];
             if (pc[r].own1) {
               st2(Fo[0] + cidx, enx);
               st2(Fo[1] + cidx, eny);

@@ -60,10 +60,10 @@ long long estimate_run_bytes(const fdtd_grid_desc& d, bool gain, int nprobe, int
   const long long px = (d.nx + 15) / 16 * 16;
   const long long nstore = px * d.ny * d.nz;
   const long long ncell = (long long)d.nx * d.ny * d.nz;
-  long long b = 12 * w * nstore + nstore;
+  long long b = 6 * kFieldSets * w * nstore + nstore;
   const int n3[3] = {d.nx, d.ny, d.nz};
   for (int a = 0; a < 3; ++a) b += 6 * w * (long long)(d.npml[2 * a] + d.npml[2 * a + 1]) * (ncell / n3[a]);
-  if (gain) b += (w == 4 ? 12 : 9) * w * nstore;
+  if (gain) b += (w == 4 ? 12 : 9) * w * ((d.nx + 31) / 32 * 32LL) * d.ny * d.nz;  // 32-node records
   b += (long long)d.record_capacity * (nprobe * 3 * w + nflux * 8);
   b += 6 * (long long)(d.nx + d.ny + d.nz) * w + 64 * 1024;
   return b;

@@ -166,6 +166,28 @@ def test_paired_kernel_is_bitwise_equal_to_tma_kernel(with_gain):
             assert np.array_equal(a, b)
 
 
+def test_observation_beside_the_step_equals_observation_in_line():
+    """A grid frozen on the paired kernel cycles three field sets and runs the
+    observation of step n on a second stream while step n+1 runs; stepped in
+    uneven chunks (1, 2, 3, ... steps per call, chunk ends join the streams)
+    its probes, flux series, fields and energy equal those of the same grid on
+    the TMA kernel with the observation in line."""
+    spec = _ragged_spec(None)
+    ref = gpu_grid(spec)
+    ref.set_kernel("tma")
+    ref.step(120)
+    g = gpu_grid(spec)
+    g.set_kernel("pair")
+    done = 0
+    for n in [1, 2, 3, 1, 7, 40]:
+        g.step(n)
+        done += n
+    g.step(120 - done)
+    for a, b in zip([g.read_fields(), g.read_probes(), g.read_flux(), np.array([g.field_energy()])],
+                    [ref.read_fields(), ref.read_probes(), ref.read_flux(), np.array([ref.field_energy()])]):
+        assert np.array_equal(a, b)
+
+
 def test_paired_kernel_matches_oracle_on_ragged_grid():
     gain = inputs.GainSpec(pump=5e11, noise_amp=1e-3, init="ground")
     spec = _ragged_spec(gain)
