@@ -391,8 +391,16 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
       if (a == 0) return plane * ny * G.Sd[0] + c.px0;
       return plane * G.Sd[1] * nx + c.py0;
     };
+    // slab axes the item's columns (x0-1 .. x0+31), rows (y0-1 .. y0+OY-1) or
+    // planes (kstart .. z1-1) reach; an item that reaches none copies no CPML
+    // memory or coefficients at all (no copy groups, so its waits are free)
+    const bool tsx = G.Sd[0] && (x0 - 1 < G.L[0] || x0 + OX - 1 >= nx - G.L[1]);
+    const bool tsy = G.Sd[1] && (y0 - 1 < G.L[2] || y0 + OY - 1 >= ny - G.L[3]);
+    const bool tsz = G.Sd[2] && (kstart < G.L[4] || z1 - 1 >= G.nz - G.L[5]);
+    const bool psi_item = tsx || tsy || tsz;
     // fetch this thread's CPML memory of `plane` into the stage slots (one commit group per plane)
     auto issue_psi = [&](int plane, int stage) {
+      if (!psi_item) return;
       T* slots = reinterpret_cast<T*>(stages + (size_t)stage * L::stage_bytes + L::field_bytes + L::mat_bytes);
       const int sz = plane_slab(plane);
       if (plane < z1 && (sz >= 0 || col_axis >= 0 || hrow || hcolm)) {
@@ -424,11 +432,7 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
     // grading coefficients of the columns, rows and planes this item touches
     // (joined to the first plane's copy group; visible after the barrier below)
     {
-      // only the axes whose slabs the item's columns (x0-1 .. x0+31), rows
-      // (y0-1 .. y0+OY-1) or planes (kstart .. z1-1) reach: no other entry is read
-      const bool tsx = G.Sd[0] && (x0 - 1 < G.L[0] || x0 + OX - 1 >= nx - G.L[1]);
-      const bool tsy = G.Sd[1] && (y0 - 1 < G.L[2] || y0 + OY - 1 >= ny - G.L[3]);
-      const bool tsz = G.Sd[2] && (kstart < G.L[4] || z1 - 1 >= G.nz - G.L[5]);
+      // only the axes whose slabs the item reaches: no other entry is read
       const int e0 = tsx ? 0 : (tsy ? L::CXN : L::CXN + L::CYN);
       const int e1 = tsz ? L::CXN + L::CYN + 6 * (NP - 1) : (tsy ? L::CXN + L::CYN : (tsx ? L::CXN : 0));
       for (int e = e0 + tid; e < e1; e += OX * OY) {
