@@ -676,8 +676,9 @@ __global__ void __launch_bounds__(256) k_observe(const ObsGrid<T>* __restrict__ 
   const T* H2b = G.F[fo][3 + d2];
   double acc = 0.0;
   for (long long q = beg + threadIdx.x; q < end; q += blockDim.x) {
-    // consecutive threads take consecutive x (the fastest memory axis) when x is transverse
-    const bool ufast = (d1 == 0);
+    // consecutive threads take consecutive x (the fastest memory axis) when x
+    // is transverse, else consecutive y (x-normal planes: rows one pitch apart)
+    const bool ufast = (d1 == 0) || (d == 0);
     const int u = u0 + (int)(ufast ? q % nu : q / nv), v = v0 + (int)(ufast ? q / nu : q % nv);
     int c[3];
     auto at = [&](int pp, int uu, int vv) {
