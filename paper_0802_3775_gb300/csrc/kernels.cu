@@ -8,7 +8,8 @@
 //             copies into a 3-stage mbarrier pipeline (the current plane, the
 //             next one, one in flight).  H on the -x / -y halo is recomputed
 //             so no block needs a neighbour's output of the same step; fields
-//             and H-side CPML memory are double-buffered (read set n&1, write
+//             cycle through nsets sets (read set n % nsets, write the next),
+//             H-side CPML memory is double-buffered (read set n&1, write
 //             set (n+1)&1); E-side CPML memory and gain state are updated in
 //             place by the owning thread; new values are stored from
 //             registers; H of a plane goes to one of two shared buffers, so
