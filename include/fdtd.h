@@ -406,7 +406,8 @@ int fdtd_field_energy_noalloc(const void* const fields[6], const uint8_t* mat, i
 
 /* Checkpoint: write / read every state array (fields, CPML slabs, gain state,
  * step count, recorders) to / from a file.  load requires a grid created
- * with the same description. */
+ * with the same description; it may step with another kernel than the grid
+ * that saved (the current field set is moved into its own cycle). */
 int fdtd_save_state(fdtd_grid* g, const char* path);
 int fdtd_load_state(fdtd_grid* g, const char* path);
 

@@ -585,7 +585,7 @@ int fdtd_batch_kernel_time(fdtd_batch* b, double* ms, int64_t* launches) {
   });
 }
 
-static const char kMagic[8] = {'F', 'D', 'T', 'D', 'C', 'K', 'P', '2'};
+static const char kMagic[8] = {'F', 'D', 'T', 'D', 'C', 'K', 'P', '3'};
 
 int fdtd_save_state(fdtd_grid* g, const char* path) {
   return guarded([&]() -> int {
@@ -603,7 +603,9 @@ int fdtd_save_state(fdtd_grid* g, const char* path) {
     ok = ok && std::fwrite(&G->desc, sizeof(G->desc), 1, f) == 1;
     const long long st = G->steps;
     const long long nb = (long long)blobs.size();
-    ok = ok && std::fwrite(&st, sizeof(st), 1, f) == 1 && std::fwrite(&nb, sizeof(nb), 1, f) == 1;
+    const int32_t ns = G->field_sets();
+    ok = ok && std::fwrite(&st, sizeof(st), 1, f) == 1 && std::fwrite(&nb, sizeof(nb), 1, f) == 1 &&
+         std::fwrite(&ns, sizeof(ns), 1, f) == 1;
     std::vector<unsigned char> buf;
     for (auto& b : blobs) {
       if (!ok) break;
@@ -633,9 +635,11 @@ int fdtd_load_state(fdtd_grid* g, const char* path) {
     char magic[8];
     fdtd_grid_desc d;
     long long st = 0, nb = 0;
+    int32_t ns = 0;
     bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0;
     ok = ok && std::fread(&d, sizeof(d), 1, f) == 1 && std::memcmp(&d, &G->desc, sizeof(d)) == 0;
-    ok = ok && std::fread(&st, sizeof(st), 1, f) == 1 && std::fread(&nb, sizeof(nb), 1, f) == 1;
+    ok = ok && std::fread(&st, sizeof(st), 1, f) == 1 && std::fread(&nb, sizeof(nb), 1, f) == 1 &&
+         std::fread(&ns, sizeof(ns), 1, f) == 1 && ns >= 2 && ns <= fdtd::kFieldSets;
     std::vector<std::pair<void*, size_t>> blobs;
     G->state_blobs(blobs);
     ok = ok && nb == (long long)blobs.size();
@@ -655,6 +659,8 @@ int fdtd_load_state(fdtd_grid* g, const char* path) {
     std::fclose(f);
     if (!ok) return set_error(FDTD_E_INVAL, "%s is not a checkpoint of an identically described grid", path);
     G->set_steps(st);
+    r = G->adopt_field_sets(ns);  // the saving grid may have cycled another number of field sets
+    if (r != FDTD_OK) return r;
     return G->replan();
   });
 }

@@ -789,6 +789,20 @@ struct GridImpl final : GridBase {
     if (og.flux_ring) v.push_back({og.flux_ring, sizeof(double) * (size_t)og.cap * og.nflux});
   }
 
+  int field_sets() const override { return sg.nsets; }
+  int adopt_field_sets(int from) override {
+    if (from < 2 || from > kFieldSets) return set_error(FDTD_E_INVAL, "field sets %d", from);
+    const int a = (int)(steps % from), b = (int)(steps % sg.nsets);
+    if (a == b) return FDTD_OK;
+    cudaError_t e;
+    for (int c = 0; c < 6; ++c)
+      if ((e = cudaMemcpyAsync(sg.F[b][c], sg.F[a][c], sizeof(T) * (size_t)nstore, cudaMemcpyDeviceToDevice, stream)) !=
+          cudaSuccess)
+        return cuda_error(e, "move the current field set");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "sync");
+    return FDTD_OK;
+  }
+
   void set_steps(long long s) override {
     steps = s;
     sg.step = og.step = s;

@@ -162,6 +162,10 @@ struct GridBase {
   virtual int error_flags(int* flags) = 0;
   virtual void state_blobs(std::vector<std::pair<void*, size_t>>& v) = 0;
   virtual void set_steps(long long s) = 0;
+  // field sets in the grid's cycle, and taking over a state whose fields
+  // cycled through `from` sets (a checkpoint of another kernel's grid)
+  virtual int field_sets() const = 0;
+  virtual int adopt_field_sets(int from) = 0;
   virtual const void* step_record() const = 0;
   virtual const void* obs_record() const = 0;
   virtual size_t step_record_size() const = 0;

@@ -394,6 +394,31 @@ def test_checkpoint_restart_is_bitwise():
     assert np.array_equal(c.read_probes(t0=120, count=80), a.read_probes(t0=120, count=80))
 
 
+@pytest.mark.parametrize("saver,loader", [("tma", "pair"), ("pair", "tma")])
+def test_checkpoint_moves_between_kernels(saver, loader):
+    """A grid on the paired kernel cycles three field sets, one on the TMA
+    kernel two: a checkpoint taken on one continues bitwise on the other."""
+    spec = small_opal(precision="f32", source="dipole")
+    a = gpu_grid(spec)
+    a.set_kernel(saver)
+    a.step(200)
+    ref = a.read_fields()
+    b = gpu_grid(spec)
+    b.set_kernel(saver)
+    b.step(122)  # 122 % 3 != 122 % 2: the current set moves
+    import tempfile, os
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        b.save_state(path)
+        c = gpu_grid(spec)
+        c.set_kernel(loader)
+        c.load_state(path)
+    c.step(78)
+    assert c.kernel_in_use()[0] == {"tma": 2, "pair": 3}[loader]
+    assert np.array_equal(c.read_fields(), ref)
+    assert np.array_equal(c.read_probes(t0=122, count=78), a.read_probes(t0=122, count=78))
+
+
 def test_nonfinite_values_are_reported():
     from paper_0802_3775_gb300.fdtd import FdtdError
     spec = small_opal(precision="f32", source="dipole")
