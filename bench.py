@@ -167,13 +167,13 @@ def rank_max(x: float, dist, device: str = "cuda") -> float:
 def configure_grid(args, g):
     if args.kernel != "auto":
         g.set_kernel(args.kernel)
-    if args.by:
-        g.set_launch(32, args.by, 0, 0)
+    if args.by or args.zdepth:
+        g.set_launch(32, args.by, args.zdepth, 0)
 
 
 def configure_batch(args, b):
-    if args.kernel != "auto" or args.by:
-        b.set_launch(args.kernel, args.by, 0, 0)
+    if args.kernel != "auto" or args.by or args.zdepth:
+        b.set_launch(args.kernel, args.by, args.zdepth, 0)
 
 
 def run_gpu(args, rank, world, dist):
@@ -202,7 +202,7 @@ def run_gpu(args, rank, world, dist):
     else:
         stepper = grids[0]
     tune = None
-    if not args.no_autotune and args.kernel == "auto" and not args.by:
+    if not args.no_autotune and args.kernel == "auto" and not args.by and not args.zdepth:
         # launch shape picked by timing the candidates on this workload (state restored)
         tune = stepper.autotune(trial_steps=10 if batch is None else 4)
     stepper.step(args.warmup)
@@ -267,7 +267,7 @@ def run_gpu(args, rank, world, dist):
             rec = json.load(f)
         # DRAM bytes of one launch from an ncu capture of this workload, when
         # it was taken on the kernel this run uses
-        zd = tune["zdepth"] if tune else 0
+        zd = tune["zdepth"] if tune else args.zdepth
         if len(in_use) == 1 and rec.get("kernel") == kname and rec.get("tile") == tiles[0] and rec.get("zdepth") == zd:
             traffic = rec.get("dram_bytes_per_launch")
 
@@ -506,6 +506,7 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma", "pair"],
                     help="step kernel (default: the library's automatic choice)")
     ap.add_argument("--by", type=int, default=0, help="tile rows of the step kernel (0: library default)")
+    ap.add_argument("--zdepth", type=int, default=0, help="planes per work item (0: library default)")
     ap.add_argument("--no-serve", action="store_true", help="skip the served request stream")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shape")
     args = ap.parse_args()
