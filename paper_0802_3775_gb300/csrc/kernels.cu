@@ -290,8 +290,24 @@ size_t step_tma_smem_bytes(int oy) {
 #define FDTD_TMA_MIN_BLOCKS 4
 #endif
 
+// Threads of a TMA-kernel block.  Binary32: OY warps, one row of 32 nodes
+// each, warps 0 and 1 also recomputing H on the -y halo row and the -x halo
+// column; 4 blocks per SM at 64 registers (two extra halo warps measured 5 %
+// slower on the 140^3 gain grid: fewer resident warps).  Binary64, whose
+// blocks shared memory limits to 2 per SM at 8 rows (3 at 4): two extra
+// warps recompute the halo row and column, so every warp carries one H
+// update per plane, with registers for 2 (3) blocks (the 184^3 binary64 step
+// 0.583 -> 0.531 ms; the register budget alone gave 0.569 ms).
+template <typename T, int OY>
+struct TmaThreads {
+  static constexpr bool HALO_WARPS = sizeof(T) == 8;
+  static constexpr int ROWS = OY + (HALO_WARPS ? 2 : 0);  // blockDim.y
+  static constexpr int NT = kTmaOX * ROWS;
+  static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? FDTD_TMA_MIN_BLOCKS * 8 / OY : (OY == 8 ? 2 : 3);
+};
+
 template <typename T, bool GAIN, int OY>
-__global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
+__global__ void __launch_bounds__(TmaThreads<T, OY>::NT, TmaThreads<T, OY>::MIN_BLOCKS)
     k_step_tma(const StepGrid<T>* __restrict__ grids, const TmaGrid* __restrict__ maps,
                const int4* __restrict__ items, int nitems, int offset) {
   using L = TmaLayout<T, OY>;
@@ -309,8 +325,13 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
   T* cfx = reinterpret_cast<T*>(smem + L::coef_off);
   T* cfy = cfx + L::CXN;
   T* cfz = cfy + L::CYN;
+  using TT = TmaThreads<T, OY>;
+  constexpr int NTALL = TT::NT;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * OX + tx;
+  const bool owner = !TT::HALO_WARPS || ty < OY;            // rows 0..OY-1 of the tile
+  const bool hwrow = TT::HALO_WARPS ? ty == OY : ty == 0;    // recomputes the -y halo row
+  const bool hwcol = TT::HALO_WARPS ? ty == OY + 1 : ty == 1;  // lanes 0..OY-1: the -x halo column
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
@@ -328,7 +349,7 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
     __syncthreads();
     const bool fresh = item.x != cur;
     if (fresh) {
-      load_record(grids + item.x, smem, tid, OX * OY);
+      load_record(grids + item.x, smem, tid, NTALL);
       cur = item.x;
     }
     __syncthreads();
@@ -365,7 +386,7 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
     __syncthreads();
 
     const int i = x0 + tx, j = y0 + ty;
-    const bool own = i < nx && j < ny;
+    const bool own = owner && i < nx && j < ny;
     constexpr int xo = AX;      // own node: staged column tx + AX, row ty + 1
     const int oe = (ty + 1) * BXT + tx + xo;
     const int oh = (ty + 1) * HW + tx + 1;
@@ -376,10 +397,10 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
     // gain state of the own node in plane 0 and the stride between planes
     const long long gbase = GAIN ? gain_base(G, own ? i : 0, own ? j : 0, 0) : 0;
     const long long gplane = (long long)ny * G.gxb * (GainWords<T>::NW * 32);
-    // halo node of this thread, if any: -y row (ty == 0) or -x column (ty == 1, tx < OY)
-    const bool hrow = (ty == 0) && y0 > 0 && i < nx;
-    const bool hcolm = (ty == 1) && tx < OY && x0 > 0 && y0 + tx < ny;
-    const int hid = ty == 0 ? tx : OX + tx;
+    // halo node of this thread, if any: -y row (x0 + tx, y0 - 1) or -x column (x0 - 1, y0 + tx)
+    const bool hrow = hwrow && y0 > 0 && i < nx;
+    const bool hcolm = hwcol && tx < OY && x0 > 0 && y0 + tx < ny;
+    const int hid = hwrow ? tx : OX + tx;
     const int hi = hrow ? i : x0 - 1, hj = hrow ? y0 - 1 : y0 + tx;
 
     // slab axis whose CPML memory is fetched ahead for a node: z for the planes
@@ -436,7 +457,7 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
       // only the axes whose slabs the item reaches: no other entry is read
       const int e0 = tsx ? 0 : (tsy ? L::CXN : L::CXN + L::CYN);
       const int e1 = tsz ? L::CXN + L::CYN + 6 * (NP - 1) : (tsy ? L::CXN + L::CYN : (tsx ? L::CXN : 0));
-      for (int e = e0 + tid; e < e1; e += OX * OY) {
+      for (int e = e0 + tid; e < e1; e += NTALL) {
         int a, pos;
         T* dst;
         if (e < L::CXN) {
@@ -509,12 +530,15 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
 
       T hx = T(0), hy = T(0), hz = T(0);
       const CoefShared<T> ocf{cfx + 6 * (tx + 1), cfy + 6 * (ty + 1), cz};
-      const T eox = Fk[oe], eoy = Fk[PL + oe], eoz = Fk[2 * PL + oe];  // E^n of the own node, for the E update
+      // E^n of the own node, for the E update
+      const T eox = owner ? Fk[oe] : T(0), eoy = owner ? Fk[PL + oe] : T(0), eoz = owner ? Fk[2 * PL + oe] : T(0);
       if (ok && own) h_at(col, ocf, oe, active, hx, hy, hz, &pre);
-      sHx[oh] = hx;
-      sHy[oh] = hy;
-      sHz[oh] = hz;
-      if (ty == 0 || (ty == 1 && tx < OY)) {
+      if (owner) {
+        sHx[oh] = hx;
+        sHy[oh] = hy;
+        sHz[oh] = hz;
+      }
+      if (hwrow || (hwcol && tx < OY)) {
         T a = T(0), b = T(0), c = T(0);
         if (ok && (hrow || hcolm)) {
           Column hc;
@@ -527,7 +551,7 @@ __global__ void __launch_bounds__(kTmaOX * OY, FDTD_TMA_MIN_BLOCKS * 8 / OY)
           const CoefShared<T> hcf{hrow ? cfx + 6 * (tx + 1) : cfx, hrow ? cfy : cfy + 6 * (tx + 1), cz};
           h_at(hc, hcf, hrow ? tx + xo : (tx + 1) * BXT + xo - 1, false, a, b, c, &hp);
         }
-        const int slot = ty == 0 ? tx + 1 : (tx + 1) * HW;
+        const int slot = hwrow ? tx + 1 : (tx + 1) * HW;
         sHx[slot] = a;
         sHy[slot] = b;
         sHz[slot] = c;
@@ -579,7 +603,7 @@ int step_blocks_per_sm(bool tma, bool gain, int bx, int by) {
     if (by == 4) f = gain ? (const void*)k_step_tma<T, true, 4> : (const void*)k_step_tma<T, false, 4>;
     else f = gain ? (const void*)k_step_tma<T, true, 8> : (const void*)k_step_tma<T, false, 8>;
     cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kTmaOX * by, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, by == 4 ? TmaThreads<T, 4>::NT : TmaThreads<T, 8>::NT, smem);
   } else {
     const size_t smem = step_smem_bytes<T>(bx, by);
     if (gain) {
@@ -603,8 +627,8 @@ static cudaError_t launch_tma_variant(const StepGrid<T>* grids, const TmaGrid* m
   const size_t smem = TmaLayout<T, OY>::total;
   cudaError_t e = cudaFuncSetAttribute(k_step_tma<T, GAIN, OY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return launch_programmatic(k_step_tma<T, GAIN, OY>, dim3(blocks), dim3(kTmaOX, OY), smem, st, grids, maps, items,
-                             nitems, offset);
+  return launch_programmatic(k_step_tma<T, GAIN, OY>, dim3(blocks), dim3(kTmaOX, TmaThreads<T, OY>::ROWS), smem, st,
+                             grids, maps, items, nitems, offset);
 }
 
 template <typename T>
