@@ -312,6 +312,7 @@ def run_gpu(args, rank, world, dist):
                 "steps_per_realization": steps_run,
                 "note": f"FP64 path: each realization stepped alone (automatic kernel), mean of the first {nsamp}; "
                         "accuracy of both against the FP64 oracle is asserted by the parity tests"}
+            result["fp32_vs_fp64"] = fp32_vs_fp64_errors(specs, grids)
         result["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(result))
     if batch is not None:
@@ -401,6 +402,33 @@ def serve_stream(capacity_mcell: float, count: int = 48, load: float = 0.7, seed
             "mcell_updates_per_s": round(sum(work) / wall / 1e6, 1), "failed": st["failed"],
             "stream": "Poisson arrivals, grid edge 64..160 incl. CPML, 2000..8000 steps, half passive half "
                       "lasing (served-workload generator scaled down), 150 GB budget, 64 slots, 500-step chunks"}
+
+
+def fp32_vs_fp64_errors(specs, grids, sample: int = 4):
+    """Per realization (the first `sample` of the workload): the binary32
+    member, as the batch left it, against the same realization stepped alone
+    in binary64 on the GPU for as many steps: relative L2 of the six fields and
+    of each flux series."""
+    import numpy as np
+
+    from paper_0802_3775_gb300.fdtd import Grid
+
+    out = []
+    for q, (s, g) in enumerate(zip(specs[:sample], grids[:sample])):
+        n = int(g.steps_done)
+        s64 = dataclasses.replace(s, precision="f64")
+        g64 = Grid.from_spec(s64, record_capacity=n + 16)
+        g64.step(n)
+        g64.sync()
+        F32, F64 = g.read_fields(), g64.read_fields()
+        rec = {"realization": q, "gain": s.gain is not None, "steps": n,
+               "fields_rel_l2": float(np.linalg.norm(F32 - F64) / max(np.linalg.norm(F64), 1e-300))}
+        if g.nflux:
+            T32, T64 = g.read_flux(), g64.read_flux()
+            rec["flux_rel_l2"] = float(np.linalg.norm(T32 - T64) / max(np.linalg.norm(T64), 1e-300))
+        out.append(rec)
+        g64.close()
+    return out
 
 
 def fp64_plain_rate(specs, steps_run: int, steps: int = 60, sample: int = 4):
