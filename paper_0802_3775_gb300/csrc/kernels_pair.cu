@@ -20,7 +20,12 @@
 //     registers (a half-warp writes one 128-byte row segment), and H of a
 //     plane goes to one of two shared buffers, so one block barrier per plane
 //     suffices (measured: as fast as a TMA store of an output tile, without
-//     its 12 KB of shared memory and its second barrier).
+//     its 12 KB of shared memory and its second barrier);
+//   - a persistent block (the default for single grids) issues the first two
+//     planes of its next item into the stages that its current item's last
+//     planes free, so an item starts with its planes already in flight;
+//   - on gain grids the polarization and populations of both nodes are
+//     updated with f32x2 operations on 8-byte words of the gain state.
 // Every operation is the one the scalar kernels perform on that node, in the
 // same order and rounding (f32x2 lanes round like the scalar instruction), so
 // the results equal theirs bit for bit.
