@@ -1,0 +1,56 @@
+"""The seeded workload generators follow their stated recipes (no GPU): the
+passive and lasing opals, the 64-realization mixed batch and the served
+request stream.  Only shapes, ranges and statistics are checked; the
+generators hold none of the method's arithmetic."""
+import math
+
+import numpy as np
+
+from paper_0802_3775_gb300 import inputs
+
+
+def test_planewave_and_lasing_workloads():
+    pw = inputs.opal_planewave_f32(ncell=8, res=20, npml=12, sigma=0.06)
+    assert pw.shape == (184, 184, 184) and pw.npml == (12,) * 6 and pw.gain is None
+    assert pw.eps == (11.9, 11.9, 1.0) and pw.precision == "f32"
+    las = inputs.opal_lasing_f32(ncell=6, res=20, npml=10, sigma=0.05)
+    assert las.shape == (140, 140, 140) and las.npml == (10,) * 6
+    g = las.gain
+    assert (g.n_total, g.fa_hat, g.dw_rel, g.tau32, g.tau21, g.tau10, g.noise_amp) == \
+        (1e24, 0.80, 0.02, 100e-15, 1e-9, 100e-15, 1e-6)
+    assert las.eps[2] == 2.25
+    # sphere radius a / (2 sqrt 2) in cells, jittered by sigma: the mean stays at r0
+    r0 = 20 / (2 * math.sqrt(2))
+    r = np.asarray(las.spheres).reshape(-1, 4)[:, 3]
+    assert abs(np.mean(r) / r0 - 1) < 0.02 and 0.02 < np.std(r / r0) < 0.08
+
+
+def test_mixed_batch_recipe():
+    specs = inputs.mixed_batch(64, seed=4000)
+    assert len(specs) == 64
+    for q, s in enumerate(specs):
+        n = s.shape[0]
+        assert s.shape == (n, n, n) and s.npml == (12,) * 6
+        res = int(s.res)
+        assert 16 <= res <= 20
+        ncell = (n - 24) / res
+        assert ncell == int(ncell) and 4 <= ncell <= 8
+        assert (s.gain is not None) == (q % 2 == 1)
+        assert s.seed == 4000 + q
+    # sizes and resolutions vary across the batch
+    assert len({s.shape for s in specs}) > 8 and len({s.res for s in specs}) == 5
+
+
+def test_request_stream_is_poisson_at_the_stated_rate():
+    stream = inputs.request_stream(400, rate_hz=4.0, seed=5000)
+    t = np.array([a for a, _ in stream])
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert np.all(gaps > 0)
+    assert abs(np.mean(gaps) - 0.25) < 0.03                 # mean arrival interval 1 / (4 per s)
+    assert abs(np.std(gaps) / np.mean(gaps) - 1.0) < 0.15   # exponential: coefficient of variation 1
+    edges = np.array([s.shape[0] for _, s in stream])
+    assert edges.min() >= 2 * 16 + 24 and edges.max() <= 200 + 20
+    steps = np.array([s.steps for _, s in stream])
+    assert steps.min() >= 5000 and steps.max() <= 50000
+    lasing = np.mean([s.gain is not None for _, s in stream])
+    assert 0.4 < lasing < 0.6
