@@ -59,12 +59,14 @@ __device__ __forceinline__ void gain_normals(unsigned long long seed, long long 
   const float u2 = ((float)(x.z >> 9) + 0.5f) * 0x1p-23f;
   const float u3 = ((float)(x.w >> 9) + 0.5f) * 0x1p-23f;
   constexpr float kTwoPi = 6.28318530717958648f;
-  const float rho = sqrtf(-2.0f * __logf(u0));
+  // log u < 0, but within its error bound the approximation may come out
+  // positive for u just below 1: clamp before the square root
+  const float rho = sqrtf(fmaxf(-2.0f * __logf(u0), 0.0f));
   float s, co;
   __sincosf(kTwoPi * (u1 - 0.5f), &s, &co);
   a = -(rho * co);
   b = -(rho * s);
-  c = -(sqrtf(-2.0f * __logf(u2)) * __cosf(kTwoPi * (u3 - 0.5f)));
+  c = -(sqrtf(fmaxf(-2.0f * __logf(u2), 0.0f)) * __cosf(kTwoPi * (u3 - 0.5f)));
 }
 
 __device__ __forceinline__ void gain_normals(unsigned long long seed, long long cell, long long step, double& a,
