@@ -162,3 +162,42 @@ def test_touching_fcc_fill_fraction(res):
         cls = (mat >> (2 * c)) & 3
         assert set(np.unique(cls)) <= {1, 2}
         assert abs(float(np.mean(cls == 2)) - target) < 0.005
+
+
+@pytest.mark.parametrize("kind,comp,d,where", [("H", 0, 2, "z+"), ("E", 1, 0, "x-"), ("E", 2, 1, "y+"), ("H", 2, 0, "x+")])
+def test_cpml_memory_is_the_recursive_convolution(kind, comp, d, where):
+    """Inside an absorbing slab the memory psi^n = b psi^{n-1} + c D^n is the
+    recursive convolution of the raw difference D with c b^k: scipy's lfilter
+    with numerator [c] and denominator [1, -b] reproduces the oracle's psi
+    series at a slab node from the recorded D series, and the difference the
+    update uses is D / kappa + psi (kappa_max = 3 here, so 1/kappa != 1)."""
+    import dataclasses
+    from scipy.signal import lfilter
+
+    from helpers import small_opal
+
+    class Recording(Oracle):
+        def _term(self, D, dd, cc, kk):
+            out = super()._term(D, dd, cc, kk)
+            if (kk, cc, dd) == (kind, comp, d):
+                self.rec.append((D[node], self.psi[kk][(cc, dd)][node], out[node]))
+            return out
+
+    spec = dataclasses.replace(small_opal(n_cells=2, res=8, npml=5, precision="f64", source="dipole"),
+                               cpml_kappa_max=3.0)
+    o = Recording.from_spec(spec)
+    n3 = o.shape
+    mid = [s // 2 for s in n3]
+    depth = 2  # nodes into the slab
+    axis = "xyz".index(where[0])
+    mid[axis] = depth if where[1] == "-" else n3[axis] - 1 - depth
+    node = tuple(mid)
+    o.rec = []
+    o.step(300)
+    D, psi, used = map(np.array, zip(*o.rec))
+    ik, b, c = (float(np.ravel(v)[node[d]]) for v in o.prof[kind][d])
+    assert 0.0 < b < 1.0 and c < 0.0 and 0.0 < ik < 1.0
+    assert np.max(np.abs(psi)) > 0.0
+    ref = lfilter([c], [1.0, -b], D)
+    assert np.max(np.abs(psi - ref)) <= 1e-13 * np.max(np.abs(psi))
+    assert np.max(np.abs(used - (ik * D + psi))) <= 1e-15 * np.max(np.abs(used))
