@@ -11,6 +11,9 @@
 * CPML reflection (the paper's absorbing layer, Sec. "Sample and numerical
   approach"): a probe near the layer agrees with a run in a much larger box
   to better than -40 dB until the outer box's echo returns;
+* CPML memory: at slab nodes of each kind the memory series equals the
+  recursive convolution of the raw differences (scipy's lfilter), and the
+  update uses D / kappa + psi;
 * rasterizer: brute force with scalar Python arithmetic on tiny grids equals the
   oracle bit for bit; touching fcc spheres fill pi/(3 sqrt 2) = 0.7405 of space.
 """
