@@ -9,7 +9,12 @@
 * lossless closed box with random inhomogeneous eps: the discrete energy
   1/2 sum H~^{n+1/2}.H~^{n+1/2} + 1/2 sum eps E^{n+1}.E^n is invariant;
 * a randomly excited PEC cavity rings at the discrete resonances, which
-  approach the continuum ones c pi sqrt(sum (m_d/L_d)^2) as O(dx^2).
+  approach the continuum ones c pi sqrt(sum (m_d/L_d)^2) as O(dx^2);
+* discrete Gauss laws: with random eps, gain cells, pump and noise kicks, the
+  node divergence of D~ = eps E + P~ and the cell divergence of H~ stay at
+  their initial values (the divergence of a Yee curl vanishes identically),
+  so a wrong index, sign or coefficient in a curl or in the polarization
+  coupling breaks them.
 """
 import math
 
@@ -155,3 +160,53 @@ def test_pec_cavity_resonances_from_ringing():
     f_disc = 2 * math.asin(o.S * math.sqrt(math.sin(math.pi / 16) ** 2 + math.sin(math.pi / 14) ** 2)) / (2 * math.pi)
     f_cont = o.S * 0.5 * math.sqrt((1 / 8) ** 2 + (1 / 7) ** 2)
     assert abs(f_disc - f_cont) / f_cont < 0.01
+
+
+def _div_nodes(F, periodic):
+    """Backward-difference divergence of an E-staggered field at the nodes."""
+    out = np.zeros(F.shape[1:])
+    for d in range(3):
+        lo = np.roll(F[d], 1, axis=d)
+        if not periodic[d]:
+            idx = [slice(None)] * 3
+            idx[d] = 0
+            lo[tuple(idx)] = 0.0
+        out += F[d] - lo
+    return out
+
+
+def _div_cells(F, periodic):
+    """Forward-difference divergence of an H-staggered field at the cell centres."""
+    out = np.zeros(F.shape[1:])
+    for d in range(3):
+        hi = np.roll(F[d], -1, axis=d)
+        if not periodic[d]:
+            idx = [slice(None)] * 3
+            idx[d] = -1
+            hi[tuple(idx)] = 0.0
+        out += hi - F[d]
+    return out
+
+
+def test_discrete_gauss_laws_with_gain_and_noise():
+    shape = (9, 8, 7)
+    periodic = (False, True, False)
+    o = Oracle(shape, 12, courant=0.5, periodic=periodic, eps=(1.0, 2.5, 11.9), seed=5)
+    o.set_material(inputs.random_material(shape, seed=31, gain_fraction=0.5, classes=(0, 1, 2)))
+    o.set_gain(n_total=1e24, fa_hat=0.8, dw_rel=0.02, tau32=100e-15, tau21=1e-9, tau10=100e-15,
+               pump=1e10, noise_amp=1e5)
+    o.set_fields_memory_order(inputs.random_fields(shape, seed=32, scale=1e7))
+    o._pec(o.E)
+    D0 = _div_nodes(o.eps_E * o.E + o.P, periodic)
+    B0 = _div_cells(o.H, periodic)
+    o.step(200)
+    # the polarization took part: it is of the field's size
+    assert np.max(np.abs(o.P)) > 0.1 * np.max(np.abs(o.E))
+    # nodes off the closed index-0 planes (tangential E held at zero there)
+    inner = (slice(1, None), slice(None), slice(1, None))
+    D1 = _div_nodes(o.eps_E * o.E + o.P, periodic)
+    assert np.max(np.abs(D1 - D0)[inner]) <= 1e-13 * np.max(np.abs(D0))
+    assert np.max(np.abs(_div_cells(o.H, periodic) - B0)) <= 1e-13 * np.max(np.abs(B0))
+    # leaving out the polarization, or the permittivity, breaks the law
+    assert np.max(np.abs(_div_nodes(o.eps_E * o.E, periodic) - D0)[inner]) > 1e-3 * np.max(np.abs(D0))
+    assert np.max(np.abs(_div_nodes(o.E + o.P, periodic) - D0)[inner]) > 1e-3 * np.max(np.abs(D0))
