@@ -11,6 +11,5 @@ Modules:
   gain       -- four-level rate matrix, equilibrium, Crank-Nicolson and
                 polarization-oscillator coefficients
   philox     -- Philox4x32-10 and Box-Muller, written from their definitions
-  analysis   -- spectra and decay fits of recorded series
 """
 from .fdtd import Oracle, waveform, C0, MU0, EPS0, ETA0, HBAR  # noqa: F401
