@@ -15,14 +15,18 @@
   recursive convolution of the raw differences (scipy's lfilter), and the
   update uses D / kappa + psi;
 * rasterizer: brute force with scalar Python arithmetic on tiny grids equals the
-  oracle bit for bit; touching fcc spheres fill pi/(3 sqrt 2) = 0.7405 of space.
+  oracle bit for bit; touching fcc spheres fill pi/(3 sqrt 2) = 0.7405 of space;
+* Poynting theorem: the flux a dipole pulse sends through the six faces of a
+  closed cube, summed over time, equals the energy that ends up outside it,
+  with a mismatch that falls as the square of the frequency (the faces' E and
+  H are averaged to the face centres, a second-order approximation).
 """
 import math
 
 import numpy as np
 import pytest
 
-from oracle import ETA0, Oracle, waveform
+from oracle import EPS0, ETA0, Oracle, waveform
 from oracle.rasterize import rasterize
 from paper_0802_3775_gb300 import inputs
 
@@ -204,3 +208,47 @@ def test_cpml_memory_is_the_recursive_convolution(kind, comp, d, where):
     ref = lfilter([c], [1.0, -b], D)
     assert np.max(np.abs(psi - ref)) <= 1e-13 * np.max(np.abs(psi))
     assert np.max(np.abs(used - (ik * D + psi))) <= 1e-15 * np.max(np.abs(used))
+
+
+def _radiated_through_cube(f0_hat, n=48, half=6, steps=145):
+    """z dipole at the centre of a closed lossless box; flux planes on the six
+    faces of the cube [c - half, c + half]^3, outward signs.  Returns the
+    time-summed outward flux of each face, the energy outside the cube and
+    the energy inside it after `steps` (the pulse has left the cube, its
+    echo from the walls has not come back)."""
+    o = Oracle((n, n, n), 6, courant=0.5)
+    c = n // 2
+    o.add_source(kind="point", comp=2, pos=(c, c, c), f0_hat=f0_hat, rel_bw=1.0)
+    lo, hi = c - half, c + half
+    for d in range(3):
+        o.add_flux(d, lo, -1.0, (lo, hi), (lo, hi))
+        o.add_flux(d, hi, 1.0, (lo, hi), (lo, hi))
+    for _ in range(steps - 1):
+        o.step(1)
+    E_prev = o.E.copy()
+    o.step(1)
+    # the discrete invariant 1/2 eps0 dx^3 (sum eps_r E^{n+1}.E^n + sum H~^{n+1/2}.H~^{n+1/2})
+    dens = np.concatenate([o.eps_E * o.E * E_prev, o.H * o.H])
+    inside = np.zeros((n, n, n), dtype=bool)
+    inside[lo:hi + 1, lo:hi + 1, lo:hi + 1] = True
+    w = 0.5 * EPS0 * o.dx ** 3
+    u_in = w * float(np.sum(dens[:, inside]))
+    u_out = w * float(np.sum(dens[:, ~inside]))
+    faces = o.flux_series().sum(axis=1) * o.dt
+    return faces, u_out, u_in
+
+
+def test_poynting_theorem_over_a_closed_cube():
+    m = {}
+    for f0 in (0.5, 0.35):
+        faces, u_out, u_in = _radiated_through_cube(f0)
+        assert u_in < 2e-3 * u_out
+        # the four side faces see the same flux, the two end faces of the dipole axis another
+        np.testing.assert_allclose(faces[:4], faces[0], rtol=1e-12)
+        m[f0] = (u_out - faces.sum()) / u_out
+        assert 0 < m[f0] < 0.025
+        # one face counted with the wrong orientation breaks the balance
+        bad = faces.sum() - 2 * faces[1]
+        assert abs(u_out - bad) / u_out > 0.2
+    # second order: the mismatch scales as f0^2
+    assert abs(m[0.5] / m[0.35] / (0.5 / 0.35) ** 2 - 1) < 0.03
