@@ -122,6 +122,12 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
+        return self.summarize(out)
+
+    @staticmethod
+    def summarize(out: str):
+        """Median SM clock under load, the maximum clock and the throttle
+        reasons seen, from nvidia-smi's csv rows (noheader, nounits)."""
         rows = []
         for line in out.strip().splitlines():
             parts = [p.strip() for p in line.split(",")]
