@@ -54,3 +54,40 @@ def test_request_stream_is_poisson_at_the_stated_rate():
     assert steps.min() >= 5000 and steps.max() <= 50000
     lasing = np.mean([s.gain is not None for _, s in stream])
     assert 0.4 < lasing < 0.6
+
+
+def test_sources_observers_and_seeds_of_the_workloads():
+    # passive: x-polarized sheet at z = npml + 2, flux plane at z = nz - npml - 3 over the interior faces
+    pw = inputs.opal_planewave_f32(ncell=4, res=10, npml=8, sigma=0.03, realization=5)
+    n = pw.shape[0]
+    (src,) = pw.sources
+    assert (src.kind, src.comp, src.axis, src.index, src.f0_hat, src.rel_bw) == ("sheet", 0, 2, 10, 0.80, 0.10)
+    (fl,) = pw.fluxes
+    assert (fl.axis, fl.index, fl.sign, fl.u, fl.v) == (2, n - 11, 1.0, (8, n - 9), (8, n - 9))
+    assert pw.seed == 1005 and pw.box_lo == (8,) * 3 and pw.box_hi == (n - 8,) * 3
+    # probes: 8 cells of the non-absorbing interior, drawn from PCG64(seed + 1)
+    assert pw.probes.shape == (8, 3)
+    assert np.all(pw.probes >= 8) and np.all(pw.probes < n - 8)
+    again = inputs.probe_cells(pw.shape, pw.npml, 8, seed=1006)
+    assert np.array_equal(pw.probes, again)
+    # lasing: six outward planes two cells inside the CPML, enclosing a closed box
+    las = inputs.opal_lasing_f32(ncell=3, res=10, npml=6, realization=2)
+    n = las.shape[0]
+    lo, hi = 8, n - 8
+    got = {(f.axis, f.index, f.sign, f.u, f.v) for f in las.fluxes}
+    assert got == {(d, i, s, (lo, hi), (lo, hi)) for d in range(3) for i, s in ((lo, -1.0), (hi, 1.0))}
+    assert las.sources == [] and las.seed == 2002 and las.gain.init == "steady"
+    # FP64 dipole: Ez point source at the centre cell
+    dp = inputs.opal_dipole_f64()
+    (src,) = dp.sources
+    assert dp.shape == (40, 40, 40) and dp.precision == "f64"
+    assert (src.kind, src.comp, src.pos) == ("point", 2, (20, 20, 20))
+
+
+def test_batch_members_per_rank_are_distinct_realizations():
+    a = inputs.mixed_batch(8, seed=4000)
+    b = inputs.mixed_batch(8, seed=5000)
+    assert [s.seed for s in a] == list(range(4000, 4008))
+    # the same member index on two ranks draws another size, resolution and disorder
+    diff = [(x.shape, x.res) != (y.shape, y.res) or not np.array_equal(x.spheres, y.spheres) for x, y in zip(a, b)]
+    assert all(diff)
