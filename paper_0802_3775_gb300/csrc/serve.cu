@@ -21,9 +21,12 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <exception>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <new>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -277,9 +280,24 @@ struct fdtd_server {
 
 using fdtd::set_error;
 
-extern "C" {
+namespace {
 
-int fdtd_server_create(const fdtd_server_desc* desc, void* stream, fdtd_server** out) {
+// No C++ exception leaves an entry point: host allocation failures (request
+// copies, the worker thread) come back as error codes.
+template <typename F>
+int guard(F&& f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return set_error(FDTD_E_NOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return set_error(FDTD_E_INVAL, "%s", e.what());
+  } catch (...) {
+    return set_error(FDTD_E_INVAL, "unknown error");
+  }
+}
+
+int server_create_impl(const fdtd_server_desc* desc, void* stream, fdtd_server** out) {
   (void)stream;
   if (!desc || !out) return set_error(FDTD_E_INVAL, "null argument");
   *out = nullptr;
@@ -298,12 +316,25 @@ int fdtd_server_create(const fdtd_server_desc* desc, void* stream, fdtd_server**
     delete s;
     return set_error(FDTD_E_CUDA, "stream creation failed");
   }
-  s->worker = std::thread([s] { s->loop(); });
-  *out = new fdtd_server{s};
+  auto* h = new (std::nothrow) fdtd_server{s};
+  if (h) {
+    try {
+      s->worker = std::thread([s] { s->loop(); });
+    } catch (const std::system_error&) {
+      delete h;
+      h = nullptr;
+    }
+  }
+  if (!h) {
+    cudaStreamDestroy(s->stream);
+    delete s;
+    return set_error(FDTD_E_NOMEM, "the server's worker thread could not start");
+  }
+  *out = h;
   return FDTD_OK;
 }
 
-int fdtd_server_destroy(fdtd_server* srv) {
+int server_destroy_impl(fdtd_server* srv) {
   if (!srv) return FDTD_OK;
   fdtd::Server* s = srv->impl;
   {
@@ -321,7 +352,7 @@ int fdtd_server_destroy(fdtd_server* srv) {
   return FDTD_OK;
 }
 
-int fdtd_submit(fdtd_server* srv, const fdtd_request* req, uint64_t* ticket) {
+int submit_impl(fdtd_server* srv, const fdtd_request* req, uint64_t* ticket) {
   if (!srv || !req || !ticket) return set_error(FDTD_E_INVAL, "null argument");
   fdtd::Server* s = srv->impl;
   if (req->steps < 1) return set_error(FDTD_E_INVAL, "steps must be >= 1");
@@ -362,7 +393,7 @@ int fdtd_submit(fdtd_server* srv, const fdtd_request* req, uint64_t* ticket) {
   return FDTD_OK;
 }
 
-int fdtd_poll(fdtd_server* srv, uint64_t ticket, fdtd_result* out, int32_t timeout_ms) {
+int poll_impl(fdtd_server* srv, uint64_t ticket, fdtd_result* out, int32_t timeout_ms) {
   if (!srv || !out) return set_error(FDTD_E_INVAL, "null argument");
   fdtd::Server* s = srv->impl;
   std::unique_lock<std::mutex> lk(s->mu);
@@ -383,7 +414,7 @@ int fdtd_poll(fdtd_server* srv, uint64_t ticket, fdtd_result* out, int32_t timeo
   return FDTD_OK;
 }
 
-int fdtd_result_probes(fdtd_server* srv, uint64_t ticket, double* out) {
+int result_probes_impl(fdtd_server* srv, uint64_t ticket, double* out) {
   if (!srv || !out) return set_error(FDTD_E_INVAL, "null argument");
   fdtd::Server* s = srv->impl;
   std::lock_guard<std::mutex> lk(s->mu);
@@ -394,7 +425,7 @@ int fdtd_result_probes(fdtd_server* srv, uint64_t ticket, double* out) {
   return FDTD_OK;
 }
 
-int fdtd_result_flux(fdtd_server* srv, uint64_t ticket, double* out) {
+int result_flux_impl(fdtd_server* srv, uint64_t ticket, double* out) {
   if (!srv || !out) return set_error(FDTD_E_INVAL, "null argument");
   fdtd::Server* s = srv->impl;
   std::lock_guard<std::mutex> lk(s->mu);
@@ -405,7 +436,7 @@ int fdtd_result_flux(fdtd_server* srv, uint64_t ticket, double* out) {
   return FDTD_OK;
 }
 
-int fdtd_result_release(fdtd_server* srv, uint64_t ticket) {
+int result_release_impl(fdtd_server* srv, uint64_t ticket) {
   if (!srv) return set_error(FDTD_E_INVAL, "null argument");
   fdtd::Server* s = srv->impl;
   std::lock_guard<std::mutex> lk(s->mu);
@@ -416,7 +447,7 @@ int fdtd_result_release(fdtd_server* srv, uint64_t ticket) {
   return FDTD_OK;
 }
 
-int fdtd_server_get_stats(fdtd_server* srv, fdtd_server_stats* out) {
+int server_get_stats_impl(fdtd_server* srv, fdtd_server_stats* out) {
   if (!srv || !out) return set_error(FDTD_E_INVAL, "null argument");
   fdtd::Server* s = srv->impl;
   std::lock_guard<std::mutex> lk(s->mu);
@@ -425,6 +456,42 @@ int fdtd_server_get_stats(fdtd_server* srv, fdtd_server_stats* out) {
   out->queued = (int32_t)s->queue.size();
   out->used_bytes = s->used_bytes;
   return FDTD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdtd_server_create(const fdtd_server_desc* desc, void* stream, fdtd_server** out) {
+  return guard([&] { return server_create_impl(desc, stream, out); });
+}
+
+int fdtd_server_destroy(fdtd_server* srv) {
+  return guard([&] { return server_destroy_impl(srv); });
+}
+
+int fdtd_submit(fdtd_server* srv, const fdtd_request* req, uint64_t* ticket) {
+  return guard([&] { return submit_impl(srv, req, ticket); });
+}
+
+int fdtd_poll(fdtd_server* srv, uint64_t ticket, fdtd_result* out, int32_t timeout_ms) {
+  return guard([&] { return poll_impl(srv, ticket, out, timeout_ms); });
+}
+
+int fdtd_result_probes(fdtd_server* srv, uint64_t ticket, double* out) {
+  return guard([&] { return result_probes_impl(srv, ticket, out); });
+}
+
+int fdtd_result_flux(fdtd_server* srv, uint64_t ticket, double* out) {
+  return guard([&] { return result_flux_impl(srv, ticket, out); });
+}
+
+int fdtd_result_release(fdtd_server* srv, uint64_t ticket) {
+  return guard([&] { return result_release_impl(srv, ticket); });
+}
+
+int fdtd_server_get_stats(fdtd_server* srv, fdtd_server_stats* out) {
+  return guard([&] { return server_get_stats_impl(srv, out); });
 }
 
 }  // extern "C"

@@ -72,3 +72,44 @@ def test_create_without_device_fails_loudly(lib):
     with pytest.raises(F.FdtdError) as e:
         F.Grid((8, 8, 8), 10, allocator=None)
     assert e.value.code == -3
+
+
+def test_batch_and_server_checks_without_gpu(lib):
+    import ctypes as C
+
+    from paper_0802_3775_gb300 import fdtd as F
+    from paper_0802_3775_gb300 import serve as S
+    L = S._lib()
+    h = C.c_void_p()
+    # batches: null handles and empty member lists
+    assert L.fdtd_batch_create(None, 0, None, C.byref(h)) == -1
+    assert L.fdtd_batch_set_launch(None, 0, 0, 0, 0) == -1
+    assert L.fdtd_batch_step_n(None, 1) == -1
+    assert L.fdtd_batch_sync(None) == -1
+    assert L.fdtd_batch_destroy(None) == 0
+    # server: null arguments and a description that admits nothing
+    assert L.fdtd_server_create(None, None, C.byref(h)) == -1
+    for bad in (S.ServerDesc(0, 4, 10, F.FP32, 0), S.ServerDesc(1 << 30, 0, 10, F.FP32, 0),
+                S.ServerDesc(1 << 30, 4, 0, F.FP32, 0)):
+        assert L.fdtd_server_create(C.byref(bad), None, C.byref(h)) == -1
+        assert b"positive" in L.fdtd_last_error()
+    t = C.c_uint64()
+    res = S.Result()
+    assert L.fdtd_submit(None, None, C.byref(t)) == -1
+    assert L.fdtd_poll(None, 0, C.byref(res), 0) == -1
+    assert L.fdtd_result_probes(None, 0, None) == -1
+    assert L.fdtd_result_flux(None, 0, None) == -1
+    assert L.fdtd_result_release(None, 0) == -1
+    assert L.fdtd_server_get_stats(None, None) == -1
+    assert L.fdtd_server_destroy(None) == 0
+
+
+def test_server_without_device_fails_loudly(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_0802_3775_gb300 import fdtd as F
+    from paper_0802_3775_gb300.serve import Server
+    with pytest.raises(F.FdtdError) as e:
+        Server(hbm_budget_bytes=1 << 30, max_slots=2, steps_per_chunk=10)
+    assert e.value.code == -3
