@@ -91,3 +91,24 @@ def test_batch_members_per_rank_are_distinct_realizations():
     # the same member index on two ranks draws another size, resolution and disorder
     diff = [(x.shape, x.res) != (y.shape, y.res) or not np.array_equal(x.spheres, y.spheres) for x, y in zip(a, b)]
     assert all(diff)
+
+
+def test_111_rotation_stacks_close_packed_layers_along_z():
+    # without disorder, the [111] lattice puts the sphere centres on planes
+    # normal to z spaced a / sqrt 3, each a triangular net of spacing a / sqrt 2
+    res = 10.0
+    sph = inputs.fcc_opal_spheres((0, 0, 0), (40, 40, 40), res, rotation="111", sigma=0.0)
+    c = sph[:, :3]
+    assert np.allclose(sph[:, 3], res / (2 * np.sqrt(2)))
+    z = np.unique(np.round(c[:, 2], 9))
+    gaps = np.diff(z)
+    assert np.allclose(gaps, res / np.sqrt(3), atol=1e-9)
+    # nearest neighbours in one layer sit a / sqrt 2 apart, six around an inner site
+    mid = c[np.isclose(c[:, 2], z[len(z) // 2])]
+    inner = mid[np.argmin(np.sum((mid[:, :2] - 20.0) ** 2, axis=1))]
+    d = np.sqrt(np.sum((mid[:, :2] - inner[:2]) ** 2, axis=1))
+    d = np.sort(d[d > 1e-9])
+    assert np.allclose(d[:6], res / np.sqrt(2), atol=1e-9) and d[6] > res / np.sqrt(2) + 1.0
+    # the identity lattice instead stacks (001) planes a / 2 apart
+    sph0 = inputs.fcc_opal_spheres((0, 0, 0), (40, 40, 40), res, sigma=0.0)
+    assert np.allclose(np.diff(np.unique(np.round(sph0[:, 2], 9))), res / 2)
