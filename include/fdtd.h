@@ -171,12 +171,14 @@ typedef struct fdtd_source_desc {
 int fdtd_add_source(fdtd_grid* g, const fdtd_source_desc* s, int32_t* id);
 
 /* Field probe at cell (i,j,k): after update n it records E^{n+1} (three
- * components) of that cell (paper, Sec. "Wide-band excitation": field in a
- * low-symmetry point).  At most 64 probes; before the first step only. */
+ * components) of that cell (paper, Sec. "Wide-band excitation": the field is
+ * sampled at a generic point inside the crystal).  At most 64 probes; before
+ * the first step only. */
 int fdtd_add_probe(fdtd_grid* g, int32_t i, int32_t j, int32_t k, int32_t* id);
 
-/* Poynting flux plane (paper, Sec. "Dynamical diffusion": transversely
- * integrated Poynting vector T(t) at the output face).  Plane `index` normal
+/* Poynting flux plane (paper, Sec. "Dynamical diffusion": the transmitted
+ * power T(t) is the Poynting vector summed across the exit side of the
+ * crystal).  Plane `index` normal
  * to `axis`; faces at ((u+1/2), (v+1/2)) for u in [u0,u1), v in [v0,v1) along
  * the cyclic transverse axes (axis+1)%3, (axis+2)%3.  During update n it
  * records T^n = sign dx^2 sum (E x H).n in watts, E at time n averaged onto the

@@ -9,9 +9,9 @@ finite-difference time-domain leapfrog for Maxwell's curl equations over a
 per-node permittivity map, an absorbing layer at the box faces, and -- for the
 lasing runs (Sec. "3+1D simulation of lasing") -- a four-level gain medium
 coupled cell by cell through a polarization oscillator per field component,
-with spontaneous-emission noise as a stochastic source.  Observables: field
-probes (Sec. "Wide-band excitation and gap filling") and the transversely
-integrated Poynting flux T(t) through a plane (Sec. "Dynamical diffusion and
+with spontaneous-emission noise entering as a random term.  Observables: field
+probes (Sec. "Wide-band excitation and gap filling") and the Poynting flux
+T(t) summed over the faces of a plane (Sec. "Dynamical diffusion and
 localization").
 
 Units (normalized, exact rescalings of SI):

@@ -3,8 +3,8 @@
 Test infrastructure only: imported by the tests, the smoke check and the
 benchmark's CPU-baseline leg, never by the product path.
 
-The paper solves Maxwell-Bloch equations for a four-level system with three
-degenerate levels coupled to the three field components (Sec. "Sample and
+The gain medium of the paper has four levels, three of them degenerate and
+each tied to one field component (Sec. "Sample and
 numerical approach"), pumped externally for the lasing runs (Sec. "3+1D
 simulation of lasing").  Its su(4) density-matrix form lives in a cited work
 that is not available here, so the model follows the rate-equation form of

@@ -4,7 +4,7 @@ Test infrastructure only: imported by the tests, the smoke check and the
 benchmark's CPU-baseline leg, never by the product path.
 
 The spontaneous-emission noise of the gain model (Sec. "Sample and numerical
-approach": noise included as a stochastic source term) needs one Gaussian
+approach", where it enters the field evolution as a random term) needs one Gaussian
 number per gain cell, per polarization component and per time step.  Those are
 too many to pass in as inputs, so both sides implement the same published
 generator: Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, "Parallel

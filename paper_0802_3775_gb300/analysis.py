@@ -5,8 +5,8 @@ T^n): the quantities the paper extracts from its runs.
   lasing": emission spectra): Hann-windowed power spectrum of the last half
   of the series, peak refined by a parabola through the log power of the
   three bins around the maximum.
-* `tail_time_constant` and `diffusion_constant`: the trailing edge of the
-  transmission T(t) fitted by exp(-t/tau0) and D = L^2 / (pi^2 tau0) (Sec.
+* `tail_time_constant` and `diffusion_constant`: the decaying tail of the
+  transmitted power T(t) fitted by exp(-t/tau0) and D = L^2 / (pi^2 tau0) (Sec.
   "Dynamical diffusion and localization", diffusion constant and decay
   times).
 * `decay_time_distribution`: the weights g(tau) >= 0 of a sum of

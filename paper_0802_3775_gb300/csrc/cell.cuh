@@ -4,7 +4,7 @@
 //
 // Paper: Yee leapfrog (Sec. "Sample and numerical approach"), absorbing layer
 // (same section; CPML reading), four-level gain with the polarization at the
-// Yee node and noise as a stochastic source (same section), soft pulsed
+// Yee node and spontaneous-emission noise as a random kick (same section), soft pulsed
 // sources (Secs. "Wide-band excitation", "Dynamical diffusion").
 #pragma once
 

@@ -22,8 +22,8 @@
 // k_rasterize sphere list -> material bytes (FP64, no contraction).
 //
 // Paper: Yee FDTD (Sec. "Sample and numerical approach"), four-level
-// Maxwell-Bloch gain solved at the Yee cell (same section), noise as a
-// stochastic source (same section), pulsed sources and flux T(t) (Secs.
+// Maxwell-Bloch gain solved at the Yee cell (same section), spontaneous-
+// emission noise as a random kick (same section), pulsed sources and flux T(t) (Secs.
 // "Wide-band excitation", "Dynamical diffusion").
 #include <math.h>
 

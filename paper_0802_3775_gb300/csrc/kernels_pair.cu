@@ -31,8 +31,8 @@
 // the results equal theirs bit for bit.
 //
 // Paper: Yee FDTD (Sec. "Sample and numerical approach"), four-level
-// Maxwell-Bloch gain solved at the Yee cell (same section), noise as a
-// stochastic source (same section).
+// Maxwell-Bloch gain solved at the Yee cell (same section), spontaneous-
+// emission noise as a random kick (same section).
 #include <math.h>
 
 #include "cell.cuh"

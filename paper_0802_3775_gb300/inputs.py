@@ -10,7 +10,7 @@ approach"): an fcc inverted opal of air spheres of radius r0 = a/(2*sqrt(2))
 (touching neighbours) in a high-index background, made disordered by random
 radii.  Two disorder laws are offered:
 
-* ``"paper"``    -- uniform deviates xi in [-1/2, 1/2], r = r0 (1 + gamma xi),
+* ``"paper"``    -- xi drawn uniformly from [-1/2, 1/2], r = r0 (1 + gamma xi),
                     radii only (the paper's law);
 * ``"gaussian"`` -- independent Gaussian deviates delta ~ N(0, sigma) for the
                     radius and for each centre coordinate: r = r0 (1 + delta_r)

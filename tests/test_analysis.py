@@ -40,7 +40,7 @@ def test_decay_time_distribution_recovers_two_components():
     dt = 1.0e-16
     taus = np.geomspace(1e-14, 1e-11, 61)
     w = np.zeros_like(taus)
-    w[15], w[45] = 1.0, 0.3            # a fast and a slow component on the grid
+    w[15], w[45] = 1.0, 0.3            # two components on the grid, one short-lived, one long-lived
     t = np.arange(6000) * dt
     T = np.exp(-t / taus[15]) * w[15] + np.exp(-t / taus[45]) * w[45]
     g = A.decay_time_distribution(T, dt, taus, window=(0, len(T)), alpha=1e-9)

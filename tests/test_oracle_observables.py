@@ -3,7 +3,7 @@
 * Poynting flux T^n of a discrete travelling eigenmode through a plane has the
   closed form  dx^2 N_faces E0^2 sqrt(eps_r) cos(k/2) cos(omega dt/2)
   cos^2(k p - omega n) / eta0  (the transmitted power T(t) of Sec. "Dynamical
-  diffusion and localization" is this flux through the output face);
+  diffusion and localization" is this flux through the crystal's exit side);
 * the source waveform has the stated centre frequency and power-spectrum FWHM
   (single-cycle / 100 fs pulses of Secs. "Wide-band excitation" and
   "Dynamical diffusion");
