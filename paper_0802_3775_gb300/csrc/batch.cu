@@ -6,9 +6,9 @@
 // member that reaches its limit stops being updated while the others go on.
 //
 // Paper: the realizations of the disorder studies (Sec. "Wide-band
-// excitation and gap filling": results averaged over 10 realizations per
-// disorder strength) are independent runs; here they share the GPU in one
-// launch per step.
+// excitation and gap filling": ten of them are averaged for each disorder
+// strength) are independent runs; here they share the GPU in one launch per
+// step.
 #include <cuda_runtime.h>
 
 #include <algorithm>
