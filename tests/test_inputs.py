@@ -112,3 +112,15 @@ def test_111_rotation_stacks_close_packed_layers_along_z():
     # the identity lattice instead stacks (001) planes a / 2 apart
     sph0 = inputs.fcc_opal_spheres((0, 0, 0), (40, 40, 40), res, sigma=0.0)
     assert np.allclose(np.diff(np.unique(np.round(sph0[:, 2], 9))), res / 2)
+
+
+def test_paper_disorder_moves_radii_only_uniformly():
+    res, gamma = 10.0, 0.2
+    ordered = inputs.fcc_opal_spheres((0, 0, 0), (60, 60, 60), res, sigma=0.0)
+    paper = inputs.fcc_opal_spheres((0, 0, 0), (60, 60, 60), res, disorder="paper", gamma=gamma, seed=3)
+    assert np.array_equal(paper[:, :3], ordered[:, :3])        # centres stay on the lattice
+    r0 = res / (2 * np.sqrt(2))
+    xi = paper[:, 3] / r0 - 1.0
+    assert np.all(np.abs(xi) <= gamma / 2)
+    # uniform on [-gamma/2, gamma/2]: mean 0, variance gamma^2 / 12
+    assert abs(np.mean(xi)) < 0.01 and abs(np.var(xi) / (gamma ** 2 / 12) - 1) < 0.1
