@@ -370,6 +370,10 @@ typedef struct fdtd_server_stats {
   int64_t used_bytes;
 } fdtd_server_stats;
 
+/* E_INVAL for a null argument or a budget, slot count or chunk that is not
+ * positive; E_CUDA without a CUDA device; E_NOMEM if the worker thread cannot
+ * start.  `stream` is unused (the worker owns its stream).  As everywhere in
+ * this header, failures come back as codes: no C++ exception leaves a call. */
 int fdtd_server_create(const fdtd_server_desc* desc, void* stream, fdtd_server** out);
 /* Fails queued requests, finishes resident runs, joins the worker. */
 int fdtd_server_destroy(fdtd_server* s);
