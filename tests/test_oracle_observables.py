@@ -16,6 +16,10 @@
   update uses D / kappa + psi;
 * rasterizer: brute force with scalar Python arithmetic on tiny grids equals the
   oracle bit for bit; touching fcc spheres fill pi/(3 sqrt 2) = 0.7405 of space;
+* sheet source: in a transversely periodic box a uniform sheet radiates the
+  field of a continuum current sheet, E = -eta K / 2 on each side, with a
+  mismatch second order in k dx (it scales as eps_r f0^2); with a waist the
+  sheet's profile is centred on the interior and isotropic on every axis;
 * Poynting theorem: the flux a dipole pulse sends through the six faces of a
   closed cube, summed over time, equals the energy that ends up outside it,
   with a mismatch that falls as the square of the frequency (the faces' E and
@@ -252,3 +256,70 @@ def test_poynting_theorem_over_a_closed_cube():
         assert abs(u_out - bad) / u_out > 0.2
     # second order: the mismatch scales as f0^2
     assert abs(m[0.5] / m[0.35] / (0.5 / 0.35) ** 2 - 1) < 0.03
+
+
+def _sheet_mismatch(eps_r, f0_hat, amplitude=2.0, steps=1400):
+    """Uniform x-polarized sheet at z = 200 of a 1 x 1 x 1200 box, periodic in
+    x and y (a 1D problem), probe 100 cells downstream.  The soft term
+    -(A/eps_r) g per step is a surface current K = eps0 A g c / S, whose
+    continuum field is E = -(eta0 / sqrt(eps_r)) K / 2 = -A g / (2 S sqrt(eps_r)),
+    delayed by the travel time.  Returns the relative mismatch of the
+    time-summed E^2, the best correlation with the delayed continuum pulse and
+    the delay of that best match beyond the continuum travel time."""
+    o = Oracle((1, 1, 1200), 12, courant=0.5, periodic=(True, True, False), eps=(eps_r,) * 3)
+    o.add_source(kind="sheet", comp=0, axis=2, index=200, f0_hat=f0_hat, rel_bw=0.5, amplitude=amplitude)
+    o.add_probe(0, 0, 300)
+    o.step(steps)
+    e = o.probe_series()[:, 0, 0]
+    ref = amplitude * waveform(np.arange(steps), f0_hat, 0.5, o.S, 12) / (2 * o.S * math.sqrt(eps_r))
+    # best match over delays from the continuum travel time to a few steps
+    # more (the grid's group velocity is a little lower)
+    lag0 = 100 * math.sqrt(eps_r) / o.S
+    corr = {lag: np.dot(e[lag:], ref[:-lag]) / math.sqrt(np.dot(e, e) * np.dot(ref, ref))
+            for lag in range(int(lag0) - 1, int(lag0) + 8)}
+    best = min(corr, key=corr.get)
+    return float(np.sum(e * e) / np.sum(ref * ref) - 1.0), float(corr[best]), best - lag0
+
+
+def test_sheet_source_radiates_the_current_sheet_field():
+    m = {}
+    for eps_r in (1.0, 2.5):
+        for f0 in (0.25, 0.5):
+            m[eps_r, f0], corr, delay = _sheet_mismatch(eps_r, f0)
+            assert 0 < m[eps_r, f0] < 0.06
+            assert corr < -0.99          # E = -eta K / 2: opposite to the current
+            assert -1.0 < delay < 6.0
+    for eps_r in (1.0, 2.5):
+        assert abs(m[eps_r, 0.5] / m[eps_r, 0.25] / 4.0 - 1) < 0.1
+    for f0 in (0.25, 0.5):
+        assert abs(m[2.5, f0] / m[1.0, f0] / 2.5 - 1) < 0.1
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_sheet_waist_profile_is_centred_and_isotropic(axis):
+    shape = (20, 26, 32)
+    npml = (2, 4, 3, 5, 6, 2)
+    o = Oracle(shape, 10, npml=npml)
+    o.add_source(kind="sheet", comp=(axis + 1) % 3, axis=axis, index=9, waist=3.0)
+    w = o.sources[-1]["w"]
+    plane = np.take(w, 9, axis=axis)
+    assert np.count_nonzero(w) == np.count_nonzero(plane)      # only the sheet plane is driven
+    d1, d2 = (axis + 1) % 3, (axis + 2) % 3
+    # the plane's array axes are the remaining axes in increasing order
+    a1, a2 = sorted((d1, d2))
+    lo = {d: npml[2 * d] for d in range(3)}
+    hi = {d: shape[d] - npml[2 * d + 1] for d in range(3)}
+    # zero outside the non-absorbing interior of the plane
+    inside = np.zeros_like(plane, dtype=bool)
+    inside[lo[a1]:hi[a1], lo[a2]:hi[a2]] = True
+    assert np.all(plane[~inside] == 0) and np.all(plane[inside] > 0)
+    # centred: the profile is mirror-symmetric about the interior centre on both axes
+    sub = plane[lo[a1]:hi[a1], lo[a2]:hi[a2]]
+    np.testing.assert_allclose(sub, sub[::-1, :], rtol=1e-13)
+    np.testing.assert_allclose(sub, sub[:, ::-1], rtol=1e-13)
+    # isotropic: one cell off the centre row weighs the same along either axis
+    c1, c2 = 0.5 * (lo[a1] + hi[a1] - 1), 0.5 * (lo[a2] + hi[a2] - 1)
+    i1, i2 = int(math.floor(c1)), int(math.floor(c2))
+    f = lambda x1, x2: math.exp(-((x1 - c1) ** 2 + (x2 - c2) ** 2) / 9.0)
+    assert math.isclose(plane[i1, i2] / plane[i1 + 1, i2], f(i1, i2) / f(i1 + 1, i2), rel_tol=1e-12)
+    assert math.isclose(plane[i1, i2] / plane[i1, i2 + 1], f(i1, i2) / f(i1, i2 + 1), rel_tol=1e-12)
