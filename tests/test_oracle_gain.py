@@ -11,7 +11,12 @@ checked against:
 * a one-cell periodic box (no curl): the coupled E / P / N system against an
   independent high-accuracy ODE integration of the continuum equations, with
   second-order convergence, and exact conservation of D = eps_r E + P~;
-* Philox4x32-10 published known-answer vectors and Gaussian statistics.
+* Philox4x32-10 published known-answer vectors and Gaussian statistics;
+* a slab of inverted (or absorbing) medium in a 1D waveguide amplifies (or
+  attenuates) a pulse by the plane-wave factor of a Lorentz medium,
+  exp(-2 Im k L) with k = (w/c) sqrt(eps_r + chi(w)) and
+  chi = (kappa/eps0)(N1 - N2)/(w_a^2 - w^2 - i w dw), averaged over the
+  pulse spectrum, the exponent converging at second order in dx.
 """
 import math
 import os
@@ -271,3 +276,57 @@ def test_polarization_recurrence_against_the_damped_oscillator(steps_per_period)
     for _ in range(200 * steps_per_period):
         p, p_prev = a1 * p - a2 * p_prev + a3 * dn * E, p
     assert abs(p / P_star - 1) < 1e-9
+
+
+def _slab_transmission(inversion, res, kappa=4.2e-7, f0=0.4, dw_rel=0.2, rel_bw=0.1):
+    """x-polarized pulse from a uniform sheet through a 100-cell slab (at
+    res = 12; lengths scale with res) of gain cells in a 1 x 1 x n box that
+    is periodic across and absorbing at both z ends.  inversion: fraction of
+    the atoms moved from level 0 to level 2 (> 0) or to level 1 (< 0), with
+    relaxation and pump off.  Returns (sum of E^2 at a probe behind the slab,
+    the oracle, the probe series)."""
+    sc = res // 12
+    n = 260 * sc
+    o = Oracle((1, 1, n), res, courant=0.5, periodic=(True, True, False), npml=(0, 0, 0, 0, 20 * sc, 20 * sc))
+    mat = np.full((n, 1, 1), 0b010101, dtype=np.uint8)
+    mat[60 * sc:160 * sc] |= 64
+    o.set_material(mat)
+    o.set_gain(n_total=1e24, fa_hat=f0, dw_rel=dw_rel, tau32=1e6, tau21=1e6, tau10=1e6, pump=0.0,
+               kappa=kappa, noise_amp=0.0, init="ground")
+    m = o.gain["mask"]
+    o.dN[0][m] -= abs(inversion) * 1e24
+    o.dN[2 if inversion > 0 else 1][m] += abs(inversion) * 1e24
+    o.add_source(kind="sheet", comp=0, axis=2, index=30 * sc, f0_hat=f0, rel_bw=rel_bw, amplitude=1.0)
+    o.add_probe(0, 0, 200 * sc)
+    o.step(4000 * sc)             # the whole pulse passes the probe
+    e = o.probe_series()[:, 0, 0]
+    return float(np.sum(e * e)), o, e
+
+
+def _lorentz_factor(o, inversion, kappa, weights, length):
+    """Spectrum-averaged plane-wave power factor of the continuum Lorentz medium."""
+    m = 8 * len(weights)
+    spec = np.abs(np.fft.rfft(weights, m)) ** 2
+    w = 2 * np.pi * np.fft.rfftfreq(m, d=o.dt)
+    wa, dwa = o.gain["omega_a"], o.gain["domega"]
+    chi = (kappa / EPS0) * (-inversion * 1e24) / (wa ** 2 - w ** 2 - 1j * w * dwa)
+    k = (w / C0) * np.sqrt(1.0 + chi + 0j)
+    return float(np.sum(spec * np.exp(-2.0 * np.imag(k) * length)) / np.sum(spec))
+
+
+def test_slab_gain_and_loss_match_the_lorentz_medium():
+    kappa = 4.2e-7
+    err = {}
+    for res in (12, 24):
+        ref, _, e0 = _slab_transmission(0.0, res, kappa)
+        for inv in (0.5, -0.5):
+            u, o, _ = _slab_transmission(inv, res, kappa)
+            expect = _lorentz_factor(o, inv, kappa, e0, 100 * (res // 12) * o.dx)
+            assert (expect > 2.0) if inv > 0 else (expect < 0.5)    # a strong effect
+            err[res, inv] = math.log(u / ref) / math.log(expect) - 1.0
+            # linear regime: the populations have not moved
+            N = o.populations()[:, o.gain["mask"]]
+            assert np.max(np.abs(N[2] - (0.5e24 if inv > 0 else 0.0))) < 1e-9 * 1e24
+    for inv in (0.5, -0.5):
+        assert abs(err[12, inv]) < 0.012
+        assert abs(err[24, inv]) < 0.4 * abs(err[12, inv])        # second order in dx
