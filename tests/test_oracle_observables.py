@@ -323,3 +323,18 @@ def test_sheet_waist_profile_is_centred_and_isotropic(axis):
     f = lambda x1, x2: math.exp(-((x1 - c1) ** 2 + (x2 - c2) ** 2) / 9.0)
     assert math.isclose(plane[i1, i2] / plane[i1 + 1, i2], f(i1, i2) / f(i1 + 1, i2), rel_tol=1e-12)
     assert math.isclose(plane[i1, i2] / plane[i1, i2 + 1], f(i1, i2) / f(i1, i2 + 1), rel_tol=1e-12)
+
+
+def test_rasterizer_degenerate_inputs():
+    shape = (5, 4, 3)
+    # no spheres: background inside the box, class 0 outside, no gain
+    lo, hi = (1, 0, 1), (4, 4, 3)
+    got = rasterize(shape, np.zeros((0, 4)), lo, hi)
+    assert np.array_equal(got, _brute_force_material(shape, [], lo, hi))
+    assert not np.any(got & 64)
+    # an empty box: every node outside, whatever the spheres
+    got = rasterize(shape, np.array([[2.0, 2.0, 1.0, 3.0]]), (2, 2, 2), (2, 2, 2))
+    assert not np.any(got)
+    # a zero-radius sphere on a sample point covers nothing (strict test)
+    got = rasterize(shape, np.array([[1.5, 1.0, 1.0, 0.0]]), (0, 0, 0), shape)
+    assert np.array_equal(got, np.full(shape[::-1], 0b010101, dtype=np.uint8))
