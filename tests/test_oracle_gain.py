@@ -330,3 +330,23 @@ def test_slab_gain_and_loss_match_the_lorentz_medium():
     for inv in (0.5, -0.5):
         assert abs(err[12, inv]) < 0.012
         assert abs(err[24, inv]) < 0.4 * abs(err[12, inv])        # second order in dx
+
+
+def test_gain_model_without_gain_cells_leaves_the_passive_run_unchanged():
+    """Degenerate case: a gain medium switched on in a grid whose cells are
+    all outside the spheres changes nothing, noise included, bit for bit."""
+    shape = (8, 7, 6)
+    mat = inputs.random_material(shape, seed=41, classes=(1, 2))     # gain bit clear everywhere
+    runs = []
+    for with_gain in (False, True):
+        o = Oracle(shape, 10, npml=(2, 2, 0, 0, 1, 3), eps=(1.0, 2.5, 11.9), seed=7)
+        o.set_material(mat)
+        if with_gain:
+            o.set_gain(n_total=1e24, fa_hat=0.8, dw_rel=0.02, tau32=100e-15, tau21=1e-9, tau10=100e-15,
+                       pump=1e12, noise_amp=1e3)
+        o.add_source(kind="point", comp=1, pos=(4, 3, 3), f0_hat=0.8, rel_bw=0.5)
+        o.step(120)
+        runs.append(o)
+    assert np.any(runs[0].E != 0)
+    assert np.array_equal(runs[0].E, runs[1].E) and np.array_equal(runs[0].H, runs[1].H)
+    assert not np.any(runs[1].P) and not np.any(runs[1].dN)
