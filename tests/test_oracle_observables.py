@@ -10,7 +10,8 @@
 * a soft source in a one-cell periodic box drives E = -(A/eps_r) sum_n g(n);
 * CPML reflection (the paper's absorbing layer, Sec. "Sample and numerical
   approach"): a probe near the layer agrees with a run in a much larger box
-  to better than -40 dB until the outer box's echo returns;
+  to better than -40 dB until the outer box's echo returns, for a plain
+  (kappa_max 1) and a stretched (kappa_max 3) layer;
 * CPML memory: at slab nodes of each kind the memory series equals the
   recursive convolution of the raw differences (scipy's lfilter), and the
   update uses D / kappa + psi;
@@ -101,12 +102,14 @@ def test_soft_source_in_one_cell_box():
 
 
 @pytest.mark.slow
-def test_cpml_reflection_below_minus_40db():
+@pytest.mark.parametrize("kappa_max", [1.0, 3.0])
+def test_cpml_reflection_below_minus_40db(kappa_max):
     res, npml, interior, pad = 10, 8, 20, 16
 
     def run(n_extra):
         n = interior + 2 * npml + 2 * n_extra
-        o = Oracle((n, n, n), res, npml=(npml,) * 6, eps=(1.0, 1.0, 1.0), cpml_f_hat=0.6)
+        o = Oracle((n, n, n), res, npml=(npml,) * 6, eps=(1.0, 1.0, 1.0), cpml_f_hat=0.6,
+                   cpml_kappa_max=kappa_max)
         c = n // 2
         o.add_source(kind="point", comp=2, pos=(c, c, c), f0_hat=0.6, rel_bw=1.0)
         # probe two cells inside the small box's absorbing layer boundary
