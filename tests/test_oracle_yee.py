@@ -210,3 +210,73 @@ def test_discrete_gauss_laws_with_gain_and_noise():
     # leaving out the polarization, or the permittivity, breaks the law
     assert np.max(np.abs(_div_nodes(o.eps_E * o.E, periodic) - D0)[inner]) > 1e-3 * np.max(np.abs(D0))
     assert np.max(np.abs(_div_nodes(o.E + o.P, periodic) - D0)[inner]) > 1e-3 * np.max(np.abs(D0))
+
+
+# SI constants for the energy pins (CODATA 2018 mu0, exact c), written here so
+# that the expected energies do not reuse the oracle's normalization
+_MU0 = 1.25663706212e-6
+_C = 299792458.0
+_EPS0 = 1.0 / (_MU0 * _C * _C)
+
+
+@pytest.mark.parametrize("eps_r,m,res", [(1.0, (1, 2, -1), 12), (11.9, (2, 0, 3), 20), (2.25, (0, -1, 1), 16)])
+def test_energy_of_a_travelling_plane_wave(eps_r, m, res):
+    """Oracle.energy() of a discrete travelling plane wave in a periodic box
+    equals the continuum energy of a plane wave, (1/2) eps0 eps_r E0^2 V,
+    at every step: its electric and magnetic parts are each half of it (the
+    discrete H~ amplitude is sqrt(eps_r) E0 by the dispersion relation), and
+    cos^2 summed over whole periods of the box is half the node count.  A
+    dx^2 in place of dx^3, eps_r left out of the electric part or a missing
+    1/2 each fail by a factor."""
+    shape = (12, 10, 14)
+    a = 480e-9
+    o = Oracle(shape, res, a=a, courant=0.5, periodic=(True, True, True), eps=(eps_r, eps_r, eps_r))
+    S = o.S
+    k = np.array([2 * math.pi * m[d] / shape[d] for d in range(3)])
+    K = 2.0 * np.sin(k / 2.0)
+    E_hat = np.cross(K, [0.3, -0.7, 1.1])
+    E0 = 37.0  # V/m
+    E_hat *= E0 / np.linalg.norm(E_hat)
+    Om = S * np.linalg.norm(K) / math.sqrt(eps_r)
+    w = 2.0 * math.asin(Om / 2.0)
+    H_hat = (S / Om) * np.cross(K, E_hat)
+    for c in range(3):
+        X, Y, Z = _coords(shape, NODE[c])
+        o.E[c] = E_hat[c] * np.cos(k[0] * X + k[1] * Y + k[2] * Z)
+        X, Y, Z = _coords(shape, NODE[c + 3])
+        o.H[c] = H_hat[c] * np.cos(k[0] * X + k[1] * Y + k[2] * Z + 0.5 * w)
+    dx = a / res
+    V = shape[0] * shape[1] * shape[2] * dx ** 3
+    U = 0.5 * _EPS0 * eps_r * E0 ** 2 * V
+    assert abs(o.energy() / U - 1.0) < 1e-12
+    for _ in range(3):
+        o.step(37)
+        assert abs(o.energy() / U - 1.0) < 1e-12
+
+
+def test_energy_of_uniform_static_fields_in_a_layered_box():
+    """A uniform E0 and H0 in a periodic box are static (every Yee difference
+    of a uniform field is zero), so Oracle.energy() must equal the field energy
+    of electrostatics and magnetostatics: (1/2) eps0 E0^2 (eps_1 V_1 + eps_2 V_2)
+    + (1/2) mu0 H0^2 V for two layers of permittivity eps_1, eps_2 filling
+    half the box each, with H0 = H~0 / eta0 the SI magnetic field."""
+    shape = (6, 8, 10)
+    res, a = 16, 480e-9
+    eps1, eps2 = 1.0, 11.9
+    o = Oracle(shape, res, a=a, periodic=(True, True, True), eps=(eps1, eps2, eps2))
+    mat = np.zeros(shape[::-1], dtype=np.uint8)  # class 0 (eps1) for z < nz/2
+    mat[shape[2] // 2:] = 0b010101                # class 1 (eps2) above
+    o.set_material(mat)
+    E0 = np.array([3.0, -4.0, 12.0])      # V/m
+    Ht0 = np.array([-2.0, 5.0, 1.5])      # H~ = eta0 H, V/m
+    for c in range(3):
+        o.E[c] = E0[c]
+        o.H[c] = Ht0[c]
+    dx = a / res
+    V = shape[0] * shape[1] * shape[2] * dx ** 3
+    eta0 = _MU0 * _C
+    H0 = Ht0 / eta0
+    U = 0.5 * _EPS0 * (E0 @ E0) * (eps1 * V / 2 + eps2 * V / 2) + 0.5 * _MU0 * (H0 @ H0) * V
+    assert abs(o.energy() / U - 1.0) < 1e-13
+    o.step(5)
+    assert abs(o.energy() / U - 1.0) < 1e-13
