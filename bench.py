@@ -12,8 +12,20 @@ Under torchrun each rank steps its own realizations (different disorder
 seeds) with no collective on the data path (weak scaling); the timed region is
 bracketed by barriers and the max over ranks is reported.
 
+Besides the headline workload, the default single-GPU run (rank 0) adds:
+  * ``batch``: the 64-realization mixed batch (half lasing) stepped together,
+    with its roofline fraction and its realizations/hour against the plain
+    single-run FP64 GPU path;
+  * ``serve``: a Poisson request stream of the served workload's sizes;
+  * ``cpu_baseline``: the FP64 oracle timed on the host cores, one process
+    per allowed core (independent realizations) and single-threaded;
+  * ``oracle_error``: the GPU path's relative L2 errors against the oracle on
+    reduced copies of the workload (and of batch members), computed by the
+    same CPU leg.
+
 --impl reference times the FP64 CPU oracle (the reference of this build) on a
-bounded sample of the same workload, on the host cores, rank 0 only.
+bounded sample of the same workload, on the host cores (one process per
+allowed core, each stepping its own realization), rank 0 only.
 """
 from __future__ import annotations
 
@@ -21,6 +33,7 @@ import argparse
 import dataclasses
 import json
 import math
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -64,6 +77,26 @@ def workload_specs(name: str, rank: int, steps: int):
     if name == "planewave64":
         return [inputs.opal_planewave_f32(ncell=8, res=20, npml=12, sigma=0.06, realization=rank, steps=steps,
                                           precision="f64")]
+    raise SystemExit(f"unknown workload {name}")
+
+
+def reduced_specs(name: str, steps: int):
+    """Reduced copies of a workload's recipe for the error checks against the
+    oracle: 2x2x2 unit cells, the same resolution, absorber, disorder, seeds,
+    sources and observers; for the batch its first four members (two passive,
+    two lasing) reduced the same way."""
+    if name == "planewave":
+        return [inputs.opal_planewave_f32(ncell=2, res=20, npml=12, sigma=0.06, realization=0, steps=steps)]
+    if name == "planewave64":
+        return [inputs.opal_planewave_f32(ncell=2, res=20, npml=12, sigma=0.06, realization=0, steps=steps,
+                                          precision="f64")]
+    if name == "lasing":
+        return [inputs.opal_lasing_f32(ncell=2, res=20, npml=10, sigma=0.05, pump=1e10, realization=0,
+                                       steps=steps)]
+    if name == "dipole64":
+        return [inputs.opal_dipole_f64(steps=steps)]
+    if name == "batch":
+        return inputs.mixed_batch(4, seed=4000, steps=steps, ncell=2)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -182,78 +215,72 @@ def configure_batch(args, b):
         b.set_launch(args.kernel, args.by, args.zdepth, 0)
 
 
-def run_gpu(args, rank, world, dist):
+KERNEL_NAMES = {1: "k_step", 2: "k_step_tma", 3: "k_step_pair"}
+
+
+def timed_workload(args, specs, world, dist, steps, warmup, sample_clocks=True):
+    """Create the grids of `specs` (a batch when there are several), tune the
+    launch shape, warm up, and time `steps` steps with CUDA events on the
+    stream the kernels run on.  Returns (record, grids, stepper)."""
     import torch
 
-    from paper_0802_3775_gb300 import build
-    from paper_0802_3775_gb300.fdtd import Grid
+    from paper_0802_3775_gb300.fdtd import Batch, Grid
 
-    build.build()
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
-    specs = workload_specs(args.workload, rank, args.steps + args.warmup)
-    cap = args.steps + args.warmup + 16
+    cap = steps + warmup + 16
     grids = [Grid.from_spec(s, record_capacity=cap) for s in specs]
     for g in grids:
         configure_grid(args, g)
-    gain_cells = []
-    for g, s in zip(grids, specs):
-        gain_cells.append(int(np.count_nonzero(g.get_material() & 64)) if s.gain is not None else 0)
-    batch = None
+    gain_cells = [int(np.count_nonzero(g.get_material() & 64)) if s.gain is not None else 0
+                  for g, s in zip(grids, specs)]
     if len(grids) > 1:
-        from paper_0802_3775_gb300.fdtd import Batch
-        batch = Batch(grids)
-        configure_batch(args, batch)
-        stepper = batch
+        stepper = Batch(grids)
+        configure_batch(args, stepper)
     else:
         stepper = grids[0]
     tune = None
     if not args.no_autotune and args.kernel == "auto" and not args.by and not args.zdepth:
         # launch shape picked by timing the candidates on this workload (state restored)
-        tune = stepper.autotune(trial_steps=10 if batch is None else 4)
-    stepper.step(args.warmup)
+        tune = stepper.autotune(trial_steps=10 if len(grids) == 1 else 4)
+    stepper.step(warmup)
     stepper.sync()
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    # timed region: device events on the stream the kernels run on (torch's current stream)
     stream = torch.cuda.current_stream()
     # CUDA events around every 8th step-kernel launch of the timed region
     # (bracketing every launch costs a few per cent of the step rate)
     stepper.set_timing(True, every=8)
     clocks = ClockSampler()
-    clocks.start()
-    time.sleep(0.3)
+    if sample_clocks:
+        clocks.start()
+        time.sleep(0.3)
     barrier()
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    stepper.step(args.steps)
+    # step() ends by joining the observation stream (where one is used) into
+    # the grid's stream before its counter update, so ev1 follows every launch
+    stepper.step(steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ck = clocks.stop()
+    ck = clocks.stop() if sample_clocks else None
     ms = ev0.elapsed_time(ev1)
-    kernel = [stepper.kernel_time()]
-    # step kernels in use (a batch launches one per kernel group each step)
-    names = {1: "k_step", 2: "k_step_tma", 3: "k_step_pair"}
+    kms, klaunch = stepper.kernel_time()
     in_use = sorted({g.kernel_in_use() for g in grids}, key=lambda kr: -kr[0])
-    kind, rows = in_use[0]
-    kname = " + ".join(names[k] for k, _ in in_use)
+    kname = " + ".join(KERNEL_NAMES[k] for k, _ in in_use)
     tiles = [[32 if k > 1 else None, r] for k, r in in_use]
     stepper.set_timing(False)
     stepper.sync()
     ms_max = rank_max(ms, dist)
     cells = sum(s.cells for s in specs)
-    value = cells * args.steps * world / (ms_max * 1e-3) / 1e6
+    value = cells * steps * world / (ms_max * 1e-3) / 1e6
 
-    # roofline of the step kernel (dominant): algorithmic bytes per launch / mean launch time
+    # roofline of the step kernel(s): algorithmic bytes per launch / mean launch time
     peak, peak_kind = measured_peaks()
-    kms = sum(k[0] for k in kernel)
-    klaunch = sum(k[1] for k in kernel)
     bytes_step = sum(algorithmic_bytes(s, gc) for s, gc in zip(specs, gain_cells))
     # Two upper bounds of the step launches' mean duration: the launches
     # bracketed by CUDA events (every 8th step; the events cut the
@@ -262,69 +289,115 @@ def run_gpu(args, rank, world, dist):
     # the observation adds).  With the observation on a second stream the step
     # launches run back to back and the second bound is the tighter one.
     ev_ms = kms / max(klaunch, 1)
-    region_ms = ms_max / args.steps
+    region_ms = ms_max / steps
     per_launch_ms = min(ev_ms, region_ms)
     launch_time_from = "per-launch CUDA events" if ev_ms <= region_ms else "timed region / steps"
     achieved = bytes_step / (per_launch_ms * 1e-3) / 1e9
-    traffic = None
+    rec = {"value": round(value, 1), "ms_per_step": round(ms_max / steps, 5), "cells": cells,
+           "launch_shape": ({"kernel": tune["kernel"], "by": tune["by"], "zdepth": tune["zdepth"],
+                             "grid_blocks": tune["grid_blocks"], "autotuned_over": tune["candidates"]}
+                            if tune else "library default"),
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(achieved / peak, 4), "traffic": None,
+                        "kernel": kname, "tile": tiles[0] if len(tiles) == 1 else tiles,
+                        "algorithmic_bytes_per_launch": bytes_step,
+                        "mean_launch_ms": round(per_launch_ms, 5), "launch_time_from": launch_time_from,
+                        "event_timed_launch_ms": round(ev_ms, 5), "peak_source": f"{peak_kind} hbm_gbs"},
+           "launches": steps * (len(in_use) + 1) + 1,  # step kernel(s) and observation per step, one counter update
+           "clocks": ck, "tune": tune, "n_kernels": len(in_use), "kname": kname, "tiles": tiles}
+    return rec, grids, stepper
+
+
+def run_gpu(args, rank, world, dist):
+    import torch
+
+    from paper_0802_3775_gb300 import build
+
+    build.build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    specs = workload_specs(args.workload, rank, args.steps + args.warmup)
+    rec, grids, stepper = timed_workload(args, specs, world, dist, args.steps, args.warmup)
+    roof = rec["roofline"]
     prof = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
     if os.path.exists(prof):
         with open(prof) as f:
-            rec = json.load(f)
+            tr = json.load(f)
         # DRAM bytes of one launch from an ncu capture of this workload, when
-        # it was taken on the kernel this run uses
-        zd = tune["zdepth"] if tune else args.zdepth
-        if len(in_use) == 1 and rec.get("kernel") == kname and rec.get("tile") == tiles[0] and rec.get("zdepth") == zd:
-            traffic = rec.get("dram_bytes_per_launch")
+        # it was taken on the kernel and launch shape this run uses
+        zd = rec["tune"]["zdepth"] if rec["tune"] else args.zdepth
+        if rec["n_kernels"] == 1 and tr.get("kernel") == rec["kname"] and tr.get("tile") == rec["tiles"][0] \
+                and tr.get("zdepth") == zd:
+            roof["traffic"] = tr.get("dram_bytes_per_launch")
 
-    # end to end through the public API with host inputs and host results
-    e2e = run_e2e(args, specs, rank, dist)
-
-    launches = args.steps * (len(in_use) + 1) + 1  # step kernel(s) and observation per step, one counter update
+    batch_grids = []
     result = {
-        "metric": METRIC, "value": round(value, 1), "unit": "Mcell-updates/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5),
+        "metric": METRIC, "value": rec["value"], "unit": "Mcell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if specs[0].precision == "f32" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload], "grids_per_gpu": len(specs),
-                   "cells_per_gpu": cells, "l2": "state larger than L2 (%.0f MB per GPU)" %
-                   (sum(s.cells for s in specs) * (49 if specs[0].precision == "f32" else 97) / 1e6),
+                   "cells_per_gpu": rec["cells"], "l2": "state larger than L2 (%.0f MB per GPU)" %
+                   (rec["cells"] * (49 if specs[0].precision == "f32" else 97) / 1e6),
                    "parallelism": f"replicas x{world} (independent realizations)",
                    "launch": "direct launches; CUDA events around the step-kernel launch(es) of every 8th time step of the timed region",
-                   "launch_shape": ({"kernel": tune["kernel"], "by": tune["by"], "zdepth": tune["zdepth"],
-                                     "grid_blocks": tune["grid_blocks"], "autotuned_over": tune["candidates"]}
-                                    if tune else "library default")},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": kname, "tile": tiles[0] if len(tiles) == 1 else tiles,
-                     "algorithmic_bytes_per_launch": bytes_step,
-                     "mean_launch_ms": round(per_launch_ms, 5), "launch_time_from": launch_time_from,
-                     "event_timed_launch_ms": round(ev_ms, 5), "peak_source": f"{peak_kind} hbm_gbs"},
-        "e2e": e2e,
-        "gpu_launches": launches,
-        "clocks": ck,
+                   "launch_shape": rec["launch_shape"]},
+        "roofline": roof,
+        "gpu_launches": rec["launches"],
+        "clocks": rec["clocks"],
     }
-    if rank == 0:
-        if world == 1 and not args.no_serve:
-            result["serve"] = serve_stream(capacity_mcell=0.6 * value)
-        if len(specs) > 1 and specs[0].precision == "f32":
-            # FP32 batched vs plain single-run FP64 GPU path, realizations/hour
-            steps_run = 20000  # steps per realization of the batched workload
-            rph32 = len(specs) / (ms_max / args.steps * 1e-3 * steps_run) * 3600.0
-            rph64, nsamp = fp64_plain_rate(specs, steps_run)
-            result["vs_fp64_plain"] = {
-                "fp32_batched_realizations_per_hour": round(rph32, 2),
-                "fp64_plain_realizations_per_hour": round(rph64, 2), "factor": round(rph32 / rph64, 2),
-                "steps_per_realization": steps_run,
-                "note": f"FP64 path: each realization stepped alone (automatic kernel), mean of the first {nsamp}; "
-                        "accuracy of both against the FP64 oracle is asserted by the parity tests"}
-            result["fp32_vs_fp64"] = fp32_vs_fp64_errors(specs, grids)
-        result["cpu_baseline"] = cpu_baseline(args)
-        print(json.dumps(result))
-    if batch is not None:
-        batch.close()
+    if rank == 0 and len(specs) > 1 and specs[0].precision == "f32":
+        result.update(batch_extras(specs, grids, rec, args.steps))
+    for g in grids:
+        g.sync()
+    if len(grids) > 1:
+        stepper.close()
     for g in grids:
         g.close()
+
+    # end to end through the public API with host inputs and host results
+    result["e2e"] = run_e2e(args, specs, rank, dist)
+
+    if rank == 0 and world == 1:
+        if not args.no_serve:
+            result["serve"] = serve_stream(count=args.serve_requests)
+        if args.workload == "planewave" and not args.no_batch:
+            result["batch"] = batch_record(args)
+            result["gpu_launches"] += result["batch"]["gpu_launches"]
+        result["cpu_baseline"], result["oracle_error"] = cpu_leg(args)
+    if rank == 0:
+        print(json.dumps(result))
+
+
+def batch_extras(specs, grids, rec, steps):
+    """FP32 batched against the plain single-run FP64 GPU path: realizations
+    per hour, and each of the first members against its FP64 GPU twin."""
+    steps_run = 20000  # steps per realization of the batched workload
+    rph32 = len(specs) / (rec["ms_per_step"] * 1e-3 * steps_run) * 3600.0
+    rph64, nsamp = fp64_plain_rate(specs, steps_run)
+    return {"vs_fp64_plain": {
+        "fp32_batched_realizations_per_hour": round(rph32, 2),
+        "fp64_plain_realizations_per_hour": round(rph64, 2), "factor": round(rph32 / rph64, 2),
+        "steps_per_realization": steps_run,
+        "note": f"FP64 path: each realization stepped alone (automatic kernel), mean of the first {nsamp}; "
+                "both paths' errors against the FP64 oracle are in oracle_error"},
+        "fp32_vs_fp64": fp32_vs_fp64_errors(specs, grids)}
+
+
+def batch_record(args):
+    """The 64-realization mixed batch (the batched workload) on this GPU,
+    timed like the headline workload, with its FP64-plain comparison."""
+    specs = workload_specs("batch", 0, args.steps + args.warmup)
+    rec, grids, stepper = timed_workload(args, specs, 1, None, args.steps, args.warmup)
+    out = {"workload": WORKLOAD_TEXT["batch"], "value": rec["value"], "unit": "Mcell-updates/s",
+           "ms_per_step": rec["ms_per_step"], "realizations": len(specs), "cells": rec["cells"],
+           "launch_shape": rec["launch_shape"], "roofline": rec["roofline"], "clocks": rec["clocks"],
+           "gpu_launches": rec["launches"]}
+    out.update(batch_extras(specs, grids, rec, args.steps))
+    stepper.close()
+    for g in grids:
+        g.close()
+    return out
 
 
 def run_e2e(args, specs, rank, dist):
@@ -371,43 +444,49 @@ def run_e2e(args, specs, rank, dist):
 
 
 # ----------------------------------------------------------------------------- serving
-def serve_stream(capacity_mcell: float, count: int = 48, load: float = 0.7, seed: int = 5000):
-    """Served request stream (the served-workload generator scaled to run in
-    about 15 s): Poisson arrivals of passive and lasing runs with grid edge
-    64..160 (CPML included) and 2000..8000 steps, the arrival rate set so the
-    offered load is `load` of `capacity_mcell`; every run is submitted at its
-    arrival time to one server (150 GB budget, continuous batching).
-    Latency = completion - submission, on the server's clock."""
+def serve_stream(count: int = 32, rate_hz: float = 4.0, seed: int = 5000, capacity_mcell: float = None):
+    """Served request stream with the served workload's sizes: Poisson
+    arrivals at `rate_hz` of passive and lasing runs (grid edge 64..200 with
+    the CPML, 5000..50000 steps), each submitted at its arrival time to one
+    server (150 GB HBM budget, 64 slots, continuous batching at 500-step chunk
+    boundaries).  Latency = completion - submission on the server's clock.
+    The offered load rho = arrival rate x mean service time, the service
+    time of a run being its cell-updates at the stream's measured throughput;
+    rho > 1 means the queue grows over the stream, so latencies grow with its
+    length."""
     from paper_0802_3775_gb300.serve import Server
 
-    stream = inputs.request_stream(count, rate_hz=1.0, seed=seed, n_range=(64, 160), steps_range=(2000, 8000))
+    stream = inputs.request_stream(count, rate_hz=rate_hz, seed=seed, n_range=(64, 200), steps_range=(5000, 50000))
     work = [s.cells * s.steps for _, s in stream]
-    rate = load * capacity_mcell * 1e6 / (sum(work) / len(work))
     srv = Server(hbm_budget_bytes=150 << 30, max_slots=64, steps_per_chunk=500)
     t0 = time.perf_counter()
     tickets = []
     for t_arr, spec in stream:
-        t_sub = t_arr / rate
         now = time.perf_counter() - t0
-        if t_sub > now:
-            time.sleep(t_sub - now)
+        if t_arr > now:
+            time.sleep(t_arr - now)
         tickets.append(srv.submit(spec, steps=spec.steps))
-    lat = []
+    lat, wait = [], []
     for t in tickets:
-        r = srv.wait(t)
+        r = srv.wait(t, timeout_s=1800.0)
         lat.append(r.done_s - r.submit_s)
+        wait.append(r.admit_s - r.submit_s)
         srv.release(t)
     wall = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
+    thr = sum(work) / wall / 1e6
+    mean_service = (sum(work) / len(work)) / (thr * 1e6)
     lat.sort()
-    pick = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]
-    return {"requests": count, "offered_load": load, "arrival_rate_hz": round(rate, 3),
-            "p50_s": round(pick(0.50), 3), "p99_s": round(pick(0.99), 3), "max_s": round(lat[-1], 3),
+    return {"requests": count, "arrival_rate_hz": rate_hz,
+            "offered_load": round(rate_hz * mean_service, 2),
+            "p50_s": round(float(np.percentile(lat, 50)), 3), "p99_s": round(float(np.percentile(lat, 99)), 3),
+            "max_s": round(lat[-1], 3), "mean_admission_wait_s": round(float(np.mean(wait)), 3),
             "realizations_per_hour": round(count / wall * 3600.0, 1),
-            "mcell_updates_per_s": round(sum(work) / wall / 1e6, 1), "failed": st["failed"],
-            "stream": "Poisson arrivals, grid edge 64..160 incl. CPML, 2000..8000 steps, half passive half "
-                      "lasing (served-workload generator scaled down), 150 GB budget, 64 slots, 500-step chunks"}
+            "mcell_updates_per_s": round(thr, 1), "failed": st["failed"],
+            "stream": f"{count} requests, Poisson arrivals at {rate_hz}/s, passive and lasing runs of the served "
+                      "workload generator, grid edge 64..200 incl. CPML, 5000..50000 steps, 150 GB budget, 64 slots, "
+                      "500-step chunks; p50/p99 by linear interpolation between order statistics"}
 
 
 def fp32_vs_fp64_errors(specs, grids, sample: int = 4):
@@ -415,8 +494,6 @@ def fp32_vs_fp64_errors(specs, grids, sample: int = 4):
     member, as the batch left it, against the same realization stepped alone
     in binary64 on the GPU for as many steps: relative L2 of the six fields and
     of each flux series."""
-    import numpy as np
-
     from paper_0802_3775_gb300.fdtd import Grid
 
     out = []
@@ -461,9 +538,82 @@ def fp64_plain_rate(specs, steps_run: int, steps: int = 60, sample: int = 4):
     return 3600.0 / per, len(secs)
 
 
-# ----------------------------------------------------------------------------- CPU oracle
+# ----------------------------------------------------------------------------- CPU oracle leg
+# Everything below that runs the oracle is the benchmark's CPU leg: the oracle
+# timed on the host cores, and the oracle results the GPU path is measured
+# against.  Worker processes are started with "spawn" (never forked from a
+# process that has touched the GPU).
+
+def _single_thread_env():
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+
+
+def _oracle_timing_worker(spec, seconds, steps, warmup, barrier, queue, slot):
+    """One process: build the oracle of `spec`, step `warmup` steps, wait for
+    the others, then step for `steps` steps (or for `seconds` when steps is
+    0); reports (slot, steps, seconds)."""
+    _single_thread_env()
+    sys.path.insert(0, ROOT)
+    from oracle import Oracle
+    o = Oracle.from_spec(spec)
+    o.step(max(1, warmup))
+    try:
+        barrier.wait(timeout=600)
+    except Exception:
+        pass
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        o.step(1)
+        n += 1
+        t = time.perf_counter() - t0
+        if (steps and n >= steps) or (not steps and t >= seconds):
+            break
+    queue.put((slot, n, t))
+
+
+def oracle_processes(spec_cells, lasing):
+    """Processes for the all-core oracle timing: one per allowed core, fewer
+    when the host's available memory would not hold them at half of it
+    (~360 B per cell for a passive oracle grid at its peak, ~600 with gain)."""
+    cores = len(os.sched_getaffinity(0))
+    avail = None
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    per = spec_cells * (600 if lasing else 360)
+    if avail:
+        cores = max(1, min(cores, int(0.5 * avail // per)))
+    return cores
+
+
+def time_oracle_all_cores(specs, seconds=10.0, steps=0, warmup=1):
+    """Aggregate oracle rate with one process per spec stepping concurrently
+    (independent realizations): sum over processes of cells x steps / time.
+    Returns (Mcell/s, per-process (steps, seconds))."""
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(len(specs))
+    queue = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_timing_worker, args=(s, seconds, steps, warmup, barrier, queue, q))
+             for q, s in enumerate(specs)]
+    for p in procs:
+        p.start()
+    res = [queue.get(timeout=1800) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+    res.sort()
+    rate = sum(specs[q].cells * n / t for q, n, t in res) / 1e6
+    return rate, [(n, t) for _, n, t in res]
+
+
 def _oracle_sample(spec, seconds: float):
-    """Time the FP64 oracle on `spec` for about `seconds`; returns (Mcell/s, steps, cells)."""
+    """Time the FP64 oracle on `spec` in this process for about `seconds`;
+    returns (Mcell/s, steps, cells)."""
     from oracle import Oracle
     o = Oracle.from_spec(spec)
     o.step(1)
@@ -478,13 +628,99 @@ def _oracle_sample(spec, seconds: float):
     return spec.cells * n / t / 1e6, n, spec.cells
 
 
-def cpu_baseline(args, seconds: float = 12.0):
+def _oracle_run_worker(spec, steps, coef32):
+    """Oracle results of `steps` steps of `spec` (fields, flux, probes)."""
+    _single_thread_env()
+    sys.path.insert(0, ROOT)
+    from oracle import Oracle
+    o = Oracle.from_spec(spec, coef32=coef32)
+    o.step(steps)
+    return (o.fields_memory_order(), o.flux_series() if o.fluxes else None,
+            o.probe_series() if o.probes else None)
+
+
+def _rel(a, b):
+    nb = float(np.linalg.norm(np.asarray(b).ravel()))
+    return float(np.linalg.norm((np.asarray(a) - np.asarray(b)).ravel()) / (nb if nb > 0 else 1.0))
+
+
+def oracle_errors(args, steps=150):
+    """The GPU path against the FP64 oracle on reduced copies of the workload
+    (2x2x2 unit cells of the same recipe; for the default workload also the
+    first four members of the batch, reduced the same way and stepped as a
+    batch): relative L2 of the six fields, of each flux series and of the
+    probe series after `steps` steps, against the oracle fed the run's
+    rounded coefficient tables (coef32 for binary32 runs) and, for the first
+    run, the fields against the exact-coefficient oracle too.  The oracle
+    runs go to a spawn pool while the GPU steps its copies."""
+    import torch
+
+    from paper_0802_3775_gb300.fdtd import Batch, Grid
+
+    sets = [(args.workload, reduced_specs(args.workload, steps))]
+    if args.workload == "planewave" and not args.no_batch:
+        sets.append(("batch", reduced_specs("batch", steps)))
+    runs = [(name, s) for name, specs in sets for s in specs]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(processes=min(len(runs) + 1, len(os.sched_getaffinity(0)))) as pool:
+        rounded = [pool.apply_async(_oracle_run_worker, (s, steps, s.precision == "f32")) for _, s in runs]
+        s0 = runs[0][1]
+        exact = pool.apply_async(_oracle_run_worker, (s0, steps, False)) if s0.precision == "f32" else None
+        gpu = []
+        for name, specs in sets:
+            grids = [Grid.from_spec(s, record_capacity=steps + 16) for s in specs]
+            if len(grids) > 1:
+                b = Batch(grids)
+                b.step(steps)
+                b.sync()
+                b.close()
+            else:
+                grids[0].step(steps)
+                grids[0].sync()
+            for g in grids:
+                gpu.append((g.read_fields(), g.read_flux() if g.nflux else None,
+                            g.read_probes() if g.nprobe else None))
+                g.close()
+        torch.cuda.synchronize()
+        ref = [p.get(timeout=1800) for p in rounded]
+        ref_exact = exact.get(timeout=1800) if exact is not None else None
+    out = []
+    for q, ((name, s), (F, T, P), (Fo, To, Po)) in enumerate(zip(runs, gpu, ref)):
+        rec = {"what": f"{name}: {s.shape[0]}x{s.shape[1]}x{s.shape[2]} "
+                       f"{'lasing' if s.gain is not None else 'passive'} {s.precision}, {steps} steps",
+               "fields_rel_l2": _rel(F, Fo)}
+        if T is not None and To is not None:
+            rec["flux_rel_l2"] = _rel(T, To)
+        if P is not None and Po is not None:
+            rec["probes_rel_l2"] = _rel(P, Po)
+        if q == 0 and ref_exact is not None:
+            rec["fields_rel_l2_vs_exact_coefficients"] = _rel(F, ref_exact[0])
+        out.append(rec)
+    return {"reference": "FP64 oracle fed the run's rounded coefficient tables", "runs": out}
+
+
+def cpu_leg(args, seconds: float = 10.0):
+    """The oracle on the host cores: all cores (one process per allowed core,
+    each stepping its own realization of the workload) and one thread (one
+    realization in this process); then the error checks against it."""
     specs = workload_specs(args.workload, 0, 1)
     spec = specs[1] if len(specs) > 1 and specs[1].gain is not None else specs[0]
-    v, n, cells = _oracle_sample(spec, seconds)
-    return {"value": round(v, 3), "unit": "Mcell-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} steps of one {spec.shape[0]}x{spec.shape[1]}x{spec.shape[2]} realization of the "
-                      f"workload (numpy FP64, single thread)"}
+    lasing = spec.gain is not None
+    nproc = oracle_processes(spec.cells, lasing)
+    if len(specs) == 1:
+        pspecs = [workload_specs(args.workload, q, 1)[0] for q in range(nproc)]
+    else:
+        pspecs = [s for s in specs if (s.gain is not None) == lasing][:nproc]
+    rate_all, per = time_oracle_all_cores(pspecs, seconds=seconds)
+    v1, n1, _ = _oracle_sample(spec, seconds)
+    sh = f"{spec.shape[0]}x{spec.shape[1]}x{spec.shape[2]}"
+    baseline = {"value": round(rate_all, 3), "unit": "Mcell-updates/s", "cores": len(pspecs), "kind": "oracle",
+                "sample": f"{len(pspecs)} processes, each stepping its own realization of the workload "
+                          f"({'lasing' if lasing else 'passive'}, up to {sh} cells) for ~{seconds:.0f} s "
+                          f"({min(n for n, _ in per)}..{max(n for n, _ in per)} steps); numpy FP64, one thread each",
+                "single_thread": {"value": round(v1, 3), "cores": 1,
+                                  "sample": f"{n1} steps of one {sh} realization of the workload (numpy FP64)"}}
+    return baseline, oracle_errors(args)
 
 
 def run_reference(args, rank):
@@ -500,31 +736,39 @@ def run_reference(args, rank):
     t0 = time.perf_counter()
     probe.step(1)
     t1 = time.perf_counter() - t0
-    note = "full realization"
+    note = "full realizations"
+    shrink_ncell = None
     if t1 > per_step:
         shrink = max(0.2, (per_step / t1) ** (1 / 3))
-        if sample.gain is not None:
-            ncell = max(2, int(round(6 * shrink)))
-            sample = inputs.opal_lasing_f32(ncell=ncell, res=20, npml=10, sigma=0.05, pump=1e10)
-        else:
-            ncell = max(2, int(round(8 * shrink)))
-            sample = inputs.opal_planewave_f32(ncell=ncell, res=20, npml=12, sigma=0.06,
-                                               precision=spec.precision)
-        note = f"{ncell}^3 unit cells ({sample.shape[0]}^3 grid) of the same workload"
-        probe = Oracle.from_spec(sample)
-    for _ in range(args.warmup):
-        probe.step(1)
-    t0 = time.perf_counter()
-    probe.step(args.steps)
-    t = time.perf_counter() - t0
-    value = sample.cells * args.steps / t / 1e6
+        base = 6 if sample.gain is not None else 8
+        shrink_ncell = max(2, int(round(base * shrink)))
+    del probe
+
+    def sample_spec(q):
+        s = workload_specs(args.workload, q, 1)[0]
+        if shrink_ncell is None:
+            return s
+        if s.gain is not None:
+            return inputs.opal_lasing_f32(ncell=shrink_ncell, res=20, npml=10, sigma=0.05, pump=1e10, realization=q)
+        return inputs.opal_planewave_f32(ncell=shrink_ncell, res=20, npml=12, sigma=0.06, realization=q,
+                                         precision=s.precision)
+
+    nproc = oracle_processes(sample_spec(0).cells, spec.gain is not None)
+    pspecs = [sample_spec(q) for q in range(nproc)]
+    if shrink_ncell is not None:
+        s0 = pspecs[0]
+        note = f"{shrink_ncell}^3 unit cells ({s0.shape[0]}^3 grid) of the same workload"
+    # every process steps warmup + steps; the timed part is its last `steps`
+    value, per = time_oracle_all_cores(pspecs, steps=args.steps, warmup=args.warmup)
+    ms = 1e3 * statistics.mean(t / n for n, t in per)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "Mcell-updates/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t / args.steps, 3),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT[args.workload]},
-        "cpu_baseline": {"value": round(value, 3), "unit": "Mcell-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": note + ", numpy FP64 oracle, single thread"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "Mcell-updates/s", "cores": nproc, "kind": "oracle",
+                         "sample": note + f", numpy FP64 oracle, {nproc} processes (one per allowed core, each its "
+                                          "own realization, one thread each)"},
         "e2e": {"value": round(value, 3), "unit": "Mcell-updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }))
@@ -542,6 +786,8 @@ def main():
     ap.add_argument("--by", type=int, default=0, help="tile rows of the step kernel (0: library default)")
     ap.add_argument("--zdepth", type=int, default=0, help="planes per work item (0: library default)")
     ap.add_argument("--no-serve", action="store_true", help="skip the served request stream")
+    ap.add_argument("--serve-requests", type=int, default=32, help="requests of the served stream")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched sub-record of the default workload")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shape")
     args = ap.parse_args()
     if args.warmup < 3:

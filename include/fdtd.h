@@ -286,6 +286,18 @@ int fdtd_field_energy(fdtd_grid* g, double* out);
  * fdtd_step_n or a batch).  Default: no limit. */
 int fdtd_set_step_limit(fdtd_grid* g, int64_t limit);
 
+/* Limit, in nanoseconds, of every wait of the TMA-staged step kernels for a
+ * staged plane of this grid (default 2e9).  A wait that runs out makes the
+ * kernel let its copies in flight land (each within 2 s), stop its block and
+ * flag the grid, and the next fdtd_sync / read returns FDTD_E_TIMEOUT; the
+ * CUDA context stays usable, the grid's state is then undefined.  0 makes
+ * every such wait give up at once without looking at the copy (a healthy
+ * run's way to test that error path).  The paper has no counterpart: this is
+ * the library's guard against a copy that never completes.  E_INVAL if
+ * ns < 0.  Takes effect at the next step call; a batch takes each member's
+ * limit when it is created. */
+int fdtd_set_wait_limit(fdtd_grid* g, int64_t ns);
+
 /* ---------------------------------------------------------------- batches
  * Many grids of mixed size stepped together (the disorder realizations of the
  * paper, Sec. "Wide-band excitation and gap filling", are independent runs):
@@ -404,8 +416,10 @@ int fdtd_server_get_stats(fdtd_server* s, fdtd_server_stats* out);
  * 65536); larger inputs return E_INVAL.  The call synchronizes `stream`.
  * Every call shares that scratch and leaves the last call's contents there;
  * calls that overlap on the GPU race, so serialize them.  The scratch's
- * device address is looked up on the first call made on each device, so make
- * that first call before capturing a stream into a CUDA graph. */
+ * device address is looked up on every call whose stream is not being
+ * captured (a device reset may move it) and remembered per device for calls
+ * made during a capture, so make the first call on each device before
+ * capturing a stream into a CUDA graph. */
 int fdtd_field_energy_noalloc(const void* const fields[6], const uint8_t* mat, int32_t nx, int32_t ny, int32_t nz,
                               int32_t pitch, int32_t precision, const double eps[3], double dx, void* stream,
                               double* out);

@@ -467,6 +467,16 @@ int fdtd_set_step_limit(fdtd_grid* g, int64_t limit) {
   });
 }
 
+int fdtd_set_wait_limit(fdtd_grid* g, int64_t ns) {
+  return guarded([&]() -> int {
+    CHECK_GRID(g);
+    if (ns < 0) return set_error(FDTD_E_INVAL, "negative wait limit");
+    G->wait_ns = ns;
+    G->tables_dirty = true;
+    return FDTD_OK;
+  });
+}
+
 #define CHECK_BATCH(b)                                                  \
   if (!(b) || !(b)->impl) return set_error(FDTD_E_INVAL, "null batch"); \
   fdtd::BatchBase* B = (b)->impl

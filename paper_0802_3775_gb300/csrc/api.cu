@@ -226,6 +226,7 @@ struct GridImpl final : GridBase {
     sg.nsets = og.nsets = 2;  // three once the grid is frozen on the paired kernel
     sg.step = 0;
     sg.step_end = (long long)0x7fffffffffffffffLL;
+    sg.wait_ns = wait_ns;
     og.step = 0;
     og.step_end = sg.step_end;
     og.err = d_err;
@@ -609,6 +610,7 @@ struct GridImpl final : GridBase {
     cudaError_t e;
     sg.step = og.step = steps;
     sg.step_end = og.step_end = step_limit;
+    sg.wait_ns = wait_ns;
     tables_dirty = false;
     if ((e = cudaMemcpyAsync(d_sg, &sg, sizeof(sg), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return cuda_error(e, "upload grid");
     if ((e = cudaMemcpyAsync(d_og, &og, sizeof(og), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return cuda_error(e, "upload grid");

@@ -124,6 +124,7 @@ struct BatchImpl final : BatchBase {
       std::memcpy(&hog[q], g->obs_record(), sizeof(ObsGrid<T>));
       hsg[q].step = hog[q].step = g->steps;
       hsg[q].step_end = hog[q].step_end = g->step_limit;
+      hsg[q].wait_ns = g->wait_ns;
       std::vector<int4> si, oi;
       g->work_items(si, oi);
       // members' lists are ordered longest first; merge them by position so

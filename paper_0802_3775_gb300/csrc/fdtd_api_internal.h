@@ -138,6 +138,7 @@ struct GridBase {
   uint8_t* d_mat = nullptr;
   LaunchTimer timer;
   long long step_limit = 0x7fffffffffffffffLL;  // no update n >= step_limit
+  long long wait_ns = 2000000000LL;              // limit of the TMA step kernels' bounded waits
   bool tables_dirty = false;                     // device records stale (stepped by a batch)
 
   virtual ~GridBase() { mem.release_all(); }

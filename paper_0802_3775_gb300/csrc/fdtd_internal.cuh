@@ -71,6 +71,7 @@ struct StepGrid {
   int nsrc;
   long long step;       // steps completed before this launch sequence
   long long step_end;   // no update n >= step_end is performed
+  long long wait_ns;    // limit of a bounded wait of the TMA step kernels (ns; <= 0: give up at once)
   T* F[kFieldSets][6];  // field sets (set n%nsets: E^n, H~^{n-1/2}): Ex Ey Ez Hx Hy Hz
   int nsets;            // field sets in the cycle (2 or 3)
   const uint8_t* mat;   // material bytes
@@ -86,7 +87,7 @@ struct StepGrid {
   T a1, a2, a3, n12eq, q, noise;
   T D[3][3], w[3];
   unsigned long long seed;
-  int* err;             // bit 1: a bounded wait of the step kernel ran out
+  int* err;             // bit 1: a bounded wait of the step kernel ran out; bit 2: a drain after it ran out too
   SrcDev src[kMaxSrc];
 };
 

@@ -343,6 +343,7 @@ __global__ void __launch_bounds__(TmaThreads<T, OY>::NT, TmaThreads<T, OY>::MIN_
   __syncthreads();
 
   unsigned ld = 0;  // plane loads issued by this block so far (same value in every thread)
+  IssuedLoads loads;  // thread 0: the loads it issued, drained if the block gives up
   int cur = -1;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int4 item = items[it];
@@ -370,6 +371,7 @@ __global__ void __launch_bounds__(TmaThreads<T, OY>::NT, TmaThreads<T, OY>::MIN_
     auto issue = [&](unsigned q, int plane) {
       const int s = (int)(q % S);
       unsigned char* dst = stages + (size_t)s * L::stage_bytes;
+      loads.note(s);
       mbar_arrive_expect_tx(&full[s], TX_BYTES);
       tma_load_4d(dst, fmap, x0 - AX, y0 - 1, plane, fs * 6, &full[s]);
       tma_load_3d(dst + L::field_bytes, mmap, x0, y0, plane, &full[s]);
@@ -486,8 +488,8 @@ __global__ void __launch_bounds__(TmaThreads<T, OY>::NT, TmaThreads<T, OY>::MIN_
       T* sHx = reinterpret_cast<T*>(smem + L::h_off + (p & 1) * L::hbuf_bytes);  // H of this plane
       T* sHy = sHx + HPL;
       T* sHz = sHy + HPL;
-      if (p == 0) ok = ok && mbar_wait(&full[q % S], (q / S) & 1);
-      ok = ok && mbar_wait(&full[(q + 1) % S], ((q + 1) / S) & 1);
+      if (p == 0) ok = ok && mbar_wait(&full[q % S], (q / S) & 1, G.wait_ns);
+      ok = ok && mbar_wait(&full[(q + 1) % S], ((q + 1) / S) & 1, G.wait_ns);
       cp_async_wait<S - 1>();  // this thread's CPML memory of plane p
       const unsigned char* stg = stages + (size_t)(q % S) * L::stage_bytes;
       const T* Fk = reinterpret_cast<const T*>(stg);
@@ -557,8 +559,10 @@ __global__ void __launch_bounds__(TmaThreads<T, OY>::NT, TmaThreads<T, OY>::MIN_
         sHz[slot] = c;
       }
       if (__syncthreads_or(!ok)) {
+        // a wait ran out: let this thread's copies and the block's loads in
+        // flight land (bounded) before the block leaves, then report
         cp_async_wait<0>();
-        if (tid == 0) atomicOr(G.err, 2);
+        if (tid == 0) atomicOr(G.err, loads.drain(full, S) ? 2 : 6);
         return;
       }
       // nothing reads the fields of plane p's stage after this barrier: refill it

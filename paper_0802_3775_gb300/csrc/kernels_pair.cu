@@ -455,6 +455,7 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
 
   unsigned ld = 0;     // planes of the items before this one (same value in every thread)
   unsigned phase = 0;  // bit s: parity of the next completion of stage s's barrier
+  IssuedLoads loads;   // producer: the loads it issued, drained if the block gives up
   int pf = 0;          // producer: planes of this item already issued by the previous item
   int cur = -1;
   for (int it = blockIdx.x, r = 0; it < nitems; it += gridDim.x, ++r) {
@@ -487,6 +488,7 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
 
     auto issue = [&](int s, int plane) {
       unsigned char* dst = stages + (size_t)s * L::stage_bytes;
+      loads.note(s);
       mbar_arrive_expect_tx(&full[s], TX_BYTES);
       tma_load_4d(dst, fmap, x0 - AX, y0 - 1, plane, fs * 6, &full[s]);
       tma_load_3d(dst + L::field_bytes, mmap, x0, y0, plane, &full[s]);
@@ -698,7 +700,7 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
     // stages of the current and the next plane, advanced by rotation
     int sk = (int)(q0 % S), sn = sk + 1 == S ? 0 : sk + 1;
     auto wait_stage = [&](int s) {
-      ok = ok && mbar_wait(&full[s], (phase >> s) & 1u);
+      ok = ok && mbar_wait(&full[s], (phase >> s) & 1u, G.wait_ns);
       phase ^= 1u << s;
     };
     for (int p = 0; p < NP - 1; ++p) {
@@ -779,8 +781,10 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
         }
       }
       if (__syncthreads_or(!ok)) {
+        // a wait ran out: let this thread's copies and the block's loads in
+        // flight land (bounded) before the block leaves, then report
         cp_async_wait<0>();
-        if (producer) atomicOr(G.err, 2);
+        if (producer) atomicOr(G.err, loads.drain(full, S) ? 2 : 6);
         return;
       }
       // nothing reads the fields of plane p's stage after this barrier: refill
@@ -793,6 +797,7 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
         } else if (p + S - NP < nxt.cnt) {
           fence_proxy_async_smem();
           unsigned char* dst = stages + (size_t)sk * L::stage_bytes;
+          loads.note(sk);
           mbar_arrive_expect_tx(&full[sk], TX_BYTES);
           tma_load_4d(dst, nxt.fmap, nxt.x0 - AX, nxt.y0 - 1, nxt.kstart + p + S - NP, nxt.fs * 6, &full[sk]);
           tma_load_3d(dst + L::field_bytes, nxt.mmap, nxt.x0, nxt.y0, nxt.kstart + p + S - NP, &full[sk]);

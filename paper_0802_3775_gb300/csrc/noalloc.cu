@@ -15,9 +15,10 @@
 // last call; the arrival counter is cleared at the start of each call.  Calls
 // that overlap on the GPU (two streams, or two host threads) use the same
 // scratch and race; serialize them.  The scratch's device address is looked
-// up once per device, on the first call made with that device current, so
-// make the first call on each device before capturing any stream into a CUDA
-// graph.
+// up with the device current on every call whose stream is not being
+// captured (a device reset reloads the module and may move the array), and
+// kept per device for calls made during a capture, so make the first call on
+// each device before capturing any stream into a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,12 +45,15 @@ struct StaticScratch {
 static __device__ __align__(256) StaticScratch g_static_scratch;
 
 std::mutex g_scratch_mu;
-std::vector<StaticScratch*> g_scratch_addr;  // per device, looked up once
+std::vector<StaticScratch*> g_scratch_addr;  // per device, the address last looked up
 
-int scratch_address(int dev, StaticScratch** out) {
+// Device address of the scratch on device `dev` (current).  Looked up again
+// unless `capturing`: a device reset between calls reloads the module, and
+// the array may then sit elsewhere.
+int scratch_address(int dev, bool capturing, StaticScratch** out) {
   std::lock_guard<std::mutex> lk(g_scratch_mu);
   if ((int)g_scratch_addr.size() <= dev) g_scratch_addr.resize(dev + 1, nullptr);
-  if (!g_scratch_addr[dev]) {
+  if (!g_scratch_addr[dev] || !capturing) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress of the static scratch");
@@ -123,14 +127,23 @@ extern "C" int fdtd_field_energy_noalloc(const void* const fields[6], const uint
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
-  StaticScratch* s = nullptr;
-  int r = scratch_address(dev, &s);
-  if (r != FDTD_OK) return r;
   cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return cuda_error(e, "cudaStreamIsCapturing");
+  StaticScratch* s = nullptr;
+  int r = scratch_address(dev, cap != cudaStreamCaptureStatusNone, &s);
+  if (r != FDTD_OK) return r;
   // the arrival counter must start at zero (an interrupted earlier call may have left it set)
   e = cudaMemsetAsync(&s->counter, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return cuda_error(e, "clear the static scratch counter");
-  const int blocks = (int)std::min<long long>(kStaticBlocks, (ncell + kStaticCellsPerBlock - 1) / kStaticCellsPerBlock);
+  // at least two blocks per SM (the grid-stride loop takes any count up to
+  // the kStaticBlocks partial sums), more when a block would fold more than
+  // kStaticCellsPerBlock cells
+  int sms = 0;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return cuda_error(e, "cudaDeviceGetAttribute");
+  const long long need = (ncell + kStaticCellsPerBlock - 1) / kStaticCellsPerBlock;
+  const int blocks = (int)std::min<long long>(kStaticBlocks, std::max<long long>(2LL * sms, need));
   if (precision == FDTD_FP32) {
     const float* const* f = reinterpret_cast<const float* const*>(fields);
     k_energy_static<float><<<blocks, 256, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5], mat, nx, ny, pitch, ncell,

@@ -72,15 +72,44 @@ __device__ __forceinline__ bool mbar_try_wait_for(uint64_t* bar, unsigned parity
   return ok != 0;
 }
 
-// Wait for phase `parity` of an mbarrier, giving up after about 2 s.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+// Limit of a drain wait (the copies a block issued before giving up).
+constexpr long long kDrainWaitNs = 2000000000LL;
+
+// Wait for phase `parity` of an mbarrier, giving up after `limit_ns`
+// nanoseconds (a grid's bounded-wait limit, 2 s unless set otherwise); a
+// limit <= 0 gives up at once, without looking at the barrier (the error
+// path's test).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit_ns) {
+  if (limit_ns <= 0) return false;
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (;;) {
     if (mbar_try_wait_for(bar, parity, 100000u)) return true;  // suspended up to 0.1 ms per try
-    if (global_ns() - t0 > 2000000000ull) return false;
+    if (global_ns() - t0 > (unsigned long long)limit_ns) return false;
   }
 }
+
+// Issued TMA loads of one block, per stage: the producer records every load
+// it issues, and a block that gives up waits (bounded) for the loads still in
+// flight before it exits, so no copy lands in shared memory after the block
+// has left the SM.  Each stage holds at most one load in flight (a stage is
+// refilled only after its plane was consumed), and the k-th load into a stage
+// completes its barrier's phase k, of parity k & 1.
+struct IssuedLoads {
+  unsigned used = 0;  // bit s: stage s received a load
+  unsigned par = 0;   // bit s: parity of the phase the latest load into stage s completes
+  __device__ __forceinline__ void note(int s) {
+    par = (used >> s) & 1u ? par ^ (1u << s) : par & ~(1u << s);
+    used |= 1u << s;
+  }
+  // wait for the latest load of every used stage (returns false if one never landed)
+  __device__ __forceinline__ bool drain(uint64_t* full, int stages) const {
+    bool all = true;
+    for (int s = 0; s < stages; ++s)
+      if ((used >> s) & 1u) all = mbar_wait(&full[s], (par >> s) & 1u, kDrainWaitNs) && all;
+    return all;
+  }
+};
 
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint64_t* bar) {

@@ -93,6 +93,7 @@ SIGNATURES = {
     "fdtd_set_timing": [_P, C.c_int32],
     "fdtd_kernel_time": [_P, _D, C.POINTER(C.c_int64)],
     "fdtd_set_step_limit": [_P, C.c_int64],
+    "fdtd_set_wait_limit": [_P, C.c_int64],
     "fdtd_batch_create": [C.POINTER(_P), C.c_int32, _P, C.POINTER(_P)],
     "fdtd_batch_destroy": [_P],
     "fdtd_batch_set_launch": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
@@ -296,6 +297,10 @@ class Grid:
 
     def set_step_limit(self, limit):
         check(self._lib.fdtd_set_step_limit(self.h, int(limit)))
+
+    def set_wait_limit(self, ns):
+        """Limit (ns) of the TMA step kernels' bounded waits; 0 gives up at once."""
+        check(self._lib.fdtd_set_wait_limit(self.h, int(ns)))
 
     # -- stepping
     def step(self, n=1):

@@ -299,15 +299,20 @@ def opal_lasing_f32(ncell: int = 6, res: int = 20, npml: int = 10, sigma: float 
 
 
 def mixed_batch(count: int = 64, seed: int = 4000, steps: int = 20000, npml: int = 12,
-                precision: str = "f32"):
+                precision: str = "f32", ncell: int | None = None):
     """Mixed-size batch: n in 4..8 unit cells, 16..20 cells/a, sigma ~ U(0, 10%);
-    even members passive plane-wave runs, odd members lasing runs."""
+    even members passive plane-wave runs, odd members lasing runs.  `ncell`
+    given: every member keeps its draws (resolution, sigma, seeds) but spans
+    `ncell`^3 unit cells (the reduced members of the error checks)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
+    fixed = ncell
     for r in range(count):
         ncell = int(rng.integers(4, 9))
         res = int(rng.integers(16, 21))
         sigma = float(rng.uniform(0.0, 0.10))
+        if fixed is not None:
+            ncell = int(fixed)
         if r % 2 == 0:
             s = opal_planewave_f32(ncell=ncell, res=res, npml=npml, sigma=sigma, realization=r,
                                    steps=steps, precision=precision)
