@@ -38,8 +38,16 @@ Readings where the paper is silent (also listed in the design notes):
     c = sigma (b - 1) / (sigma kappa + kappa^2 alpha).  Depth rho(x) = (L0 - x)/L0
     below L0 and (x - (n - L1))/L1 above n - L1, x the node coordinate in cells
     (integer for E-curl terms, half-integer for H-curl terms).
-  * Gain per cell: P_c(i,j,k) sits on E_c(i,j,k); the populations of cell
-    (i,j,k) drive and are driven by that cell's three components.
+  * Gain per cell ("cell" coupling): P_c(i,j,k) sits on E_c(i,j,k); the
+    populations of cell (i,j,k) drive and are driven by that cell's three
+    components.
+  * "centred" coupling (the paper solves the Bloch variables in the middle of
+    the Yee cell): P and N live at the cell centre (i+1/2, j+1/2, k+1/2); the
+    oscillator is driven by the centre average E_bar = A E of the four
+    E_c edges of the cell, the polarization current reaches each E_c edge
+    as the average A^T dP of the four cells that share the edge, and the
+    populations see r = eps0/(hbar omega_a) sum_c A((E^{n+1}+E^n)/2)_c dP_c,
+    so the field-medium exchange balances exactly (A^T is A's adjoint).
   * coef32: round every update coefficient (S, S/eps_r, 1/eps_r, 1/kappa, b, c,
     a1, a2) to binary32, which defines the discrete problem an FP32 run solves.
 """
@@ -144,7 +152,7 @@ class Oracle:
             g = spec.gain
             o.set_gain(n_total=g.n_total, fa_hat=g.fa_hat, dw_rel=g.dw_rel, tau32=g.tau32,
                        tau21=g.tau21, tau10=g.tau10, pump=g.pump, kappa=g.kappa,
-                       noise_amp=g.noise_amp, init=g.init)
+                       noise_amp=g.noise_amp, init=g.init, coupling=getattr(g, "coupling", "cell"))
         for s in spec.sources:
             o.add_source(kind=s.kind, comp=s.comp, pos=s.pos, axis=s.axis, index=s.index,
                          waist=s.waist, f0_hat=s.f0_hat, rel_bw=s.rel_bw, t0_steps=s.t0_steps,
@@ -203,7 +211,7 @@ class Oracle:
         self.set_material(_rasterize(self.shape, spheres, box_lo, box_hi))
 
     def set_gain(self, *, n_total, fa_hat, dw_rel, tau32, tau21, tau10, pump, kappa=0.0,
-                 noise_amp=0.0, init="steady"):
+                 noise_amp=0.0, init="steady", coupling="cell"):
         omega_a = 2.0 * math.pi * fa_hat * C0 / self.a
         domega = dw_rel * omega_a
         if kappa == 0.0:
@@ -217,6 +225,9 @@ class Oracle:
         self.gain = dict(a1=float(self.R(a1)), a2=float(self.R(a2)), a3=a3, A=A, MmI=m_minus_i, w=w,
                          n_eq=n_eq, n_total=n_total, omega_a=omega_a, domega=domega, kappa=kappa,
                          q=EPS0 / (HBAR * omega_a), noise_amp=float(noise_amp), mask=mask)
+        if coupling not in ("cell", "centred"):
+            raise ValueError(coupling)
+        self.gain["centred"] = coupling == "centred"
         self.P = np.zeros((3, nx, ny, nz))
         self.Pm = np.zeros((3, nx, ny, nz))
         self.dN = np.zeros((4, nx, ny, nz))
@@ -287,6 +298,44 @@ class Oracle:
         pad = np.zeros_like(np.take(F, [0], axis=d))
         return np.diff(np.concatenate([pad, F], axis=d), axis=d)
 
+    def _nb(self, F, d, s):
+        """F at the neighbour idx + s along axis d (s = +1 or -1); outside the
+        arrays it reads 0, or wraps on a periodic axis."""
+        if self.periodic[d]:
+            return np.roll(F, -s, axis=d)
+        out = np.zeros_like(F)
+        src = [slice(None)] * 3
+        dst = [slice(None)] * 3
+        if s > 0:
+            src[d], dst[d] = slice(1, None), slice(0, -1)
+        else:
+            src[d], dst[d] = slice(0, -1), slice(1, None)
+        out[tuple(dst)] = F[tuple(src)]
+        return out
+
+    def to_cells(self, E):
+        """A: the centre average of each E component over the four edges of
+        its orientation around cell (i, j, k): for E_c with (d1, d2) the other
+        two axes in cyclic order, 1/4 ((E + E[+d1]) + (E[+d2] + E[+d1+d2]))."""
+        out = np.empty_like(E)
+        for c in range(3):
+            d1, d2 = (c + 1) % 3, (c + 2) % 3
+            F = E[c]
+            F2 = self._nb(F, d2, +1)
+            out[c] = 0.25 * ((F + self._nb(F, d1, +1)) + (F2 + self._nb(F2, d1, +1)))
+        return out
+
+    def to_edges(self, P):
+        """A^T: at each E_c edge, 1/4 of the sum of the cell values of the four
+        cells sharing it, 1/4 ((P + P[-d1]) + (P[-d2] + P[-d1-d2]))."""
+        out = np.empty_like(P)
+        for c in range(3):
+            d1, d2 = (c + 1) % 3, (c + 2) % 3
+            F = P[c]
+            F2 = self._nb(F, d2, -1)
+            out[c] = 0.25 * ((F + self._nb(F, d1, -1)) + (F2 + self._nb(F2, d1, -1)))
+        return out
+
     def _term(self, D, d, comp, kind):
         """Difference D along d as seen by component `comp`: D/kappa + psi inside slabs."""
         if not self._has_pml(d):
@@ -338,22 +387,30 @@ class Oracle:
         if g is not None:
             N = self.populations()
             dn12 = (N[1] - N[2])
-            P_new = g["a1"] * self.P - g["a2"] * self.Pm + g["a3"] * dn12[None] * E_n
+            # the field that drives the oscillator: on the cell's own nodes, or
+            # averaged to the cell centre
+            E_drive = self.to_cells(E_n) if g["centred"] else E_n
+            P_new = g["a1"] * self.P - g["a2"] * self.Pm + g["a3"] * dn12[None] * E_drive
             if g["noise_amp"] != 0.0:
                 xi = gain_noise(self.seed, n, self._cell_index)
                 for c in range(3):
                     P_new[c][g["mask"]] += g["noise_amp"] * xi[c]
             P_new *= g["mask"][None]
             dP = P_new - self.P
+            # the polarization current on the E nodes
+            dP_nodes = self.to_edges(dP) if g["centred"] else dP
         # 4. electric step
         src = np.zeros_like(E_n)
         for s in self.sources:
             src[s["comp"]] += s["w"] * float(waveform(n, s["f0_hat"], s["rel_bw"], self.S, self.res, s["t0_steps"]))
-        E_new = E_n + self.cE * self.curl_H(H_new) - self.cP * (dP + src)
+        E_new = E_n + self.cE * self.curl_H(H_new) - self.cP * ((dP_nodes if g is not None else dP) + src)
         self._pec(E_new)
         # 5. populations
         if g is not None:
-            r = g["q"] * np.sum(0.5 * (E_new + E_n) * dP, axis=0)
+            E_half = 0.5 * (E_new + E_n)
+            if g["centred"]:
+                E_half = self.to_cells(E_half)
+            r = g["q"] * np.sum(E_half * dP, axis=0)
             inc = np.einsum("ab,bijk->aijk", g["MmI"], self.dN) + g["w"][:, None, None, None] * r[None]
             self.dN = (self.dN + inc) * g["mask"][None]
             self.Pm = self.P

@@ -170,6 +170,7 @@ class GainSpec:
     kappa: float = 0.0           # coupling; 0 = 6 pi eps0 c^3 / (omega_a^2 tau21)
     noise_amp: float = 0.0       # V/m (std of the normalized polarization kick per step)
     init: str = "steady"         # "steady" (N = N_eq) or "ground" (all in level 0)
+    coupling: str = "cell"       # "cell": P on the cell's own E nodes; "centred": P at the cell centre
 
 
 @dataclass
