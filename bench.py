@@ -364,7 +364,8 @@ def run_gpu(args, rank, world, dist):
         if args.workload == "planewave" and not args.no_batch:
             result["batch"] = batch_record(args)
             result["gpu_launches"] += result["batch"]["gpu_launches"]
-        result["cpu_baseline"], result["oracle_error"] = cpu_leg(args)
+        if not args.no_cpu:
+            result["cpu_baseline"], result["oracle_error"] = cpu_leg(args)
     if rank == 0:
         print(json.dumps(result))
 
@@ -789,6 +790,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=32, help="requests of the served stream")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sub-record of the default workload")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shape")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle's CPU leg (timing and error checks)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

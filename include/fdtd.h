@@ -153,6 +153,22 @@ typedef struct fdtd_gain_params {
 } fdtd_gain_params;
 int fdtd_set_gain(fdtd_grid* g, const fdtd_gain_params* p);
 
+/* Where the Bloch variables of a gain cell live (paper, Sec. "Sample and
+ * numerical approach": solved in the middle of the Yee cell).
+ * FDTD_COUPLING_CELL (default): the polarization P~_c of cell (i,j,k) sits on
+ * the node of E_c(i,j,k) and the cell's populations see its own three nodes.
+ * FDTD_COUPLING_CENTRED: P~ and the populations sit at the cell centre; the
+ * oscillator is driven by the average of the four E_c edges around the centre
+ * (beyond the grid 0, or the periodic wrap), each E_c node receives the
+ * average polarization current of the four cells that share it, and the
+ * populations see the centre average of (E^{n+1}+E^n)/2, so the exchange of
+ * energy between field and medium balances exactly.  Centred grids step their
+ * fields with the passive step kernel plus three centred kernels per step,
+ * and step alone (fdtd_batch_create refuses them).  Before the first step
+ * only (E_STATE after); E_INVAL for another value. */
+enum { FDTD_COUPLING_CELL = 0, FDTD_COUPLING_CENTRED = 1 };
+int fdtd_set_gain_coupling(fdtd_grid* g, int32_t coupling);
+
 /* Soft current source (paper, Secs. "Wide-band excitation" and "Dynamical
  * diffusion": single-cycle and 100 fs Gaussian pulses).  Waveform
  * g(n) = exp(-(t-t0)^2/(2 tau^2)) sin(2 pi f0 (t-t0)) at t = (n+1/2) dt,

@@ -467,6 +467,17 @@ int fdtd_set_step_limit(fdtd_grid* g, int64_t limit) {
   });
 }
 
+int fdtd_set_gain_coupling(fdtd_grid* g, int32_t coupling) {
+  return guarded([&]() -> int {
+    CHECK_GRID(g);
+    if (coupling != FDTD_COUPLING_CELL && coupling != FDTD_COUPLING_CENTRED)
+      return set_error(FDTD_E_INVAL, "coupling must be FDTD_COUPLING_CELL or FDTD_COUPLING_CENTRED");
+    if (G->finalized) return set_error(FDTD_E_STATE, "the coupling is only set before the first step");
+    G->coupling = coupling;
+    return FDTD_OK;
+  });
+}
+
 int fdtd_set_wait_limit(fdtd_grid* g, int64_t ns) {
   return guarded([&]() -> int {
     CHECK_GRID(g);
@@ -488,6 +499,8 @@ int fdtd_batch_create(fdtd_grid* const* grids, int32_t n, void* stream, fdtd_bat
     int prec = -1;
     for (int q = 0; q < n; ++q) {
       if (!grids[q] || !grids[q]->impl) return set_error(FDTD_E_INVAL, "null member %d", q);
+      if (grids[q]->impl->has_gain() && grids[q]->impl->coupling == FDTD_COUPLING_CENTRED)
+        return set_error(FDTD_E_INVAL, "member %d has the centred gain coupling: such grids step alone", q);
       GridBase* G = grids[q]->impl;
       if (!G->material_set) return set_error(FDTD_E_STATE, "member %d has no permittivity map", q);
       if (prec >= 0 && G->precision() != prec) return set_error(FDTD_E_INVAL, "members differ in precision");

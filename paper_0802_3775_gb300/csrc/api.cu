@@ -446,7 +446,7 @@ struct GridImpl final : GridBase {
     // plain-load kernel when an axis is periodic; by == 0: the chosen
     // kernel's default tile rows (paired 16, others 8)
     int kind = kernel_kind;
-    if (kind == 0) kind = (sizeof(T) == 4 && !sg.gain) ? 3 : 2;
+    if (kind == 0) kind = (sizeof(T) == 4 && !cell_gain()) ? 3 : 2;
     if (kind == 3 && sizeof(T) != 4) kind = 2;  // paired kernel: binary32 only
     use_pair = kind == 3 && !periodic && enc && (by == 0 || by == 8 || by == 16);
     if (kind == 3 && !use_pair) kind = 2;
@@ -465,8 +465,8 @@ struct GridImpl final : GridBase {
       int dev = 0, sms = 152;
       if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       cudaGetLastError();
-      const int wave = sms * (use_pair ? step_pair_blocks_per_sm(sg.gain != 0, tile_oy)
-                                       : step_blocks_per_sm<T>(use_tma, sg.gain != 0, bx, by_eff));
+      const int wave = sms * (use_pair ? step_pair_blocks_per_sm(cell_gain(), tile_oy)
+                                       : step_blocks_per_sm<T>(use_tma, cell_gain(), bx, by_eff));
       depth = 16;
       while (depth > 4 && (long long)tiles * ((desc.nz + depth - 1) / depth) < 2LL * wave) depth -= 2;
     }
@@ -612,7 +612,11 @@ struct GridImpl final : GridBase {
     sg.step_end = og.step_end = step_limit;
     sg.wait_ns = wait_ns;
     tables_dirty = false;
-    if ((e = cudaMemcpyAsync(d_sg, &sg, sizeof(sg), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return cuda_error(e, "upload grid");
+    // a grid with the centred coupling steps its fields with the passive
+    // step kernel (its record says: no gain) and runs the centred kernels after it
+    rec_up = sg;
+    if (!cell_gain()) rec_up.gain = 0;
+    if ((e = cudaMemcpyAsync(d_sg, &rec_up, sizeof(sg), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return cuda_error(e, "upload grid");
     if ((e = cudaMemcpyAsync(d_og, &og, sizeof(og), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return cuda_error(e, "upload grid");
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "upload grid");
     return FDTD_OK;
@@ -637,12 +641,14 @@ struct GridImpl final : GridBase {
         if (ev.first) cudaEventRecord(ev.first, stream);
         if (use_pair)
           e = launch_step_pair(reinterpret_cast<const StepGrid<float>*>(d_sg), d_tma, d_items, (int)items.size(), s,
-                               tile_oy, sg.gain != 0, grid_blocks, stream);
+                               tile_oy, cell_gain(), grid_blocks, stream);
         else if (use_tma)
-          e = launch_step_tma<T>(d_sg, d_tma, d_items, (int)items.size(), s, tile_oy, sg.gain != 0, grid_blocks, stream);
+          e = launch_step_tma<T>(d_sg, d_tma, d_items, (int)items.size(), s, tile_oy, cell_gain(), grid_blocks, stream);
         else
-          e = launch_step<T>(d_sg, d_items, (int)items.size(), s, bx, by_eff, sg.gain != 0, grid_blocks, stream);
+          e = launch_step<T>(d_sg, d_items, (int)items.size(), s, bx, by_eff, cell_gain(), grid_blocks, stream);
         if (e != cudaSuccess) return cuda_error(e, "step kernel");
+        if (centred_gain() && (e = launch_centred<T>(d_sg, ncell, s, stream)) != cudaSuccess)
+          return cuda_error(e, "centred coupling kernels");
         if (ev.second) cudaEventRecord(ev.second, stream);
         if (timer.used >= 4096) {
           if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "sync");
@@ -816,6 +822,10 @@ struct GridImpl final : GridBase {
   size_t step_record_size() const override { return sizeof(sg); }
   size_t obs_record_size() const override { return sizeof(og); }
   int has_gain() const override { return sg.gain; }
+  // gain coupled on each cell's own E nodes (inside the step kernels) / at the cell centre
+  bool cell_gain() const { return sg.gain != 0 && coupling == FDTD_COUPLING_CELL; }
+  bool centred_gain() const { return sg.gain != 0 && coupling == FDTD_COUPLING_CENTRED; }
+  StepGrid<T> rec_up{};  // the record as uploaded
   const void* tma_device() const override { return d_tma; }
   bool uses_tma() const override { return use_tma; }
   bool uses_pair() const override { return use_pair; }

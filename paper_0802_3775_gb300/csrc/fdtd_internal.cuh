@@ -166,6 +166,11 @@ cudaError_t launch_rasterize(uint8_t* mat, int nx, int ny, int nz, int px, const
                              const int* bin_list, int bin, int bnx, int bny, int bnz, const double* box,
                              cudaStream_t st);
 
+// Centred Bloch coupling of a gain grid: the polarization, current and
+// population kernels that follow the (passive) step kernel of step offset.
+template <typename T>
+cudaError_t launch_centred(const StepGrid<T>* g, long long ncell, int offset, cudaStream_t st);
+
 // Gain initialization: P slots zero, dN~ = init - N~eq in gain cells.
 template <typename T>
 cudaError_t launch_gain_init(const StepGrid<T>* g_host_copy, long long nslots, T d1, T d2, T d3, cudaStream_t st);

@@ -94,6 +94,7 @@ SIGNATURES = {
     "fdtd_kernel_time": [_P, _D, C.POINTER(C.c_int64)],
     "fdtd_set_step_limit": [_P, C.c_int64],
     "fdtd_set_wait_limit": [_P, C.c_int64],
+    "fdtd_set_gain_coupling": [_P, C.c_int32],
     "fdtd_batch_create": [C.POINTER(_P), C.c_int32, _P, C.POINTER(_P)],
     "fdtd_batch_destroy": [_P],
     "fdtd_batch_set_launch": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
@@ -251,6 +252,13 @@ class Grid:
         p = GainParams(g.n_total, g.fa_hat, g.dw_rel, g.tau32, g.tau21, g.tau10, g.pump, g.kappa, g.noise_amp,
                        0 if g.init == "steady" else 1)
         check(self._lib.fdtd_set_gain(self.h, C.byref(p)))
+        coupling = getattr(g, "coupling", "cell")
+        if coupling != "cell":
+            self.set_gain_coupling(coupling)
+
+    def set_gain_coupling(self, coupling):
+        """"cell" (P on each cell's own E nodes) or "centred" (P at the cell centre)."""
+        check(self._lib.fdtd_set_gain_coupling(self.h, {"cell": 0, "centred": 1}[coupling]))
 
     def add_source(self, s):
         d = SourceDesc(0 if s.kind == "point" else 1, s.comp, *[int(v) for v in s.pos], s.axis, s.index,
