@@ -206,6 +206,8 @@ def rank_max(x: float, dist, device: str = "cuda") -> float:
 def configure_grid(args, g):
     if args.kernel != "auto":
         g.set_kernel(args.kernel)
+    if args.order:
+        g.set_item_order(args.order)
     if args.by or args.zdepth:
         g.set_launch(32, args.by, args.zdepth, 0)
 
@@ -238,7 +240,7 @@ def timed_workload(args, specs, world, dist, steps, warmup, sample_clocks=True):
     else:
         stepper = grids[0]
     tune = None
-    if not args.no_autotune and args.kernel == "auto" and not args.by and not args.zdepth:
+    if not args.no_autotune and args.kernel == "auto" and not args.by and not args.zdepth and not args.order:
         # launch shape picked by timing the candidates on this workload (state restored)
         tune = stepper.autotune(trial_steps=10 if len(grids) == 1 else 4)
     stepper.step(warmup)
@@ -295,7 +297,8 @@ def timed_workload(args, specs, world, dist, steps, warmup, sample_clocks=True):
     achieved = bytes_step / (per_launch_ms * 1e-3) / 1e9
     rec = {"value": round(value, 1), "ms_per_step": round(ms_max / steps, 5), "cells": cells,
            "launch_shape": ({"kernel": tune["kernel"], "by": tune["by"], "zdepth": tune["zdepth"],
-                             "grid_blocks": tune["grid_blocks"], "autotuned_over": tune["candidates"]}
+                             "grid_blocks": tune["grid_blocks"], "order": ["costliest", "z"][tune["order"]],
+                             "autotuned_over": tune["candidates"]}
                             if tune else "library default"),
            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(achieved / peak, 4), "traffic": None,
@@ -326,8 +329,9 @@ def run_gpu(args, rank, world, dist):
         # DRAM bytes of one launch from an ncu capture of this workload, when
         # it was taken on the kernel and launch shape this run uses
         zd = rec["tune"]["zdepth"] if rec["tune"] else args.zdepth
+        od = ["costliest", "z"][rec["tune"]["order"]] if rec["tune"] else (args.order or "costliest")
         if rec["n_kernels"] == 1 and tr.get("kernel") == rec["kname"] and tr.get("tile") == rec["tiles"][0] \
-                and tr.get("zdepth") == zd:
+                and tr.get("zdepth") == zd and tr.get("order", "costliest") == od:
             roof["traffic"] = tr.get("dram_bytes_per_launch")
 
     batch_grids = []
@@ -786,6 +790,8 @@ def main():
                     help="step kernel (default: the library's automatic choice)")
     ap.add_argument("--by", type=int, default=0, help="tile rows of the step kernel (0: library default)")
     ap.add_argument("--zdepth", type=int, default=0, help="planes per work item (0: library default)")
+    ap.add_argument("--order", default="", choices=["", "costliest", "z"],
+                    help="work-item order of the single-node kernels (default: the library's)")
     ap.add_argument("--no-serve", action="store_true", help="skip the served request stream")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests of the served stream")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sub-record of the default workload")

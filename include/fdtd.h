@@ -220,6 +220,17 @@ int fdtd_step_n(fdtd_grid* g, int64_t n);
  * depend on the shape.  Needs bx, by >= 2, bx*by a multiple of 32, <= 512. */
 int fdtd_set_launch(fdtd_grid* g, int32_t bx, int32_t by, int32_t zdepth, int32_t grid_blocks);
 
+/* Order of the single-node kernels' work items within a launch:
+ * FDTD_ORDER_COSTLIEST (default) issues the items whose tiles or planes
+ * cross absorbing slabs first (items of equal cost in z order);
+ * FDTD_ORDER_Z issues every item in z order (z-range, then row, then column
+ * of tiles), so neighbouring tiles run together and the halo rows and
+ * columns they share are read from DRAM once.  The paired kernel keeps its
+ * own cost-bucketed z order.  Results do not depend on the order.  E_INVAL
+ * for another value. */
+enum { FDTD_ORDER_COSTLIEST = 0, FDTD_ORDER_Z = 1 };
+int fdtd_set_item_order(fdtd_grid* g, int32_t order);
+
 /* Step-kernel variant: 0 = automatic (the paired kernel for binary32 and
  * the TMA-staged kernel for binary64 grids when no axis is periodic, else the
  * plain-load kernel), 1 = plain-load kernel (blocks of bx x by threads own
@@ -255,6 +266,7 @@ typedef struct fdtd_tune_result {
   int32_t grid_blocks;  /* persistent blocks (0 = the kernel's default)     */
   int32_t candidates;   /* shapes timed                                     */
   double ms_per_step;   /* time of one step with the chosen shape           */
+  int32_t order;        /* item order (fdtd_set_item_order)                 */
 } fdtd_tune_result;
 int fdtd_autotune(fdtd_grid* g, int32_t trial_steps, fdtd_tune_result* out);
 

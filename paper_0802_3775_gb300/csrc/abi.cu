@@ -467,6 +467,21 @@ int fdtd_set_step_limit(fdtd_grid* g, int64_t limit) {
   });
 }
 
+int fdtd_set_item_order(fdtd_grid* g, int32_t order) {
+  return guarded([&]() -> int {
+    CHECK_GRID(g);
+    if (order != FDTD_ORDER_COSTLIEST && order != FDTD_ORDER_Z)
+      return set_error(FDTD_E_INVAL, "order must be FDTD_ORDER_COSTLIEST or FDTD_ORDER_Z");
+    G->item_order = order;
+    if (G->finalized) {
+      cudaError_t e = cudaStreamSynchronize(G->stream);
+      if (e != cudaSuccess) return fdtd::cuda_error(e, "sync");
+      return G->replan();
+    }
+    return FDTD_OK;
+  });
+}
+
 int fdtd_set_gain_coupling(fdtd_grid* g, int32_t coupling) {
   return guarded([&]() -> int {
     CHECK_GRID(g);

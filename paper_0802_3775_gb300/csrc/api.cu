@@ -504,8 +504,10 @@ struct GridImpl final : GridBase {
         return a.second.y < b.second.y;
       });
     } else {
-      // Costliest items first over the whole launch (measured faster for the
-      // single-node kernels); items of equal cost in z order.
+      // Items generated in z order (z-range, row, column); by default the
+      // costliest go first over the whole launch (items of equal cost stay in
+      // z order), with FDTD_ORDER_Z all stay in z order, so the halo rows and
+      // columns neighbouring tiles share are read while they sit in L2.
       for (int z0 = 0; z0 < desc.nz; z0 += depth) {
         const int z1 = std::min(desc.nz, z0 + depth);
         for (int ty = 0; ty < tny; ++ty)
@@ -514,9 +516,10 @@ struct GridImpl final : GridBase {
             work.push_back({item_cost(it, ox, oy), it});
           }
       }
-      std::stable_sort(work.begin(), work.end(), [](const std::pair<double, int4>& a, const std::pair<double, int4>& b) {
-        return a.first > b.first;
-      });
+      if (item_order != FDTD_ORDER_Z)
+        std::stable_sort(work.begin(), work.end(), [](const std::pair<double, int4>& a, const std::pair<double, int4>& b) {
+          return a.first > b.first;
+        });
     }
     for (auto& w : work) items.push_back(w.second);
     oitems.clear();

@@ -23,7 +23,7 @@ namespace fdtd {
 namespace {
 
 struct Candidate {
-  int kind, bx, by, zdepth, grid_blocks;
+  int kind, bx, by, zdepth, grid_blocks, order = FDTD_ORDER_COSTLIEST;
 };
 
 // Device copy of a grid's evolving state (fields, CPML and gain memory,
@@ -33,7 +33,7 @@ struct Snapshot {
   std::vector<std::pair<void*, size_t>> blobs;
   std::vector<void*> saved;
   long long steps = 0, limit = 0;
-  int kind = 0, bx = 0, by = 0, zdepth = 0, grid_blocks = 0;
+  int kind = 0, bx = 0, by = 0, zdepth = 0, grid_blocks = 0, order = 0;
 
   int take(GridBase* grid) {
     g = grid;
@@ -45,6 +45,7 @@ struct Snapshot {
     by = g->by;
     zdepth = g->zdepth;
     grid_blocks = g->grid_blocks;
+    order = g->item_order;
     cudaError_t e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_error(e, "sync");
     for (auto& b : blobs) {
@@ -76,6 +77,7 @@ struct Snapshot {
     g->by = by;
     g->zdepth = zdepth;
     g->grid_blocks = grid_blocks;
+    g->item_order = order;
   }
   ~Snapshot() {
     if (g) cudaStreamSynchronize(g->stream);
@@ -94,6 +96,14 @@ std::vector<Candidate> grid_candidates(const GridBase* g) {
   } else {
     c = {{2, 32, 8, 0, 0}, {2, 32, 4, 0, 0}, {2, 32, 8, 8, 0}, {2, 32, 4, 16, 0}, {2, 32, 8, 24, 0}};
   }
+  // the single-node kernels' items also in plain z order
+  const size_t n0 = c.size();
+  for (size_t q = 0; q < n0; ++q)
+    if (c[q].kind == 2) {
+      Candidate z = c[q];
+      z.order = FDTD_ORDER_Z;
+      c.push_back(z);
+    }
   return c;
 }
 
@@ -150,6 +160,7 @@ int fdtd_autotune(fdtd_grid* g, int32_t trial_steps, fdtd_tune_result* out) {
       G->by = c.by;
       G->zdepth = c.zdepth;
       G->grid_blocks = c.grid_blocks;
+      G->item_order = c.order;
       if ((r = G->replan()) != FDTD_OK) break;
       double ms = 0.0;
       r = time_steps(G->stream, trial_steps, [&](long long n) { return G->step(n); }, &ms);
@@ -174,6 +185,7 @@ int fdtd_autotune(fdtd_grid* g, int32_t trial_steps, fdtd_tune_result* out) {
     G->by = c.by;
     G->zdepth = c.zdepth;
     G->grid_blocks = c.grid_blocks;
+    G->item_order = c.order;
     if ((r = snap.restore()) != FDTD_OK) return r;
     if ((r = G->replan()) != FDTD_OK) return r;
     if (out) {
@@ -184,6 +196,7 @@ int fdtd_autotune(fdtd_grid* g, int32_t trial_steps, fdtd_tune_result* out) {
       out->grid_blocks = c.grid_blocks;
       out->ms_per_step = best_ms;
       out->candidates = (int32_t)cands.size();
+      out->order = c.order;
     }
     return FDTD_OK;
   } catch (...) {
@@ -275,6 +288,7 @@ int fdtd_batch_autotune(fdtd_batch* b, int32_t trial_steps, fdtd_tune_result* ou
       out->grid_blocks = c.grid_blocks;
       out->ms_per_step = best_ms;
       out->candidates = (int32_t)cands.size();
+      out->order = FDTD_ORDER_COSTLIEST;
     }
     return FDTD_OK;
   } catch (...) {

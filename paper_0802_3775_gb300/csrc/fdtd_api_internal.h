@@ -140,6 +140,7 @@ struct GridBase {
   long long step_limit = 0x7fffffffffffffffLL;  // no update n >= step_limit
   long long wait_ns = 2000000000LL;              // limit of the TMA step kernels' bounded waits
   int coupling = 0;                              // FDTD_COUPLING_CELL or FDTD_COUPLING_CENTRED
+  int item_order = 0;                            // FDTD_ORDER_COSTLIEST or FDTD_ORDER_Z
   bool tables_dirty = false;                     // device records stale (stepped by a batch)
 
   virtual ~GridBase() { mem.release_all(); }

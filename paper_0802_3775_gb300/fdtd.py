@@ -60,7 +60,8 @@ class Allocator(C.Structure):
 
 class TuneResult(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("bx", C.c_int32), ("by", C.c_int32), ("zdepth", C.c_int32),
-                ("grid_blocks", C.c_int32), ("candidates", C.c_int32), ("ms_per_step", C.c_double)]
+                ("grid_blocks", C.c_int32), ("candidates", C.c_int32), ("ms_per_step", C.c_double),
+                ("order", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -95,6 +96,7 @@ SIGNATURES = {
     "fdtd_set_step_limit": [_P, C.c_int64],
     "fdtd_set_wait_limit": [_P, C.c_int64],
     "fdtd_set_gain_coupling": [_P, C.c_int32],
+    "fdtd_set_item_order": [_P, C.c_int32],
     "fdtd_batch_create": [C.POINTER(_P), C.c_int32, _P, C.POINTER(_P)],
     "fdtd_batch_destroy": [_P],
     "fdtd_batch_set_launch": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
@@ -282,6 +284,10 @@ class Grid:
 
     def set_launch(self, bx=32, by=8, zdepth=0, grid_blocks=0):
         check(self._lib.fdtd_set_launch(self.h, int(bx), int(by), int(zdepth), int(grid_blocks)))
+
+    def set_item_order(self, order):
+        """"costliest" (slab items first) or "z" (plain z order) for the single-node kernels."""
+        check(self._lib.fdtd_set_item_order(self.h, {"costliest": 0, "z": 1}[order]))
 
     def set_kernel(self, kind):
         """0 automatic, 1 plain-load step kernel, 2 TMA-staged step kernel,
