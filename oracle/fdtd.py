@@ -50,6 +50,19 @@ Readings where the paper is silent (also listed in the design notes):
     so the field-medium exchange balances exactly (A^T is A's adjoint).
   * coef32: round every update coefficient (S, S/eps_r, 1/eps_r, 1/kappa, b, c,
     a1, a2) to binary32, which defines the discrete problem an FP32 run solves.
+  * absorber="upml" (the paper's uniaxial PML): the same sigma' = sigma dt/eps0
+    and kappa grading as the CPML, no alpha, evaluated at each field node's own
+    position on every axis (half-integer along the component's axis for E,
+    integer for H, and the other way round on the other axes).  Nodes where a
+    grading is non-zero keep an auxiliary field: for E_c with (d1, d2) the
+    other axes in cyclic order,
+      D~^{n+1} = [(k1 - s1/2) D~^n + S curl_b H~] / (k1 + s1/2)     (axis d1),
+      E^{n+1} = [(k2 - s2/2) E^n + ((kc + sc/2) D~^{n+1} - (kc - sc/2) D~^n)/eps_r]
+                / (k2 + s2/2)                                    (axes c, d2),
+    and H~_c the same with B~, -S curl_f E and eps_r = 1 (the uniaxial tensor
+    diag(s_y s_z/s_x, s_z s_x/s_y, s_x s_y/s_z) split into two first-order
+    steps); every other node takes the plain Yee update.  Each coefficient is
+    rounded like the others in coef32 mode.
 """
 from __future__ import annotations
 
@@ -96,7 +109,10 @@ class Oracle:
     def __init__(self, shape, res, *, a=480e-9, courant=0.5, npml=(0, 0, 0, 0, 0, 0),
                  periodic=(False, False, False), eps=(1.0, 1.0, 1.0), cpml_m=3.0,
                  cpml_sigma_factor=0.8, cpml_kappa_max=1.0, cpml_alpha_max=0.05, cpml_f_hat=0.80,
-                 coef32=False, seed=0):
+                 coef32=False, seed=0, absorber="cpml"):
+        if absorber not in ("cpml", "upml"):
+            raise ValueError(absorber)
+        self.upml = absorber == "upml"
         self.shape = tuple(int(s) for s in shape)
         nx, ny, nz = self.shape
         self.res = float(res)
@@ -126,6 +142,10 @@ class Oracle:
                 for d in ((c + 1) % 3, (c + 2) % 3):
                     if self._has_pml(d):
                         self.psi[kind][(c, d)] = np.zeros((nx, ny, nz))
+        if self.upml:
+            self.D = np.zeros((3, nx, ny, nz))
+            self.B = np.zeros((3, nx, ny, nz))
+            self._upml_h = self._upml_coefficients(True)
         self.set_material(np.full((nz, ny, nx), 0b010101, dtype=np.uint8))
         self.gain = None
         self.src = np.zeros((3, nx, ny, nz))
@@ -145,7 +165,7 @@ class Oracle:
                 periodic=spec.periodic, eps=spec.eps, cpml_m=spec.cpml_m,
                 cpml_sigma_factor=spec.cpml_sigma_factor, cpml_kappa_max=spec.cpml_kappa_max,
                 cpml_alpha_max=spec.cpml_alpha_max, cpml_f_hat=spec.cpml_f_hat, coef32=coef32,
-                seed=spec.seed)
+                seed=spec.seed, absorber=getattr(spec, "absorber", "cpml"))
         if spec.spheres is not None:
             o.rasterize(spec.spheres, spec.box_lo, spec.box_hi)
         if spec.gain is not None:
@@ -165,7 +185,52 @@ class Oracle:
         return o
 
     def _has_pml(self, d):
-        return self.npml[2 * d] > 0 or self.npml[2 * d + 1] > 0
+        """Axis d has CPML memory (a slab, and the absorber is the CPML)."""
+        return not self.upml and (self.npml[2 * d] > 0 or self.npml[2 * d + 1] > 0)
+
+    def _grading(self, d, half):
+        """(sigma dt/eps0, kappa) at the integer (or half-integer) nodes of axis d,
+        shaped to broadcast along d; the CPML's grading without alpha."""
+        n = self.shape[d]
+        L0, L1 = self.npml[2 * d], self.npml[2 * d + 1]
+        x = np.arange(n, dtype=np.float64) + (0.5 if half else 0.0)
+        rho = np.zeros(n)
+        if L0 > 0:
+            lo = x < L0
+            rho[lo] = (L0 - x[lo]) / L0
+        if L1 > 0:
+            hi = x > n - L1
+            rho[hi] = (x[hi] - (n - L1)) / L1
+        p = self._cpml
+        sig_max = p["factor"] * (p["m"] + 1.0) * self.S / math.sqrt(self.eps[0])
+        sig = sig_max * rho ** p["m"]
+        kap = 1.0 + (p["kmax"] - 1.0) * rho ** p["m"]
+        shp = [1, 1, 1]
+        shp[d] = n
+        return sig.reshape(shp), kap.reshape(shp), (rho > 0).reshape(shp)
+
+    def _upml_coefficients(self, h_side, eps_nodes=None):
+        """Per-component UPML coefficients (u1, u2, v1, v2, v3) and node mask:
+        aux^{n+1} = u1 aux^n + u2 (S curl), field^{n+1} = v1 field^n + v2 aux^{n+1} - v3 aux^n."""
+        out = []
+        for c in range(3):
+            d1, d2 = (c + 1) % 3, (c + 2) % 3
+            # E_c is half-integer along c, integer elsewhere; H_c the other way round
+            g = [self._grading(d, (d == c) != h_side) for d in range(3)]
+            s1, k1, m1 = g[d1]
+            s2, k2, m2 = g[d2]
+            sc, kc, mc = g[c]
+            er = 1.0 if h_side else eps_nodes[c]
+            den2 = k2 + 0.5 * s2
+            u1 = (k1 - 0.5 * s1) / (k1 + 0.5 * s1)
+            u2 = 1.0 / (k1 + 0.5 * s1)
+            v1 = (k2 - 0.5 * s2) / den2
+            v2 = (kc + 0.5 * sc) / (er * den2)
+            v3 = (kc - 0.5 * sc) / (er * den2)
+            shape = self.shape
+            mask = np.broadcast_to(m1 | m2 | mc, shape)
+            out.append(tuple(self.R(np.broadcast_to(v, shape)) for v in (u1, u2, v1, v2, v3)) + (mask,))
+        return out
 
     def _profile(self, d, half):
         """(1/kappa, b, c) at the nodes of axis d, shaped to broadcast along d."""
@@ -206,6 +271,8 @@ class Oracle:
         self.cE = self.R(self.S / self.eps_E)
         self.cP = self.R(1.0 / self.eps_E)
         self.gain_cell = ((m >> 6) & 1).astype(bool)
+        if self.upml:
+            self._upml_e = self._upml_coefficients(False, self.eps_E)
 
     def rasterize(self, spheres, box_lo, box_hi):
         self.set_material(_rasterize(self.shape, spheres, box_lo, box_hi))
@@ -378,7 +445,16 @@ class Oracle:
         E_n = self.E
         H_old = self.H
         # 1. magnetic half step
-        H_new = H_old - self.cH * self.curl_E(E_n)
+        if self.upml:
+            cE_n = self.curl_E(E_n)
+            H_new = H_old - self.cH * cE_n
+            for c in range(3):
+                u1, u2, v1, v2, v3, mask = self._upml_h[c]
+                B_new = u1 * self.B[c] - u2 * (self.cH * cE_n[c])
+                H_new[c] = np.where(mask, v1 * H_old[c] + v2 * B_new - v3 * self.B[c], H_new[c])
+                self.B[c] = np.where(mask, B_new, self.B[c])
+        else:
+            H_new = H_old - self.cH * self.curl_E(E_n)
         # 2. flux through the planes at time n
         flux_vals = [self._flux(f, E_n, 0.5 * (H_old + H_new)) for f in self.fluxes]
         # 3. polarization
@@ -403,7 +479,14 @@ class Oracle:
         src = np.zeros_like(E_n)
         for s in self.sources:
             src[s["comp"]] += s["w"] * float(waveform(n, s["f0_hat"], s["rel_bw"], self.S, self.res, s["t0_steps"]))
-        E_new = E_n + self.cE * self.curl_H(H_new) - self.cP * ((dP_nodes if g is not None else dP) + src)
+        cH_new = self.curl_H(H_new)
+        E_new = E_n + self.cE * cH_new - self.cP * ((dP_nodes if g is not None else dP) + src)
+        if self.upml:
+            for c in range(3):
+                u1, u2, v1, v2, v3, mask = self._upml_e[c]
+                D_new = u1 * self.D[c] + u2 * (self.cH * cH_new[c])
+                E_new[c] = np.where(mask, v1 * E_n[c] + v2 * D_new - v3 * self.D[c], E_new[c])
+                self.D[c] = np.where(mask, D_new, self.D[c])
         self._pec(E_new)
         # 5. populations
         if g is not None:

@@ -197,6 +197,7 @@ class RunSpec:
     cpml_kappa_max: float = 1.0
     cpml_alpha_max: float = 0.05
     cpml_f_hat: float = 0.80
+    absorber: str = "cpml"                  # "cpml" or "upml" (same grading, no alpha)
     precision: str = "f32"
     spheres: np.ndarray | None = None
     box_lo: tuple = (0, 0, 0)
