@@ -134,8 +134,9 @@ class Oracle:
         self.n = 0
         self._cpml = dict(m=cpml_m, factor=cpml_sigma_factor, kmax=cpml_kappa_max,
                           amax=cpml_alpha_max, fhat=cpml_f_hat)
-        self.prof = {"E": [self._profile(d, False) for d in range(3)],
-                     "H": [self._profile(d, True) for d in range(3)]}
+        # CPML grading coefficients (the UPML uses its own, built below)
+        self.prof = None if self.upml else {"E": [self._profile(d, False) for d in range(3)],
+                                              "H": [self._profile(d, True) for d in range(3)]}
         self.psi = {"E": {}, "H": {}}
         for kind in ("E", "H"):
             for c in range(3):
