@@ -217,7 +217,7 @@ def configure_batch(args, b):
         b.set_launch(args.kernel, args.by, args.zdepth, 0)
 
 
-KERNEL_NAMES = {1: "k_step", 2: "k_step_tma", 3: "k_step_pair"}
+KERNEL_NAMES = {1: "k_step", 2: "k_step_tma", 3: "k_step_pair", 4: "k_upml_h + k_upml_e"}
 
 
 def timed_workload(args, specs, world, dist, steps, warmup, sample_clocks=True):

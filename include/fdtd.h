@@ -229,6 +229,22 @@ int fdtd_set_launch(fdtd_grid* g, int32_t bx, int32_t by, int32_t zdepth, int32_
  * own cost-bucketed z order.  Results do not depend on the order.  E_INVAL
  * for another value. */
 enum { FDTD_ORDER_COSTLIEST = 0, FDTD_ORDER_Z = 1 };
+
+/* Absorbing layer of the grid's slabs (paper, Sec. "Sample and numerical
+ * approach": a uniaxial PML).  FDTD_ABSORBER_CPML (default): the convolutional
+ * PML of the descriptor's grading, inside the fused step kernels.
+ * FDTD_ABSORBER_UPML: the uniaxial PML on the same grading of sigma and
+ * kappa (alpha unused), at each field node's own position on every axis; a
+ * node where any axis is graded steps through an auxiliary D~ (E) or B~ (H~):
+ * D~' = [(k1 - s1/2) D~ + S curl H~]/(k1 + s1/2) on the axis d1 after the
+ * component c, E' = [(k2 - s2/2) E + ((kc + sc/2) D~' - (kc - sc/2) D~)/eps_r]
+ * /(k2 + s2/2) on c and the axis d2 after d1 (s = sigma dt/eps0), and H~
+ * likewise with -S curl E.  Sources act outside the layer only.  UPML grids
+ * step with two launches per step (H~, then E, one thread per node;
+ * fdtd_kernel_in_use reports kind 4), passive grids only (E_INVAL with a
+ * gain medium).  Before the first step only (E_STATE after). */
+enum { FDTD_ABSORBER_CPML = 0, FDTD_ABSORBER_UPML = 1 };
+int fdtd_set_absorber(fdtd_grid* g, int32_t absorber);
 int fdtd_set_item_order(fdtd_grid* g, int32_t order);
 
 /* Step-kernel variant: 0 = automatic (the paired kernel for binary32 and

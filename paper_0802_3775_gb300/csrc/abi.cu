@@ -216,6 +216,8 @@ int fdtd_get_material(fdtd_grid* g, uint8_t* mat) {
 int fdtd_set_gain(fdtd_grid* g, const fdtd_gain_params* p) {
   return guarded([&]() -> int {
     CHECK_GRID(g);
+    if (G->absorber == FDTD_ABSORBER_UPML)
+      return set_error(FDTD_E_INVAL, "the uniaxial PML runs passive grids (no gain medium)");
     BEFORE_FIRST_STEP(G, "fdtd_set_gain");
     if (!p) return set_error(FDTD_E_INVAL, "null gain parameters");
     if (!G->material_set) return set_error(FDTD_E_STATE, "set the material before the gain medium");
@@ -325,7 +327,7 @@ int fdtd_kernel_in_use(fdtd_grid* g, int32_t* kind, int32_t* rows) {
     CHECK_GRID(g);
     if (!kind || !rows) return set_error(FDTD_E_INVAL, "null output");
     if (!G->finalized) return set_error(FDTD_E_STATE, "the launch plan is made at the first step");
-    *kind = G->uses_pair() ? 3 : (G->uses_tma() ? 2 : 1);
+    *kind = G->kernel_in_use_kind();
     *rows = G->tile_rows();
     return FDTD_OK;
   });
@@ -463,6 +465,19 @@ int fdtd_set_step_limit(fdtd_grid* g, int64_t limit) {
     if (limit < 0) return set_error(FDTD_E_INVAL, "negative step limit");
     G->step_limit = limit;
     G->tables_dirty = true;
+    return FDTD_OK;
+  });
+}
+
+int fdtd_set_absorber(fdtd_grid* g, int32_t absorber) {
+  return guarded([&]() -> int {
+    CHECK_GRID(g);
+    if (absorber != FDTD_ABSORBER_CPML && absorber != FDTD_ABSORBER_UPML)
+      return set_error(FDTD_E_INVAL, "absorber must be FDTD_ABSORBER_CPML or FDTD_ABSORBER_UPML");
+    if (G->finalized) return set_error(FDTD_E_STATE, "the absorber is only set before the first step");
+    if (absorber == FDTD_ABSORBER_UPML && G->has_gain())
+      return set_error(FDTD_E_INVAL, "the uniaxial PML runs passive grids (no gain medium)");
+    G->absorber = absorber;
     return FDTD_OK;
   });
 }

@@ -174,6 +174,9 @@ struct GridImpl final : GridBase {
   T* d_psi = nullptr;
   size_t psi_words = 0;
   T* d_prof = nullptr;
+  T* d_upml = nullptr;     // uniaxial PML: auxiliary fields (6 arrays) and grading tables
+  size_t upml_aux_words = 0;
+  UpmlDev<T> upml{};
   TmaGrid* d_tma = nullptr;
   bool use_tma = false;
   bool use_pair = false;  // paired binary32 kernel (TMA staging, tiles of 32 x tile_oy)
@@ -447,6 +450,7 @@ struct GridImpl final : GridBase {
     // kernel's default tile rows (paired 16, others 8)
     int kind = kernel_kind;
     if (kind == 0) kind = (sizeof(T) == 4 && !cell_gain()) ? 3 : 2;
+    if (upml_grid()) kind = 1;  // its own H and E launches; nothing staged by TMA
     if (kind == 3 && sizeof(T) != 4) kind = 2;  // paired kernel: binary32 only
     use_pair = kind == 3 && !periodic && enc && (by == 0 || by == 8 || by == 16);
     if (kind == 3 && !use_pair) kind = 2;
@@ -556,8 +560,65 @@ struct GridImpl final : GridBase {
     return FDTD_OK;
   }
 
+  bool upml_grid() const { return absorber == FDTD_ABSORBER_UPML; }
+
+  // Uniaxial PML: the grading of every axis at integer and half-integer
+  // nodes (the CPML's sigma dt/eps0 and kappa, no alpha) as the four factors
+  // the update takes, and the auxiliary D~ and B~ arrays (zero).
+  int prepare_upml() {
+    if (d_upml) return FDTD_OK;
+    const int n3[3] = {desc.nx, desc.ny, desc.nz};
+    const size_t tab = (size_t)8 * (desc.nx + desc.ny + desc.nz);
+    upml_aux_words = (size_t)6 * (size_t)nstore;
+    d_upml = (T*)mem.get(sizeof(T) * (upml_aux_words + tab));
+    if (!d_upml) return set_error(FDTD_E_NOMEM, "device allocation failed (UPML auxiliary fields)");
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(d_upml, 0, sizeof(T) * upml_aux_words, stream)) != cudaSuccess)
+      return cuda_error(e, "memset UPML fields");
+    for (int c = 0; c < 3; ++c) {
+      upml.D[c] = d_upml + (size_t)c * nstore;
+      upml.B[c] = d_upml + (size_t)(3 + c) * nstore;
+    }
+    for (int q = 0; q < 6; ++q) upml.L[q] = desc.npml[q];
+    std::vector<T> h(tab);
+    T* base = d_upml + upml_aux_words;
+    size_t off = 0;
+    const double sig_max = desc.cpml_sigma_factor * (desc.cpml_m + 1.0) * S / std::sqrt(desc.eps[0]);
+    for (int d = 0; d < 3; ++d) {
+      const int n = n3[d], L0 = desc.npml[2 * d], L1 = desc.npml[2 * d + 1];
+      for (int hf = 0; hf < 2; ++hf)
+        for (int qq = 0; qq < 4; ++qq) {
+          upml.q[d][hf][qq] = base + off;
+          for (int v = 0; v < n; ++v) {
+            const double x = v + (hf ? 0.5 : 0.0);
+            double rho = 0.0;
+            if (L0 > 0 && x < L0) rho = (L0 - x) / L0;
+            if (L1 > 0 && x > n - L1) rho = (x - (n - L1)) / L1;
+            const double rm = std::pow(rho, desc.cpml_m);
+            const double s = sig_max * rm, k = 1.0 + (desc.cpml_kappa_max - 1.0) * rm;
+            const double val = qq == 0 ? (k - 0.5 * s) / (k + 0.5 * s)
+                             : qq == 1 ? 1.0 / (k + 0.5 * s)
+                             : qq == 2 ? k + 0.5 * s : k - 0.5 * s;
+            h[off + v] = (T)val;
+          }
+          off += n;
+        }
+    }
+    if ((e = cudaMemcpyAsync(base, h.data(), sizeof(T) * off, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+      return cuda_error(e, "upload UPML grading");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "UPML set-up");
+    return FDTD_OK;
+  }
+
+  int kernel_in_use_kind() const override { return upml_grid() ? 4 : (use_pair ? 3 : (use_tma ? 2 : 1)); }
+
   int finalize() override {
     cudaError_t e;
+    if (upml_grid()) {
+      if (sg.gain) return set_error(FDTD_E_INVAL, "the uniaxial PML runs passive grids (no gain medium)");
+      const int r = prepare_upml();
+      if (r != FDTD_OK) return r;
+    }
     // recorders
     const long long cap = desc.record_capacity;
     og.cap = cap;
@@ -619,6 +680,11 @@ struct GridImpl final : GridBase {
     // step kernel (its record says: no gain) and runs the centred kernels after it
     rec_up = sg;
     if (!cell_gain()) rec_up.gain = 0;
+    if (upml_grid())  // no CPML memory: the UPML launches grade the slabs themselves
+      for (int d = 0; d < 3; ++d) {
+        rec_up.Sd[d] = 0;
+        rec_up.L[2 * d] = rec_up.L[2 * d + 1] = 0;
+      }
     if ((e = cudaMemcpyAsync(d_sg, &rec_up, sizeof(sg), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return cuda_error(e, "upload grid");
     if ((e = cudaMemcpyAsync(d_og, &og, sizeof(og), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return cuda_error(e, "upload grid");
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_error(e, "upload grid");
@@ -642,7 +708,9 @@ struct GridImpl final : GridBase {
         if (beside && (e = obs.before_step(stream, s)) != cudaSuccess) return cuda_error(e, "order");
         const auto ev = timer.next();
         if (ev.first) cudaEventRecord(ev.first, stream);
-        if (use_pair)
+        if (upml_grid())
+          e = launch_upml<T>(d_sg, upml, ncell, s, stream);
+        else if (use_pair)
           e = launch_step_pair(reinterpret_cast<const StepGrid<float>*>(d_sg), d_tma, d_items, (int)items.size(), s,
                                tile_oy, cell_gain(), grid_blocks, stream);
         else if (use_tma)
@@ -795,6 +863,7 @@ struct GridImpl final : GridBase {
     v.push_back({d_F, sizeof(T) * 6 * kFieldSets * (size_t)nstore});
     v.push_back({(void*)d_mat, (size_t)nstore});
     if (d_psi) v.push_back({d_psi, sizeof(T) * psi_words});
+    if (d_upml) v.push_back({d_upml, sizeof(T) * upml_aux_words});
     if (d_gain) v.push_back({d_gain, sizeof(T) * gain_words});
     if (og.probe_ring) v.push_back({og.probe_ring, sizeof(T) * (size_t)og.cap * og.nprobe * 3});
     if (og.flux_ring) v.push_back({og.flux_ring, sizeof(double) * (size_t)og.cap * og.nflux});

@@ -88,6 +88,7 @@ struct Snapshot {
 std::vector<Candidate> grid_candidates(const GridBase* g) {
   const fdtd_grid_desc& d = g->desc;
   std::vector<Candidate> c;
+  if (g->absorber == FDTD_ABSORBER_UPML) return {{1, 32, 8, 0, 0}};  // one launch shape: the UPML launches
   if (d.periodic[0] || d.periodic[1] || d.periodic[2]) {
     c = {{1, 32, 8, 0, 0}, {1, 32, 4, 0, 0}, {1, 64, 4, 0, 0}, {1, 32, 16, 0, 0}};
   } else if (g->precision() == FDTD_FP32) {

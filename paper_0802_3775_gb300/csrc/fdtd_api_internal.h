@@ -141,6 +141,8 @@ struct GridBase {
   long long wait_ns = 2000000000LL;              // limit of the TMA step kernels' bounded waits
   int coupling = 0;                              // FDTD_COUPLING_CELL or FDTD_COUPLING_CENTRED
   int item_order = 0;                            // FDTD_ORDER_COSTLIEST or FDTD_ORDER_Z
+  int absorber = 0;                              // FDTD_ABSORBER_CPML or FDTD_ABSORBER_UPML
+  virtual int kernel_in_use_kind() const { return 0; }
   bool tables_dirty = false;                     // device records stale (stepped by a batch)
 
   virtual ~GridBase() { mem.release_all(); }

@@ -166,6 +166,19 @@ cudaError_t launch_rasterize(uint8_t* mat, int nx, int ny, int nz, int px, const
                              const int* bin_list, int bin, int bnx, int bny, int bnz, const double* box,
                              cudaStream_t st);
 
+// Uniaxial PML of a passive grid: grading tables and auxiliary fields.
+template <typename T>
+struct UpmlDev {
+  const T* q[3][2][4];  // [axis][0 integer node, 1 half-integer node][(k - s/2)/(k + s/2), 1/(k + s/2), k + s/2, k - s/2]
+  T* D[3];              // auxiliary D~ of the E nodes (read and written at graded nodes only)
+  T* B[3];              // auxiliary B~ of the H~ nodes
+  int L[6];             // slab thickness x-,x+,y-,y+,z-,z+
+};
+
+// One time step of a grid with the uniaxial PML: the H~ and E launches.
+template <typename T>
+cudaError_t launch_upml(const StepGrid<T>* g, const UpmlDev<T>& u, long long ncell, int offset, cudaStream_t st);
+
 // Centred Bloch coupling of a gain grid: the polarization, current and
 // population kernels that follow the (passive) step kernel of step offset.
 template <typename T>

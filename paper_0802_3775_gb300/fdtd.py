@@ -97,6 +97,7 @@ SIGNATURES = {
     "fdtd_set_wait_limit": [_P, C.c_int64],
     "fdtd_set_gain_coupling": [_P, C.c_int32],
     "fdtd_set_item_order": [_P, C.c_int32],
+    "fdtd_set_absorber": [_P, C.c_int32],
     "fdtd_batch_create": [C.POINTER(_P), C.c_int32, _P, C.POINTER(_P)],
     "fdtd_batch_destroy": [_P],
     "fdtd_batch_set_launch": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
@@ -221,6 +222,8 @@ class Grid:
                 precision=precision or spec.precision, eps=spec.eps, cpml_m=spec.cpml_m,
                 cpml_sigma_factor=spec.cpml_sigma_factor, cpml_kappa_max=spec.cpml_kappa_max,
                 cpml_alpha_max=spec.cpml_alpha_max, cpml_f_hat=spec.cpml_f_hat, seed=spec.seed, **kw)
+        if getattr(spec, "absorber", "cpml") != "cpml":
+            g.set_absorber(spec.absorber)
         if spec.spheres is not None:
             g.set_eps_from_spheres(spec.spheres, spec.box_lo, spec.box_hi)
         if spec.gain is not None:
@@ -284,6 +287,10 @@ class Grid:
 
     def set_launch(self, bx=32, by=8, zdepth=0, grid_blocks=0):
         check(self._lib.fdtd_set_launch(self.h, int(bx), int(by), int(zdepth), int(grid_blocks)))
+
+    def set_absorber(self, absorber):
+        """"cpml" (default) or "upml" (uniaxial PML on the same grading; passive grids)."""
+        check(self._lib.fdtd_set_absorber(self.h, {"cpml": 0, "upml": 1}[absorber]))
 
     def set_item_order(self, order):
         """"costliest" (slab items first) or "z" (plain z order) for the single-node kernels."""
