@@ -76,6 +76,12 @@ __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast
 __device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 
+// CPML memory of the planes ahead staged per thread by cp.async (1), or read
+// from global memory where the update needs it (0: smaller stages).
+#ifndef FDTD_PAIR_PSI_STAGED
+#define FDTD_PAIR_PSI_STAGED 1
+#endif
+
 // Shared-memory layout of the paired kernel (host and device agree).
 template <int OY>
 struct PairLayout {
@@ -98,7 +104,7 @@ struct PairLayout {
   static constexpr size_t field_bytes = align128((size_t)6 * PL * sizeof(float));
   static constexpr size_t mat_bytes = align128((size_t)OPL);
   // CPML memory fetched ahead: 4 slots per owned node, 2 per halo node
-  static constexpr size_t psi_bytes = align128((size_t)(4 * NC + 2 * NHC) * sizeof(float));
+  static constexpr size_t psi_bytes = FDTD_PAIR_PSI_STAGED ? align128((size_t)(4 * NC + 2 * NHC) * sizeof(float)) : 0;
   static constexpr size_t stage_bytes = field_bytes + mat_bytes + psi_bytes;
   // H of the plane (row 0 = y0-1, column 1 = x0-1), two buffers: plane p uses p & 1
   static constexpr size_t hbuf_bytes = align128((size_t)3 * HPL * sizeof(float));
@@ -597,6 +603,10 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
       col_axis[r] = (pc[r].sx0 >= 0 || pc[r].sx1 >= 0) ? 0 : (pc[r].sy >= 0 ? 1 : -1);
     const int zs_lo = G.Sd[2] ? G.L[4] : 0, zs_hi = G.Sd[2] ? G.nz - G.L[5] : G.nz;
     auto issue_psi = [&](int plane, int stage) {
+      if (!FDTD_PAIR_PSI_STAGED) {
+        cp_async_commit();
+        return;
+      }
       float* slots = reinterpret_cast<float*>(stages + (size_t)stage * L::stage_bytes + L::field_bytes + L::mat_bytes);
       const bool zs = plane < zs_lo || plane >= zs_hi;
       const int sz = zs ? slab_index(plane, G.nz, G.L[4], G.L[5]) : -1;
@@ -745,7 +755,7 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
         if (gen_h) {
           // CPML memory of this pair fetched ahead
           float2 pre[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
-          pa[r] = zslab ? 2 : col_axis[r];
+          pa[r] = FDTD_PAIR_PSI_STAGED ? (zslab ? 2 : col_axis[r]) : -1;
           if (pa[r] >= 0) {
             pre[0] = ld2(slots + sbase[r]);
             pre[1] = ld2(slots + sstride + sbase[r]);
