@@ -242,7 +242,8 @@ enum { FDTD_ORDER_COSTLIEST = 0, FDTD_ORDER_Z = 1 };
  * likewise with -S curl E.  Sources act outside the layer only.  UPML grids
  * step with two launches per step (H~, then E, one thread per node;
  * fdtd_kernel_in_use reports kind 4), passive grids only (E_INVAL with a
- * gain medium).  Before the first step only (E_STATE after). */
+ * gain medium), stepping alone (fdtd_batch_create refuses them).  Before the
+ * first step only (E_STATE after). */
 enum { FDTD_ABSORBER_CPML = 0, FDTD_ABSORBER_UPML = 1 };
 int fdtd_set_absorber(fdtd_grid* g, int32_t absorber);
 int fdtd_set_item_order(fdtd_grid* g, int32_t order);

@@ -531,6 +531,8 @@ int fdtd_batch_create(fdtd_grid* const* grids, int32_t n, void* stream, fdtd_bat
       if (!grids[q] || !grids[q]->impl) return set_error(FDTD_E_INVAL, "null member %d", q);
       if (grids[q]->impl->has_gain() && grids[q]->impl->coupling == FDTD_COUPLING_CENTRED)
         return set_error(FDTD_E_INVAL, "member %d has the centred gain coupling: such grids step alone", q);
+      if (grids[q]->impl->absorber == FDTD_ABSORBER_UPML)
+        return set_error(FDTD_E_INVAL, "member %d has the uniaxial PML: such grids step alone", q);
       GridBase* G = grids[q]->impl;
       if (!G->material_set) return set_error(FDTD_E_STATE, "member %d has no permittivity map", q);
       if (prec >= 0 && G->precision() != prec) return set_error(FDTD_E_INVAL, "members differ in precision");

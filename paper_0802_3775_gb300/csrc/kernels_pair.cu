@@ -52,6 +52,17 @@ __device__ __forceinline__ float2 upk2(unsigned long long r) {
   asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
   return v;
 }
+#ifndef FDTD_PAIR_X2_INTRINSICS
+#define FDTD_PAIR_X2_INTRINSICS 0
+#endif
+#if FDTD_PAIR_X2_INTRINSICS
+// the toolkit's packed float2 intrinsics (the compiler keeps the pairs in
+// register pairs); a - b is a + (-b), exactly, lane by lane
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+#else
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
   unsigned long long r;
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
@@ -72,6 +83,7 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
   return upk2(r);
 }
+#endif
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 __device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }

@@ -81,3 +81,14 @@ def test_upml_grid_refuses_gain():
     with pytest.raises(FdtdError) as e:
         g.set_gain(inputs.GainSpec())
     assert e.value.code == -1
+
+
+def test_a_batch_refuses_a_upml_member():
+    from paper_0802_3775_gb300.fdtd import Batch, FdtdError
+    spec = small_opal(precision="f32")
+    spec.absorber = "upml"
+    a = gpu_grid(spec)
+    b = gpu_grid(small_opal(precision="f32"))
+    with pytest.raises(FdtdError) as e:
+        Batch([a, b])
+    assert e.value.code == -1
