@@ -23,7 +23,7 @@ Besides the headline workload, the default single-GPU run (rank 0) adds:
     reduced copies of the workload (and of batch members), computed by the
     same CPU leg.
 
---impl reference times the FP64 CPU oracle (the reference of this build) on a
+--impl reference times the FP64 CPU oracle (the reference the library is checked against) on a
 bounded sample of the same workload, on the host cores (one process per
 allowed core, each stepping its own realization), rank 0 only.
 """
@@ -115,7 +115,7 @@ WORKLOAD_TEXT = {
 
 def algorithmic_bytes(spec, gain_cells: int) -> float:
     """Compulsory HBM bytes of one step-kernel launch: every state word read
-    once and written once, material read once (see the design notes)."""
+    once and written once, material read once."""
     w = 4 if spec.precision == "f32" else 8
     nx, ny, nz = spec.shape
     ncell = nx * ny * nz

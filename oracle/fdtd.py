@@ -21,7 +21,7 @@ Units (normalized, exact rescalings of SI):
 One step n -> n+1 (plain loops over whole arrays, in this order):
   1. H~^{n+1/2} = H~^{n-1/2} - S curl_f E^n, each derivative in an absorbing
      slab replaced by d/kappa + psi,  psi <- b psi + c d   (CPML, convolutional
-     form of the PML; the paper names UPML, this build reads it as CPML).
+     form of the PML; the paper names a uniaxial PML, available as absorber="upml").
   2. flux T^n from E^n and (H~^{n-1/2} + H~^{n+1/2}) / 2.
   3. gain cells: P~^{n+1} = a1 P~^n - a2 P~^{n-1} + a3 (N1 - N2)^n E^n + noise.
   4. E^{n+1} = E^n + (S/eps_r) curl_b H~^{n+1/2} - (1/eps_r)(P~^{n+1} - P~^n + src^n),
@@ -31,7 +31,7 @@ One step n -> n+1 (plain loops over whole arrays, in this order):
      dN^{n+1} = dN^n + (M - I) dN^n + w r     (dN = N - N_eq).
   6. probes record E^{n+1}.
 
-Readings where the paper is silent (also listed in the design notes):
+Readings where the paper is silent:
   * PML grading: sigma = sigma_max rho^m, kappa = 1 + (kappa_max-1) rho^m,
     alpha = alpha_max (1 - rho); sigma_max dt/eps0 = factor (m+1) S / sqrt(eps_edge),
     alpha dt/eps0 = alpha_max 2 pi f_ref dt;  b = exp(-(sigma/kappa + alpha) dt/eps0),
