@@ -9,11 +9,12 @@ workload recipe, stepped for as long as the workload runs:
   20000 steps (the passive workload's run length), solved twice: with the
   binary32-rounded coefficient tables an FP32 run uses (``coef32``) and with
   exact coefficients.  Stored: the FP64 flux series T^n, the probe series at
-  every 4th step (binary32: the bar is 1e-5), and the final six fields at
-  two full z-planes plus 2048 seeded cells (binary32) with their indices.
+  every 4th step (binary32: the bar is 1e-5), and the six fields at two full
+  z-planes plus 2048 seeded cells (binary32) after SNAP_STEPS steps (while the
+  pulse is inside the opal, on its trailing edge) and after the run.
 
 Run from the repository root:  python tests/golden/make_long_runs.py [name ...]
-(about 15 minutes per oracle run of the 64^3 opal on one core).
+(the two oracle runs of the 64^3 opal go to two processes, ~17 minutes).
 """
 from __future__ import annotations
 
@@ -31,6 +32,7 @@ from oracle import Oracle  # noqa: E402
 from paper_0802_3775_gb300 import inputs  # noqa: E402
 
 OPAL64_STEPS = 20000
+SNAP_STEPS = (2000, 5000)
 OPAL64_PLANES = (20, 44)
 OPAL64_NCELLS = 2048
 PROBE_EVERY = 4
@@ -59,16 +61,23 @@ def run_opal64(coef32):
     spec = opal64_spec()
     o = Oracle.from_spec(spec, coef32=coef32)
     t0 = time.perf_counter()
-    o.step(spec.steps)
+    out = {}
+    for q, n in enumerate(SNAP_STEPS):
+        o.step(n - o.n)
+        planes, cells = sample_fields(o.fields_memory_order(), spec.shape)
+        out[f"snap{q}_planes"], out[f"snap{q}_cells"] = planes, cells
+    o.step(spec.steps - o.n)
     print(f"opal64 coef32={coef32}: {spec.steps} steps in {time.perf_counter() - t0:.0f} s", flush=True)
     planes, cells = sample_fields(o.fields_memory_order(), spec.shape)
-    return dict(flux=o.flux_series()[0], probes=o.probe_series()[PROBE_EVERY - 1::PROBE_EVERY].astype(np.float32),
-                planes=planes, cells=cells, energy=np.array([o.energy()]))
+    out.update(flux=o.flux_series()[0], probes=o.probe_series()[PROBE_EVERY - 1::PROBE_EVERY].astype(np.float32),
+               planes=planes, cells=cells, energy=np.array([o.energy()]))
+    return out
 
 
 def make_opal64():
-    r32 = run_opal64(True)
-    rex = run_opal64(False)
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(2) as pool:
+        r32, rex = pool.map(run_opal64, [True, False])
     np.savez_compressed(os.path.join(HERE, "long_opal64_f32.npz"),
                         **{k + "_coef32": v for k, v in r32.items()},
                         **{k + "_exact": v for k, v in rex.items()})
