@@ -16,6 +16,8 @@ Besides the headline workload, the default single-GPU run (rank 0) adds:
   * ``batch``: the 64-realization mixed batch (half lasing) stepped together,
     with its roofline fraction and its realizations/hour against the plain
     single-run FP64 GPU path;
+  * ``lasing``: the 140^3 Maxwell-Bloch lasing workload, with its roofline
+    fraction;
   * ``serve``: a Poisson request stream of the served workload's sizes;
   * ``cpu_baseline``: the FP64 oracle timed on the host cores, one process
     per allowed core (independent realizations) and single-threaded;
@@ -311,6 +313,23 @@ def timed_workload(args, specs, world, dist, steps, warmup, sample_clocks=True):
     return rec, grids, stepper
 
 
+def recorded_traffic(args, workload, rec):
+    """DRAM bytes of one step launch from the ncu capture of this workload in
+    profiles/, when it was taken on the kernel and launch shape this run
+    uses; else None."""
+    prof = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
+    if not os.path.exists(prof):
+        return None
+    with open(prof) as f:
+        tr = json.load(f)
+    zd = rec["tune"]["zdepth"] if rec["tune"] else args.zdepth
+    od = ["costliest", "z"][rec["tune"]["order"]] if rec["tune"] else (args.order or "costliest")
+    if rec["n_kernels"] == 1 and tr.get("kernel") == rec["kname"] and tr.get("tile") == rec["tiles"][0] \
+            and tr.get("zdepth") == zd and tr.get("order", "costliest") == od:
+        return tr.get("dram_bytes_per_launch")
+    return None
+
+
 def run_gpu(args, rank, world, dist):
     import torch
 
@@ -322,17 +341,7 @@ def run_gpu(args, rank, world, dist):
     specs = workload_specs(args.workload, rank, args.steps + args.warmup)
     rec, grids, stepper = timed_workload(args, specs, world, dist, args.steps, args.warmup)
     roof = rec["roofline"]
-    prof = os.path.join(ROOT, "profiles", f"traffic_{args.workload}.json")
-    if os.path.exists(prof):
-        with open(prof) as f:
-            tr = json.load(f)
-        # DRAM bytes of one launch from an ncu capture of this workload, when
-        # it was taken on the kernel and launch shape this run uses
-        zd = rec["tune"]["zdepth"] if rec["tune"] else args.zdepth
-        od = ["costliest", "z"][rec["tune"]["order"]] if rec["tune"] else (args.order or "costliest")
-        if rec["n_kernels"] == 1 and tr.get("kernel") == rec["kname"] and tr.get("tile") == rec["tiles"][0] \
-                and tr.get("zdepth") == zd and tr.get("order", "costliest") == od:
-            roof["traffic"] = tr.get("dram_bytes_per_launch")
+    roof["traffic"] = recorded_traffic(args, args.workload, rec)
 
     batch_grids = []
     result = {
@@ -368,6 +377,8 @@ def run_gpu(args, rank, world, dist):
         if args.workload == "planewave" and not args.no_batch:
             result["batch"] = batch_record(args)
             result["gpu_launches"] += result["batch"]["gpu_launches"]
+            result["lasing"] = lasing_record(args)
+            result["gpu_launches"] += result["lasing"]["gpu_launches"]
         if not args.no_cpu:
             result["cpu_baseline"], result["oracle_error"] = cpu_leg(args)
     if rank == 0:
@@ -403,6 +414,19 @@ def batch_record(args):
     for g in grids:
         g.close()
     return out
+
+
+def lasing_record(args):
+    """The Maxwell-Bloch lasing workload (140^3, gain in the spheres) on this
+    GPU, timed like the headline workload."""
+    specs = workload_specs("lasing", 0, args.steps + args.warmup)
+    rec, grids, _ = timed_workload(args, specs, 1, None, args.steps, args.warmup)
+    for g in grids:
+        g.close()
+    rec["roofline"]["traffic"] = recorded_traffic(args, "lasing", rec)
+    return {"workload": WORKLOAD_TEXT["lasing"], "value": rec["value"], "unit": "Mcell-updates/s",
+            "ms_per_step": rec["ms_per_step"], "cells": rec["cells"], "launch_shape": rec["launch_shape"],
+            "roofline": rec["roofline"], "clocks": rec["clocks"], "gpu_launches": rec["launches"]}
 
 
 def run_e2e(args, specs, rank, dist):

@@ -116,3 +116,28 @@ def test_a_batch_refuses_a_centred_member():
     with pytest.raises(FdtdError) as e:
         Batch([a, b])
     assert e.value.code == -1
+
+
+def test_centred_checkpoint_and_autotune_are_bitwise():
+    """The centred coupling's gain state travels with a checkpoint and
+    survives the autotuner's trials bit for bit."""
+    import os
+    import tempfile
+    spec = _spec("f32")
+    a = gpu_grid(spec)
+    a.step(200)
+    ref = a.read_fields(), a.read_gain(3)
+    b = gpu_grid(spec)
+    b.step(120)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        b.save_state(path)
+        c = gpu_grid(spec)
+        c.load_state(path)
+    c.step(80)
+    assert np.array_equal(c.read_fields(), ref[0]) and np.array_equal(c.read_gain(3), ref[1])
+    t = gpu_grid(spec)
+    t.step(120)
+    t.autotune(trial_steps=3)
+    t.step(80)
+    assert np.array_equal(t.read_fields(), ref[0]) and np.array_equal(t.read_gain(3), ref[1])

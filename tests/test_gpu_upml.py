@@ -92,3 +92,30 @@ def test_a_batch_refuses_a_upml_member():
     with pytest.raises(FdtdError) as e:
         Batch([a, b])
     assert e.value.code == -1
+
+
+def test_upml_checkpoint_and_autotune_are_bitwise():
+    """The UPML's auxiliary fields travel with a checkpoint and survive the
+    autotuner's trials: a run split by save/load, or tuned mid-run, equals
+    the straight run bit for bit."""
+    import os
+    import tempfile
+    spec = small_opal(precision="f32", source="sheet")
+    spec.absorber = "upml"
+    a = gpu_grid(spec)
+    a.step(200)
+    ref = a.read_fields()
+    b = gpu_grid(spec)
+    b.step(120)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        b.save_state(path)
+        c = gpu_grid(spec)
+        c.load_state(path)
+    c.step(80)
+    assert np.array_equal(c.read_fields(), ref)
+    t = gpu_grid(spec)
+    t.step(120)
+    t.autotune(trial_steps=3)
+    t.step(80)
+    assert np.array_equal(t.read_fields(), ref)
