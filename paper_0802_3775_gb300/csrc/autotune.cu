@@ -92,7 +92,7 @@ std::vector<Candidate> grid_candidates(const GridBase* g) {
   if (d.periodic[0] || d.periodic[1] || d.periodic[2]) {
     c = {{1, 32, 8, 0, 0}, {1, 32, 4, 0, 0}, {1, 64, 4, 0, 0}, {1, 32, 16, 0, 0}};
   } else if (g->precision() == FDTD_FP32) {
-    c = {{3, 32, 16, 0, 0}, {3, 32, 8, 0, 0}, {3, 32, 16, 8, 0}, {2, 32, 8, 0, 0},
+    c = {{3, 32, 16, 0, 0}, {3, 32, 8, 0, 0}, {3, 32, 16, 8, 0}, {3, 32, 8, 8, 0}, {2, 32, 8, 0, 0},
          {2, 32, 4, 0, 0},  {2, 32, 8, 8, 0}, {2, 32, 8, 24, 0}};
   } else {
     c = {{2, 32, 8, 0, 0}, {2, 32, 4, 0, 0}, {2, 32, 8, 8, 0}, {2, 32, 4, 16, 0}, {2, 32, 8, 24, 0}};
@@ -237,7 +237,7 @@ int fdtd_batch_autotune(fdtd_batch* b, int32_t trial_steps, fdtd_tune_result* ou
     if (B->grids.front()->precision() == FDTD_FP32) {
       cands.push_back({3, 32, 16, 0, 0});
       cands.push_back({3, 32, 16, 8, 0});
-      if (!gain) cands.push_back({3, 32, 8, 0, 0});
+      cands.push_back({3, 32, 8, 0, 0});
     }
     const int kind0 = B->kernel_kind, by0 = B->by, zd0 = B->zdepth, gb0 = B->grid_blocks, graph0 = B->graph_steps;
     const bool timing = B->timer.on;

@@ -262,6 +262,33 @@ __device__ __forceinline__ void pair_h(const StepGrid<float>& G, const PairCol& 
   hz = fma2(ncH, sub2(dxEy, dyEx), ld2(Fk + 5 * PL + o));
 }
 
+// Gain state of a node pair (node 0 in .x, node 1 in .y), loaded at the
+// start of the plane so the loads' latency hides behind the H work.
+struct PairGain {
+  float2 pnx, pny, pnz, pmx, pmy, pmz, d1, d2, d3, k1, k2, k3;
+};
+
+// Load the gain state of the pair whose node 0 sits at gain index g0 (even:
+// 8-byte words); slot `sel` holds P~^n.
+__device__ __forceinline__ void load_pair_gain(const StepGrid<float>& G, int sel, long long g0, PairGain& s) {
+  using W = GainWords<float>;
+  const float* gw = G.gst + g0;
+  const float* pnw = gw + 32 * (sel ? W::P1 : W::P0);
+  const float* pmw = gw + 32 * (sel ? W::P0 : W::P1);
+  s.pnx = ld2(pnw);
+  s.pny = ld2(pnw + 32);
+  s.pnz = ld2(pnw + 64);
+  s.pmx = ld2(pmw);
+  s.pmy = ld2(pmw + 32);
+  s.pmz = ld2(pmw + 64);
+  s.d1 = ld2(gw + 32 * W::DN);
+  s.d2 = ld2(gw + 32 * W::DN + 32);
+  s.d3 = ld2(gw + 32 * W::DN + 64);
+  s.k1 = ld2(gw + 32 * W::CMP);
+  s.k2 = ld2(gw + 32 * W::CMP + 32);
+  s.k3 = ld2(gw + 32 * W::CMP + 64);
+}
+
 // Sources, gain and PEC of the node pair (the general part of the E update):
 // (enx, eny, enz) hold fmad(cE, curl, E^n) of both nodes on entry.  The gain
 // state of both nodes is read and written as 8-byte words (node 0 at gain
@@ -269,11 +296,14 @@ __device__ __forceinline__ void pair_h(const StepGrid<float>& G, const PairCol& 
 // polarization and population updates of both nodes run as f32x2 operations
 // in the scalar kernels' order; a node that is not a gain cell (or is off the
 // grid) keeps its state and gets no polarization current.
-template <bool GAIN>
+// PRE: the pair's gain state was loaded ahead into `gs`; otherwise it is
+// loaded here, the polarization words first and the population words after
+// the field update (fewer registers live at once).
+template <bool GAIN, bool PRE>
 __device__ __forceinline__ void pair_extras(const StepGrid<float>& G, const double* sg, const PairCol& c,
                                             const Plane& pl, int sel, long long n, long long g0, unsigned m0,
                                             unsigned m1, unsigned s0, unsigned s1, float2 ex, float2 ey, float2 ez,
-                                            float2& enx, float2& eny, float2& enz) {
+                                            const PairGain& gs, float2& enx, float2& eny, float2& enz) {
   using W = GainWords<float>;
   const bool ga = GAIN && G.gain && ((m0 >> 6) & 1);
   const bool gb = GAIN && G.gain && c.own1 && ((m1 >> 6) & 1);
@@ -298,10 +328,10 @@ __device__ __forceinline__ void pair_extras(const StepGrid<float>& G, const doub
   if (GAIN && (ga || gb)) {
     float* pmw = gw + 32 * (sel ? W::P0 : W::P1);  // P~^{n-1}, receives P~^{n+1}
     const float* pnw = gw + 32 * (sel ? W::P1 : W::P0);
-    const float2 pnx = ld2(pnw), pny = ld2(pnw + 32), pnz = ld2(pnw + 64);
-    const float2 pmx = ld2(pmw), pmy = ld2(pmw + 32), pmz = ld2(pmw + 64);
-    d1 = ld2(gw + 32 * W::DN);
-    d2 = ld2(gw + 32 * W::DN + 32);
+    const float2 pnx = PRE ? gs.pnx : ld2(pnw), pny = PRE ? gs.pny : ld2(pnw + 32), pnz = PRE ? gs.pnz : ld2(pnw + 64);
+    const float2 pmx = PRE ? gs.pmx : ld2(pmw), pmy = PRE ? gs.pmy : ld2(pmw + 32), pmz = PRE ? gs.pmz : ld2(pmw + 64);
+    d1 = PRE ? gs.d1 : ld2(gw + 32 * W::DN);
+    d2 = PRE ? gs.d2 : ld2(gw + 32 * W::DN + 32);
     const float2 drive = mul2(bc2(G.a3), add2(bc2(G.n12eq), sub2(d1, d2)));
     const float2 a1 = bc2(G.a1), na2 = bc2(-G.a2);
     float2 Px = fma2(drive, ex, fma2(a1, pnx, mul2(na2, pmx)));
@@ -358,8 +388,9 @@ __device__ __forceinline__ void pair_extras(const StepGrid<float>& G, const doub
   if (c.i0 == 0) enz.x = 0.0f;
   if (c.j == 0) enz = make_float2(0.0f, 0.0f);
   if (GAIN && (ga || gb)) {
-    const float2 d3 = ld2(gw + 32 * W::DN + 64);
-    const float2 k1 = ld2(gw + 32 * W::CMP), k2 = ld2(gw + 32 * W::CMP + 32), k3 = ld2(gw + 32 * W::CMP + 64);
+    const float2 d3 = PRE ? gs.d3 : ld2(gw + 32 * W::DN + 64);
+    const float2 k1 = PRE ? gs.k1 : ld2(gw + 32 * W::CMP), k2 = PRE ? gs.k2 : ld2(gw + 32 * W::CMP + 32),
+                 k3 = PRE ? gs.k3 : ld2(gw + 32 * W::CMP + 64);
     const float2 half = bc2(0.5f);
     const float2 hx_ = mul2(half, add2(enx, ex)), hy_ = mul2(half, add2(eny, ey)), hz_ = mul2(half, add2(enz, ez));
     const float2 r = mul2(bc2(G.q), fma2(hz_, dPz, fma2(hy_, dPy, mul2(hx_, dPx))));
@@ -420,6 +451,9 @@ static_assert(sizeof(PairNext) <= 64, "PairNext lives in the 128-byte barrier ar
 #ifndef FDTD_PAIR_MIN_BLOCKS
 #define FDTD_PAIR_MIN_BLOCKS 2
 #endif
+#ifndef FDTD_PAIR_GAIN8_MIN_BLOCKS
+#define FDTD_PAIR_GAIN8_MIN_BLOCKS 3
+#endif
 
 // Owner threads of a tile of OY rows when each owns RY rows of node pairs.
 template <int OY, int RY>
@@ -432,8 +466,14 @@ struct PairThreads {
 #define FDTD_PAIR_RY 1  // rows of node pairs per owner thread in 32 x 16 tiles (2 measured slower: fewer warps)
 #endif
 
+// Resident blocks the register budget is sized for: 2 of 288 threads (32 x
+// 16 tiles), 4 of 160 (32 x 8); gain grids on 32 x 8 tiles 3, whose gain
+// state (12 words a pair) stays in registers from the start of the plane.
+template <bool GAIN, int OY>
+constexpr int pair_min_blocks() { return (GAIN && OY == 8) ? FDTD_PAIR_GAIN8_MIN_BLOCKS : FDTD_PAIR_MIN_BLOCKS * 16 / OY; }
+
 template <bool GAIN, int OY, int RY>
-__global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS * 16 / OY)
+__global__ void __launch_bounds__(PairThreads<OY, RY>::NT, pair_min_blocks<GAIN, OY>())
     k_step_pair(const StepGrid<float>* __restrict__ grids, const TmaGrid* __restrict__ maps,
                 const int4* __restrict__ items, int nitems, int offset) {
   using L = PairLayout<OY>;
@@ -749,6 +789,15 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
         t_gain = t_gain || ((((mm[r] >> 6) | (mm[r] >> 14)) & 1u) != 0u);
       }
       if (GAIN && G.gain) gen_e = gen_e || __any_sync(0xffffffffu, t_gain);
+      // gain state of this plane's gain pairs: on 32 x 8 tiles (registers for
+      // 3 blocks per SM) loaded before the H work, so the loads' latency
+      // hides behind it; on 32 x 16 tiles (2 blocks of 288 threads, no
+      // registers to spare) loaded where the E update needs it
+      PairGain gst[RY];
+#pragma unroll
+      for (int r = 0; r < RY; ++r)
+        if (GAIN && OY == 8 && G.gain && ok && valid[r] && ((((mm[r] >> 6) | (mm[r] >> 14)) & 1u) != 0u))
+          load_pair_gain(G, sel, gbase[r] + (long long)k * gplane, gst[r]);
       Plane pl;
       if (gen_h || gen_e) pl = make_plane(G, k);
       const float* cz = cfz + 6 * p;
@@ -858,8 +907,8 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, FDTD_PAIR_MIN_BLOCKS 
               const bool pec = pc[r].i0 == 0 || pc[r].j == 0 || pl.pecz;
               const bool gainpair = GAIN && G.gain && (((m0 | m1) >> 6) & 1);
               if (src0[r] | src1[r] | pec | gainpair)
-                pair_extras<GAIN>(G, sg, pc[r], pl, sel, n, GAIN ? gbase[r] + (long long)k * gplane : 0, m0, m1,
-                                  src0[r], src1[r], ex, ey, ez, enx, eny, enz);
+                pair_extras<GAIN, OY == 8>(G, sg, pc[r], pl, sel, n, GAIN ? gbase[r] + (long long)k * gplane : 0, m0, m1,
+                                  src0[r], src1[r], ex, ey, ez, gst[r], enx, eny, enz);
             }
             // a node past the grid edge is never stored (its lane holds zeros)
             if (!pc[r].own1) enx.y = eny.y = enz.y = 0.0f;
