@@ -62,15 +62,19 @@ def measured_peaks():
 
 
 # ----------------------------------------------------------------------------- workloads
+NCELL = {"planewave": 8, "lasing": 6}  # unit cells per edge of the workloads (--ncell shrinks them for profiling)
+
+
 def workload_specs(name: str, rank: int, steps: int):
     """Run records of one rank's share of the workload."""
     if name == "planewave":
         # 8x8x8 unit cells at 20 cells/a + 12-cell CPML = 184^3, FP32, sigma 6 %
-        return [inputs.opal_planewave_f32(ncell=8, res=20, npml=12, sigma=0.06, realization=rank, steps=steps)]
+        return [inputs.opal_planewave_f32(ncell=NCELL["planewave"], res=20, npml=12, sigma=0.06, realization=rank,
+                                          steps=steps)]
     if name == "lasing":
         # 6x6x6 unit cells at 20 cells/a + 10-cell CPML = 140^3, FP32 gain
-        return [inputs.opal_lasing_f32(ncell=6, res=20, npml=10, sigma=0.05, pump=1e10, realization=rank,
-                                       steps=steps)]
+        return [inputs.opal_lasing_f32(ncell=NCELL["lasing"], res=20, npml=10, sigma=0.05, pump=1e10,
+                                       realization=rank, steps=steps)]
     if name == "dipole64":
         return [inputs.opal_dipole_f64(steps=steps)]
     if name == "batch":
@@ -315,8 +319,8 @@ def timed_workload(args, specs, world, dist, steps, warmup, sample_clocks=True):
 
 def recorded_traffic(args, workload, rec):
     """DRAM bytes of one step launch from the ncu capture of this workload in
-    profiles/, when it was taken on the kernel and launch shape this run
-    uses; else None."""
+    profiles/, when it was taken on the grid size, kernel and launch shape
+    this run uses; else None."""
     prof = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
     if not os.path.exists(prof):
         return None
@@ -325,7 +329,7 @@ def recorded_traffic(args, workload, rec):
     zd = rec["tune"]["zdepth"] if rec["tune"] else args.zdepth
     od = ["costliest", "z"][rec["tune"]["order"]] if rec["tune"] else (args.order or "costliest")
     if rec["n_kernels"] == 1 and tr.get("kernel") == rec["kname"] and tr.get("tile") == rec["tiles"][0] \
-            and tr.get("zdepth") == zd and tr.get("order", "costliest") == od:
+            and tr.get("zdepth") == zd and tr.get("order", "costliest") == od and tr.get("cells") == rec["cells"]:
         return tr.get("dram_bytes_per_launch")
     return None
 
@@ -349,7 +353,9 @@ def run_gpu(args, rank, world, dist):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if specs[0].precision == "f32" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT[args.workload], "grids_per_gpu": len(specs),
+        "config": {"workload": WORKLOAD_TEXT[args.workload] + (f" -- reduced to {args.ncell}^3 unit cells "
+                                                                 f"({specs[0].shape[0]}^3 grid)" if args.ncell else ""),
+                   "grids_per_gpu": len(specs),
                    "cells_per_gpu": rec["cells"], "l2": "state larger than L2 (%.0f MB per GPU)" %
                    (rec["cells"] * (49 if specs[0].precision == "f32" else 97) / 1e6),
                    "parallelism": f"replicas x{world} (independent realizations)",
@@ -821,7 +827,12 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sub-record of the default workload")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shape")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle's CPU leg (timing and error checks)")
+    ap.add_argument("--ncell", type=int, default=0,
+                    help="unit cells per edge of the planewave / lasing workload (0: the workload's own; a smaller "
+                         "grid for profiling captures)")
     args = ap.parse_args()
+    if args.ncell:
+        NCELL[args.workload] = args.ncell
     if args.warmup < 3:
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))
