@@ -164,21 +164,35 @@ int fdtd_set_eps_from_spheres(fdtd_grid* g, const double* spheres, int64_t n, co
     fdtd::DeviceMemory tmp;
     tmp.stream = G->stream;
     double* dsph = (double*)tmp.get(sizeof(double) * 4 * (size_t)std::max<int64_t>(n, 1));
+    float* dfsph = (float*)tmp.get(sizeof(float) * 8 * (size_t)std::max<int64_t>(n, 1));
+    // binary32 split of each centre (integer part exact, fraction rounded) and r^2, for the rasterizer's pre-test
+    std::vector<float> fsph((size_t)8 * (size_t)n);
+    for (int64_t s = 0; s < n; ++s) {
+      for (int a = 0; a < 3; ++a) {
+        const double c = spheres[4 * s + a], fl = std::floor(c);
+        fsph[8 * s + a] = (float)fl;
+        fsph[8 * s + 4 + a] = (float)(c - fl);
+      }
+      fsph[8 * s + 3] = (float)(spheres[4 * s + 3] * spheres[4 * s + 3]);
+      fsph[8 * s + 7] = 0.0f;
+    }
     int* dstart = (int*)tmp.get(sizeof(int) * count.size());
     int* dlist = (int*)tmp.get(sizeof(int) * std::max<size_t>(list.size(), 1));
-    if (!dsph || !dstart || !dlist) {
+    if (!dsph || !dfsph || !dstart || !dlist) {
       tmp.release_all();
       return set_error(FDTD_E_NOMEM, "device allocation failed (sphere bins)");
     }
     cudaError_t e = cudaSuccess;
     if (n) e = cudaMemcpyAsync(dsph, spheres, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, G->stream);
+    if (n && e == cudaSuccess)
+      e = cudaMemcpyAsync(dfsph, fsph.data(), sizeof(float) * 8 * n, cudaMemcpyHostToDevice, G->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dstart, count.data(), sizeof(int) * count.size(), cudaMemcpyHostToDevice, G->stream);
     if (e == cudaSuccess && !list.empty())
       e = cudaMemcpyAsync(dlist, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, G->stream);
     const double box[6] = {box_lo[0], box_lo[1], box_lo[2], box_hi[0], box_hi[1], box_hi[2]};
     if (e == cudaSuccess)
-      e = fdtd::launch_rasterize(G->d_mat, d.nx, d.ny, d.nz, G->px, dsph, dstart, dlist, B, bn[0], bn[1], bn[2], box,
-                                 G->stream);
+      e = fdtd::launch_rasterize(G->d_mat, d.nx, d.ny, d.nz, G->px, dsph, dfsph, dstart, dlist, B, bn[0], bn[1], bn[2],
+                                 box, G->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(G->stream);
     tmp.release_all();
     if (e != cudaSuccess) return fdtd::cuda_error(e, "rasterize");

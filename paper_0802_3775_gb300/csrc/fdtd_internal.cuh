@@ -162,9 +162,11 @@ template <typename T>
 cudaError_t launch_advance(StepGrid<T>* sg, ObsGrid<T>* og, int ngrids, int count, cudaStream_t st);
 
 // Rasterization of binned spheres (see fdtd_set_eps_from_spheres).
-cudaError_t launch_rasterize(uint8_t* mat, int nx, int ny, int nz, int px, const double* spheres, const int* bin_start,
-                             const int* bin_list, int bin, int bnx, int bny, int bnz, const double* box,
-                             cudaStream_t st);
+// fspheres: 8 floats per sphere, (floor cx, floor cy, floor cz, r^2) and
+// (cx, cy, cz) - floor(.), rounded to binary32 (16-byte aligned).
+cudaError_t launch_rasterize(uint8_t* mat, int nx, int ny, int nz, int px, const double* spheres,
+                             const float* fspheres, const int* bin_start, const int* bin_list, int bin, int bnx, int bny,
+                             int bnz, const double* box, cudaStream_t st);
 
 // Uniaxial PML of a passive grid: grading tables and auxiliary fields.
 template <typename T>

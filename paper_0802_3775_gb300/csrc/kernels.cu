@@ -830,8 +830,19 @@ cudaError_t launch_energy(const T* const* F6, const uint8_t* mat, double e0, dou
 // =====================================================================
 // Rasterizer
 // =====================================================================
+// The FP64 test of a point against a sphere, (dx*dx + dy*dy) + dz*dz < r*r
+// with each operation rounded, decides the material.  Most points lie far
+// from every surface, so a binary32 test decides them first: with the
+// sphere centre split into floor(c) (exact in binary32) and c - floor(c)
+// (rounded to binary32, error <= 2^-25), the binary32 dx, dy, dz are within
+// 2^-25 + 2^-24 |d| of i - c, and d2 within 2^-22 (d2 + r^2 + 1) of the
+// exact square distance, r^2 rounded within 2^-24 r^2.  Whenever the binary32
+// d2 and r^2 differ by more than M = 2^-19 (d2 + r^2 + 1) (eight times that
+// bound) the FP64 test gives the same answer; otherwise the FP64 test runs.
+// fsph: per sphere (floor cx, floor cy, floor cz, r^2) and (cx, cy, cz) - floor(.), in binary32.
 __global__ void k_rasterize(uint8_t* __restrict__ mat, int nx, int ny, int nz, int px, const double* __restrict__ sph,
-                            const int* __restrict__ bstart, const int* __restrict__ blist, int bin, int bnx, int bny,
+                            const float4* __restrict__ fsph, const int* __restrict__ bstart,
+                            const int* __restrict__ blist, int bin, int bnx, int bny,
                             double lo0, double lo1, double lo2, double hi0, double hi1, double hi2) {
   const long long ncell = (long long)nx * ny * nz;
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -844,15 +855,30 @@ __global__ void k_rasterize(uint8_t* __restrict__ mat, int nx, int ny, int nz, i
   const double pys[4] = {(double)j, j + 0.5, (double)j, j + 0.5};
   const double pzs[4] = {(double)k, (double)k, k + 0.5, k + 0.5};
   bool ins[4] = {false, false, false, false};
-  for (int q = bstart[b]; q < bstart[b + 1]; ++q) {
+  const float fi = (float)i, fj = (float)j, fk = (float)k;
+  for (int q = bstart[b]; q < bstart[b + 1] && !(ins[0] && ins[1] && ins[2] && ins[3]); ++q) {
     const int s = blist[q];
-    const double cx = sph[4 * s], cy = sph[4 * s + 1], cz = sph[4 * s + 2], r = sph[4 * s + 3];
-    const double rr = __dmul_rn(r, r);
+    const float4 a = fsph[2 * s], f = fsph[2 * s + 1];
+    // offsets of the integer and half-integer nodes from the centre
+    const float x0 = __fsub_rn(__fsub_rn(fi, a.x), f.x), x1 = __fsub_rn(__fsub_rn(__fadd_rn(fi, 0.5f), a.x), f.x);
+    const float y0 = __fsub_rn(__fsub_rn(fj, a.y), f.y), y1 = __fsub_rn(__fsub_rn(__fadd_rn(fj, 0.5f), a.y), f.y);
+    const float z0 = __fsub_rn(__fsub_rn(fk, a.z), f.z), z1 = __fsub_rn(__fsub_rn(__fadd_rn(fk, 0.5f), a.z), f.z);
+    const float xs[2] = {__fmul_rn(x0, x0), __fmul_rn(x1, x1)}, ys[2] = {__fmul_rn(y0, y0), __fmul_rn(y1, y1)};
+    const float zs[2] = {__fmul_rn(z0, z0), __fmul_rn(z1, z1)};
+    const int hx[4] = {1, 0, 0, 1}, hy[4] = {0, 1, 0, 1}, hz[4] = {0, 0, 1, 1};
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      const double dx = __dsub_rn(pxs[t], cx), dy = __dsub_rn(pys[t], cy), dz = __dsub_rn(pzs[t], cz);
-      const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-      ins[t] = ins[t] || (d2 < rr);
+      if (ins[t]) continue;
+      const float d2 = __fadd_rn(__fadd_rn(xs[hx[t]], ys[hy[t]]), zs[hz[t]]);
+      const float m = 0x1p-19f * __fadd_rn(__fadd_rn(d2, a.w), 1.0f);
+      if (d2 < a.w - m) {
+        ins[t] = true;
+      } else if (!(d2 > a.w + m)) {
+        const double cx = sph[4 * s], cy = sph[4 * s + 1], cz = sph[4 * s + 2], r = sph[4 * s + 3];
+        const double dx = __dsub_rn(pxs[t], cx), dy = __dsub_rn(pys[t], cy), dz = __dsub_rn(pzs[t], cz);
+        const double e2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        ins[t] = e2 < __dmul_rn(r, r);
+      }
     }
   }
   unsigned byte = 0;
@@ -865,15 +891,16 @@ __global__ void k_rasterize(uint8_t* __restrict__ mat, int nx, int ny, int nz, i
   mat[pidx3(i, j, k, px, ny)] = (uint8_t)byte;
 }
 
-cudaError_t launch_rasterize(uint8_t* mat, int nx, int ny, int nz, int px, const double* spheres, const int* bin_start,
-                             const int* bin_list, int bin, int bnx, int bny, int bnz, const double* box,
-                             cudaStream_t st) {
+cudaError_t launch_rasterize(uint8_t* mat, int nx, int ny, int nz, int px, const double* spheres,
+                             const float* fspheres, const int* bin_start, const int* bin_list, int bin, int bnx, int bny,
+                             int bnz, const double* box, cudaStream_t st) {
   (void)bnz;
   const long long ncell = (long long)nx * ny * nz;
   const int threads = 256;
   const long long blocks = (ncell + threads - 1) / threads;
-  k_rasterize<<<(unsigned)blocks, threads, 0, st>>>(mat, nx, ny, nz, px, spheres, bin_start, bin_list, bin, bnx, bny,
-                                                     box[0], box[1], box[2], box[3], box[4], box[5]);
+  k_rasterize<<<(unsigned)blocks, threads, 0, st>>>(mat, nx, ny, nz, px, spheres,
+                                                     reinterpret_cast<const float4*>(fspheres), bin_start, bin_list,
+                                                     bin, bnx, bny, box[0], box[1], box[2], box[3], box[4], box[5]);
   return cudaGetLastError();
 }
 
