@@ -62,6 +62,17 @@ def test_null_and_range_checks_without_gpu(lib):
     assert L.fdtd_create_grid(ctypes.byref(d), None, None, ctypes.byref(h)) == -1  # unstable step
     assert L.fdtd_destroy_grid(None) == 0
     assert L.fdtd_version().startswith(b"fdtd-gb300")
+    # the variant and launch options reject a null grid before looking at anything else
+    for fn, arg in (("fdtd_set_gain_coupling", 1), ("fdtd_set_absorber", 1), ("fdtd_set_item_order", 1),
+                    ("fdtd_set_wait_limit", 0)):
+        assert getattr(L, fn)(None, arg) == -1, fn
+        assert b"null" in L.fdtd_last_error()
+    # the allocation-free energy checks its arguments before touching the device
+    six = (ctypes.c_void_p * 6)(*([None] * 6))
+    eps = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    out = ctypes.c_double()
+    assert L.fdtd_field_energy_noalloc(six, None, 8, 8, 8, 8, 0, eps, ctypes.c_double(1e-8), None,
+                                       ctypes.byref(out)) == -1
 
 
 def test_create_without_device_fails_loudly(lib):
