@@ -226,9 +226,11 @@ int fdtd_set_launch(fdtd_grid* g, int32_t bx, int32_t by, int32_t zdepth, int32_
  * FDTD_ORDER_Z issues every item in z order (z-range, then row, then column
  * of tiles), so neighbouring tiles run together and the halo rows and
  * columns they share are read from DRAM once.  The paired kernel keeps its
- * own cost-bucketed z order.  Results do not depend on the order.  E_INVAL
- * for another value. */
+ * own cost-bucketed z order.  Results do not depend on the order.  A launch
+ * parameter of this library: the paper has no counterpart.  E_INVAL for
+ * another value. */
 enum { FDTD_ORDER_COSTLIEST = 0, FDTD_ORDER_Z = 1 };
+int fdtd_set_item_order(fdtd_grid* g, int32_t order);
 
 /* Absorbing layer of the grid's slabs (paper, Sec. "Sample and numerical
  * approach": a uniaxial PML).  FDTD_ABSORBER_CPML (default): the convolutional
@@ -246,7 +248,6 @@ enum { FDTD_ORDER_COSTLIEST = 0, FDTD_ORDER_Z = 1 };
  * first step only (E_STATE after). */
 enum { FDTD_ABSORBER_CPML = 0, FDTD_ABSORBER_UPML = 1 };
 int fdtd_set_absorber(fdtd_grid* g, int32_t absorber);
-int fdtd_set_item_order(fdtd_grid* g, int32_t order);
 
 /* Step-kernel variant: 0 = automatic (the paired kernel for binary32 and
  * the TMA-staged kernel for binary64 grids when no axis is periodic, else the
@@ -262,7 +263,7 @@ int fdtd_set_item_order(fdtd_grid* g, int32_t order);
 int fdtd_set_kernel(fdtd_grid* g, int32_t kind);
 
 /* The step kernel the grid's launches use under its current settings
- * (1 plain, 2 TMA, 3 paired), and the rows of its tile (*rows: the tile of
+ * (1 plain, 2 TMA, 3 paired, 4 the UPML launches), and the rows of its tile (*rows: the tile of
  * owned columns is 32 x rows for kinds 2 and 3, (bx-1) x (by-1) for kind 1).
  * Valid after the first step (or a batch build); E_STATE before. */
 int fdtd_kernel_in_use(fdtd_grid* g, int32_t* kind, int32_t* rows);
