@@ -709,7 +709,7 @@ struct GridImpl final : GridBase {
         const auto ev = timer.next();
         if (ev.first) cudaEventRecord(ev.first, stream);
         if (upml_grid())
-          e = launch_upml<T>(d_sg, upml, ncell, s, stream);
+          e = launch_upml<T>(d_sg, upml, desc.nx, desc.ny, desc.nz, s, stream);
         else if (use_pair)
           e = launch_step_pair(reinterpret_cast<const StepGrid<float>*>(d_sg), d_tma, d_items, (int)items.size(), s,
                                tile_oy, cell_gain(), grid_blocks, stream);
@@ -718,7 +718,7 @@ struct GridImpl final : GridBase {
         else
           e = launch_step<T>(d_sg, d_items, (int)items.size(), s, bx, by_eff, cell_gain(), grid_blocks, stream);
         if (e != cudaSuccess) return cuda_error(e, "step kernel");
-        if (centred_gain() && (e = launch_centred<T>(d_sg, ncell, s, stream)) != cudaSuccess)
+        if (centred_gain() && (e = launch_centred<T>(d_sg, desc.nx, desc.ny, desc.nz, s, stream)) != cudaSuccess)
           return cuda_error(e, "centred coupling kernels");
         if (ev.second) cudaEventRecord(ev.second, stream);
         if (timer.used >= 4096) {

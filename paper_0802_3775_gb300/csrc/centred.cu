@@ -95,12 +95,11 @@ __global__ void __launch_bounds__(256) k_centred_polarize(const StepGrid<T>* __r
   if (n >= G.step_end) return;
   const int fs = (int)(n % G.nsets);
   const int sel = (int)(n & 1);
-  const long long ncell = (long long)G.nx * G.ny * G.nz;
   using W = GainWords<T>;
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
-       c += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(c % G.nx), j = (int)((c / G.nx) % G.ny), k = (int)(c / ((long long)G.nx * G.ny));
-    if (!gain_cell(G, i, j, k)) continue;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+  if (i < G.nx && j < G.ny) {
+    const long long c = ((long long)k * G.ny + j) * G.nx + i;
+    if (!gain_cell(G, i, j, k)) return;
     T* g = G.gst + gain_base(G, i, j, k);
     const T* pn = g + 32 * (sel ? W::P1 : W::P0);
     T* pm = g + 32 * (sel ? W::P0 : W::P1);  // P~^{n-1}, receives P~^{n+1}
@@ -141,10 +140,8 @@ __global__ void __launch_bounds__(256) k_centred_current(const StepGrid<T>* __re
   if (n >= G.step_end) return;
   const int fs = (int)(n % G.nsets), fo = fs + 1 == G.nsets ? 0 : fs + 1;
   const int sel = (int)(n & 1);
-  const long long ncell = (long long)G.nx * G.ny * G.nz;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < ncell;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % G.nx), j = (int)((q / G.nx) % G.ny), k = (int)(q / ((long long)G.nx * G.ny));
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+  if (i < G.nx && j < G.ny) {
     const long long o = pidx3(i, j, k, G.px, G.ny);
     const unsigned m = G.mat[o];
     const int p[3] = {i, j, k};
@@ -160,7 +157,7 @@ __global__ void __launch_bounds__(256) k_centred_current(const StepGrid<T>* __re
       q12[d2] = q2[d2];
       const T a = cell_dP(G, sel, c, i, j, k), b = cell_dP(G, sel, c, q1[0], q1[1], q1[2]);
       const T c2 = cell_dP(G, sel, c, q2[0], q2[1], q2[2]), d = cell_dP(G, sel, c, q12[0], q12[1], q12[2]);
-      if (a == T(0) && b == T(0) && c2 == T(0) && d == T(0)) continue;
+      if (a == T(0) && b == T(0) && c2 == T(0) && d == T(0)) continue;  // next component
       const T dPe = T(0.25) * ((a + b) + (c2 + d));
       T* E = G.F[fo][c];
       E[o] = fmad(-G.cP[(m >> (2 * c)) & 3], dPe, E[o]);
@@ -175,12 +172,11 @@ __global__ void __launch_bounds__(256) k_centred_populations(const StepGrid<T>* 
   if (n >= G.step_end) return;
   const int fs = (int)(n % G.nsets), fo = fs + 1 == G.nsets ? 0 : fs + 1;
   const int sel = (int)(n & 1);
-  const long long ncell = (long long)G.nx * G.ny * G.nz;
   using W = GainWords<T>;
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
-       c += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(c % G.nx), j = (int)((c / G.nx) % G.ny), k = (int)(c / ((long long)G.nx * G.ny));
-    if (!gain_cell(G, i, j, k)) continue;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+  if (i < G.nx && j < G.ny) {
+    const long long c = ((long long)k * G.ny + j) * G.nx + i;
+    if (!gain_cell(G, i, j, k)) return;
     T* g = G.gst + gain_base(G, i, j, k);
     const T* pnew = g + 32 * (sel ? W::P0 : W::P1);
     const T* pold = g + 32 * (sel ? W::P1 : W::P0);
@@ -214,16 +210,16 @@ __global__ void __launch_bounds__(256) k_centred_populations(const StepGrid<T>* 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_centred(const StepGrid<T>* g, long long ncell, int offset, cudaStream_t st) {
-  const long long want = (ncell + 255) / 256;
-  const unsigned blocks = (unsigned)(want < 4096 ? (want > 0 ? want : 1) : 4096);
-  k_centred_polarize<T><<<blocks, 256, 0, st>>>(g, offset);
-  k_centred_current<T><<<blocks, 256, 0, st>>>(g, offset);
-  k_centred_populations<T><<<blocks, 256, 0, st>>>(g, offset);
+cudaError_t launch_centred(const StepGrid<T>* g, int nx, int ny, int nz, int offset, cudaStream_t st) {
+  // one thread per cell (node): blocks of 32 x 8 of one plane
+  const dim3 block(32, 8, 1), grid((unsigned)((nx + 31) / 32), (unsigned)((ny + 7) / 8), (unsigned)nz);
+  k_centred_polarize<T><<<grid, block, 0, st>>>(g, offset);
+  k_centred_current<T><<<grid, block, 0, st>>>(g, offset);
+  k_centred_populations<T><<<grid, block, 0, st>>>(g, offset);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_centred<float>(const StepGrid<float>*, long long, int, cudaStream_t);
-template cudaError_t launch_centred<double>(const StepGrid<double>*, long long, int, cudaStream_t);
+template cudaError_t launch_centred<float>(const StepGrid<float>*, int, int, int, int, cudaStream_t);
+template cudaError_t launch_centred<double>(const StepGrid<double>*, int, int, int, int, cudaStream_t);
 
 }  // namespace fdtd

@@ -179,12 +179,13 @@ struct UpmlDev {
 
 // One time step of a grid with the uniaxial PML: the H~ and E launches.
 template <typename T>
-cudaError_t launch_upml(const StepGrid<T>* g, const UpmlDev<T>& u, long long ncell, int offset, cudaStream_t st);
+cudaError_t launch_upml(const StepGrid<T>* g, const UpmlDev<T>& u, int nx, int ny, int nz, int offset,
+                        cudaStream_t st);
 
 // Centred Bloch coupling of a gain grid: the polarization, current and
 // population kernels that follow the (passive) step kernel of step offset.
 template <typename T>
-cudaError_t launch_centred(const StepGrid<T>* g, long long ncell, int offset, cudaStream_t st);
+cudaError_t launch_centred(const StepGrid<T>* g, int nx, int ny, int nz, int offset, cudaStream_t st);
 
 // Gain initialization: P slots zero, dN~ = init - N~eq in gain cells.
 template <typename T>

@@ -40,12 +40,13 @@ __device__ __forceinline__ T fld(const T* F, const StepGrid<T>& G, int i, int j,
   return (i < 0 || j < 0 || k < 0) ? T(0) : F[pidx3(i, j, k, G.px, G.ny)];
 }
 
-// the grading of axis d is non-zero at node v (+1/2 when `half`)
+// the grading of axis d is non-zero at node v (+1/2 when `half`): depth
+// below L0 or above n - L1, in integers (v + 1/2 < L0 iff v < L0;
+// v + 1/2 > n - L1 iff v >= n - L1)
 template <typename T>
 __device__ __forceinline__ bool graded(const UpmlDev<T>& u, int d, int n, int v, bool half) {
   const int L0 = u.L[2 * d], L1 = u.L[2 * d + 1];
-  const double x = v + (half ? 0.5 : 0.0);
-  return (L0 > 0 && x < L0) || (L1 > 0 && x > n - L1);
+  return (L0 > 0 && v < L0) || (L1 > 0 && (half ? v >= n - L1 : v > n - L1));
 }
 
 template <typename T>
@@ -57,11 +58,9 @@ __global__ void __launch_bounds__(256) k_upml_h(const StepGrid<T>* __restrict__ 
   const T* Ex = G.F[fs][0];
   const T* Ey = G.F[fs][1];
   const T* Ez = G.F[fs][2];
-  const long long ncell = (long long)G.nx * G.ny * G.nz;
   const int nn[3] = {G.nx, G.ny, G.nz};
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < ncell;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % G.nx), j = (int)((q / G.nx) % G.ny), k = (int)(q / ((long long)G.nx * G.ny));
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+  if (i < G.nx && j < G.ny) {
     const int p[3] = {i, j, k};
     const long long o = pidx3(i, j, k, G.px, G.ny);
     const int ip = nbr(G, 0, i, 1), jp = nbr(G, 1, j, 1), kp = nbr(G, 2, k, 1);
@@ -101,17 +100,15 @@ __global__ void __launch_bounds__(256) k_upml_e(const StepGrid<T>* __restrict__ 
   const long long n = G.step + offset;
   if (n >= G.step_end) return;
   __shared__ double sg[kMaxSrc];
-  source_waveforms(G, n, threadIdx.x, sg);
+  source_waveforms(G, n, threadIdx.y * blockDim.x + threadIdx.x, sg);
   __syncthreads();
   const int fs = (int)(n % G.nsets), fo = fs + 1 == G.nsets ? 0 : fs + 1;
   const T* Hx = G.F[fo][3];
   const T* Hy = G.F[fo][4];
   const T* Hz = G.F[fo][5];
-  const long long ncell = (long long)G.nx * G.ny * G.nz;
   const int nn[3] = {G.nx, G.ny, G.nz};
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < ncell;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % G.nx), j = (int)((q / G.nx) % G.ny), k = (int)(q / ((long long)G.nx * G.ny));
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+  if (i < G.nx && j < G.ny) {
     const int p[3] = {i, j, k};
     const long long o = pidx3(i, j, k, G.px, G.ny);
     const int im = nbr(G, 0, i, -1), jm = nbr(G, 1, j, -1), km = nbr(G, 2, k, -1);
@@ -157,16 +154,18 @@ __global__ void __launch_bounds__(256) k_upml_e(const StepGrid<T>* __restrict__ 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_upml(const StepGrid<T>* g, const UpmlDev<T>& u, long long ncell, int offset, cudaStream_t st) {
-  const long long want = (ncell + 255) / 256;
-  const unsigned blocks = (unsigned)(want < 8192 ? (want > 0 ? want : 1) : 8192);
-  k_upml_h<T><<<blocks, 256, 0, st>>>(g, u, offset);
-  k_upml_e<T><<<blocks, 256, 0, st>>>(g, u, offset);
+cudaError_t launch_upml(const StepGrid<T>* g, const UpmlDev<T>& u, int nx, int ny, int nz, int offset,
+                        cudaStream_t st) {
+  // one thread per node: blocks of 32 x 8 nodes of one plane
+  const dim3 block(32, 8, 1), grid((unsigned)((nx + 31) / 32), (unsigned)((ny + 7) / 8), (unsigned)nz);
+  k_upml_h<T><<<grid, block, 0, st>>>(g, u, offset);
+  k_upml_e<T><<<grid, block, 0, st>>>(g, u, offset);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_upml<float>(const StepGrid<float>*, const UpmlDev<float>&, long long, int, cudaStream_t);
-template cudaError_t launch_upml<double>(const StepGrid<double>*, const UpmlDev<double>&, long long, int,
+template cudaError_t launch_upml<float>(const StepGrid<float>*, const UpmlDev<float>&, int, int, int, int,
+                                        cudaStream_t);
+template cudaError_t launch_upml<double>(const StepGrid<double>*, const UpmlDev<double>&, int, int, int, int,
                                          cudaStream_t);
 
 }  // namespace fdtd
