@@ -318,19 +318,22 @@ def timed_workload(args, specs, world, dist, steps, warmup, sample_clocks=True):
 
 
 def recorded_traffic(args, workload, rec):
-    """DRAM bytes of one step launch from the ncu capture of this workload in
-    profiles/, when it was taken on the grid size, kernel and launch shape
-    this run uses; else None."""
+    """DRAM bytes of one step launch from the ncu captures of this workload in
+    profiles/ (one record, or a list of them), when one was taken on the grid
+    size, kernel and launch shape this run uses; else None."""
     prof = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
     if not os.path.exists(prof):
         return None
     with open(prof) as f:
-        tr = json.load(f)
+        captures = json.load(f)
+    if isinstance(captures, dict):
+        captures = [captures]
     zd = rec["tune"]["zdepth"] if rec["tune"] else args.zdepth
     od = ["costliest", "z"][rec["tune"]["order"]] if rec["tune"] else (args.order or "costliest")
-    if rec["n_kernels"] == 1 and tr.get("kernel") == rec["kname"] and tr.get("tile") == rec["tiles"][0] \
-            and tr.get("zdepth") == zd and tr.get("order", "costliest") == od and tr.get("cells") == rec["cells"]:
-        return tr.get("dram_bytes_per_launch")
+    for tr in captures:
+        if rec["n_kernels"] == 1 and tr.get("kernel") == rec["kname"] and tr.get("tile") == rec["tiles"][0] \
+                and tr.get("zdepth") == zd and tr.get("order", "costliest") == od and tr.get("cells") == rec["cells"]:
+            return tr.get("dram_bytes_per_launch")
     return None
 
 

@@ -53,3 +53,33 @@ def test_roofline_peak_is_the_measured_copy_bandwidth():
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
         hbm = float(json.load(f)["hbm_gbs"])
     assert bench.measured_peaks() == (hbm, "measured")
+
+
+def test_recorded_traffic_matches_the_capture_of_the_run_shape(tmp_path, monkeypatch):
+    (tmp_path / "profiles").mkdir()
+    caps = [{"kernel": "k_step_tma", "tile": [32, 8], "zdepth": 8, "order": "costliest", "cells": 1000,
+             "dram_bytes_per_launch": 111},
+            {"kernel": "k_step_tma", "tile": [32, 8], "zdepth": 0, "order": "costliest", "cells": 1000,
+             "dram_bytes_per_launch": 222}]
+    (tmp_path / "profiles" / "traffic_w.json").write_text(json.dumps(caps))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+
+    class Args:
+        zdepth = 0
+        order = ""
+
+    def rec(kname="k_step_tma", tile=(32, 8), zdepth=0, order=0, cells=1000, n_kernels=1):
+        return {"tune": {"zdepth": zdepth, "order": order}, "n_kernels": n_kernels, "kname": kname,
+                "tiles": [list(tile)], "cells": cells}
+
+    assert bench.recorded_traffic(Args, "w", rec()) == 222
+    assert bench.recorded_traffic(Args, "w", rec(zdepth=8)) == 111
+    assert bench.recorded_traffic(Args, "w", rec(zdepth=16)) is None      # no capture of that shape
+    assert bench.recorded_traffic(Args, "w", rec(order=1)) is None        # another item order
+    assert bench.recorded_traffic(Args, "w", rec(cells=999)) is None      # another grid size
+    assert bench.recorded_traffic(Args, "w", rec(kname="k_step_pair")) is None
+    assert bench.recorded_traffic(Args, "w", rec(n_kernels=2)) is None    # two kernels: no single figure
+    assert bench.recorded_traffic(Args, "none", rec()) is None            # no capture file
+    # a single record (not a list) still works
+    (tmp_path / "profiles" / "traffic_w.json").write_text(json.dumps(caps[0]))
+    assert bench.recorded_traffic(Args, "w", rec(zdepth=8)) == 111
