@@ -703,21 +703,28 @@ __global__ void __launch_bounds__(256) k_observe(const ObsGrid<T>* __restrict__ 
   const T* H1b = G.F[fo][3 + d1];
   const T* H2a = G.F[fs][3 + d2];
   const T* H2b = G.F[fo][3 + d2];
+  // element strides of the plane normal and the two transverse axes
+  auto stride = [&](int ax) -> long long { return ax == 0 ? 1LL : (ax == 1 ? (long long)px : (long long)px * ny); };
+  const long long sd = stride(d), s1 = stride(d1), s2 = stride(d2);
+  const long long base = (long long)p * sd + (long long)u0 * s1 + (long long)v0 * s2;
+  // consecutive threads take consecutive x (the fastest memory axis) when x
+  // is transverse, else consecutive y (x-normal planes: rows one pitch apart)
+  const bool ufast = (d1 == 0) || (d == 0);
+  const bool small = total < 0x7fffffffLL;  // face numbers fit 32 bits (every grid that fits in memory)
   double acc = 0.0;
   for (long long q = beg + threadIdx.x; q < end; q += blockDim.x) {
-    // consecutive threads take consecutive x (the fastest memory axis) when x
-    // is transverse, else consecutive y (x-normal planes: rows one pitch apart)
-    const bool ufast = (d1 == 0) || (d == 0);
-    const int u = u0 + (int)(ufast ? q % nu : q / nv), v = v0 + (int)(ufast ? q / nu : q % nv);
-    int c[3];
-    auto at = [&](int pp, int uu, int vv) {
-      c[d] = pp;
-      c[d1] = uu;
-      c[d2] = vv;
-      return pidx3(c[0], c[1], c[2], px, ny);
-    };
-    const long long a = at(p, u, v), av = at(p, u, v + 1), au = at(p, u + 1, v);
-    const long long b = at(p - 1, u, v), bv = at(p - 1, u, v + 1), bu = at(p - 1, u + 1, v);
+    int du, dv;
+    if (small) {
+      const unsigned qq = (unsigned)q;
+      du = (int)(ufast ? qq % (unsigned)nu : qq / (unsigned)nv);
+      dv = (int)(ufast ? qq / (unsigned)nu : qq % (unsigned)nv);
+    } else {
+      du = (int)(ufast ? q % nu : q / nv);
+      dv = (int)(ufast ? q / nu : q % nv);
+    }
+    // node (p, u, v) of the plane and its +v, +u and -normal neighbours
+    const long long a = base + (long long)du * s1 + (long long)dv * s2, av = a + s2, au = a + s1;
+    const long long b = a - sd, bv = b + s2, bu = b + s1;
     const T e1 = T(0.5) * (E1[a] + E1[av]);
     const T e2 = T(0.5) * (E2[a] + E2[au]);
     const T h2 = T(0.25) * (T(0.5) * (H2a[b] + H2b[b]) + T(0.5) * (H2a[a] + H2b[a]) +
