@@ -106,10 +106,10 @@ typedef struct fdtd_grid_desc {
 } fdtd_grid_desc;
 
 /* Create a grid: allocates the Yee fields (three sets of the six components:
- * a grid frozen on the paired kernel cycles through all three so the
- * observation of a step can run beside the next one, other grids through
- * two), the material bytes, the CPML auxiliary slabs and the recorders, all
- * zeroed.
+ * a grid frozen on a TMA-staged kernel, paired or not, cycles through all
+ * three so the observation of a step can overlap the next one, other grids
+ * through two), the material bytes, the CPML auxiliary slabs and the
+ * recorders, all zeroed.
  * The material starts as background class everywhere.
  * Errors: E_INVAL (sizes, npml on a periodic axis, npml >= axis length),
  * E_NOMEM, E_CUDA. */

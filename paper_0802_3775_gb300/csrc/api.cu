@@ -636,9 +636,9 @@ struct GridImpl final : GridBase {
         return cuda_error(e, "memset counters");
     }
     const int r = replan();
-    // a grid frozen on the paired kernel cycles through three field sets, so
-    // its observation can run beside the next step (set once, at step 0)
-    if (r == FDTD_OK && steps == 0) sg.nsets = og.nsets = use_pair ? 3 : 2;
+    // a grid frozen on a TMA-staged kernel cycles through three field sets,
+    // so its observation can overlap the next step (set once, at step 0)
+    if (r == FDTD_OK && steps == 0) sg.nsets = og.nsets = use_tma ? 3 : 2;
     return r == FDTD_OK ? upload_tables() : r;
   }
 
@@ -699,8 +699,12 @@ struct GridImpl final : GridBase {
     }
     n = std::min(n, std::max(0LL, step_limit - steps));
     long long done = 0;
-    // observation beside the next step's launch (paired kernel), else in line
+    // observation beside the next step's launch (paired kernel), else in line;
+    // in line on three field sets, the TMA kernel's blocks of step s+1 start
+    // while the observation of step s still runs (it reads sets s%3 and
+    // (s+1)%3, step s+1 writes the third)
     const bool beside = use_pair && sg.nsets == 3 && !oitems.empty();
+    const bool overlap = !beside && use_tma && !use_pair && sg.nsets == 3 && !oitems.empty() && !centred_gain();
     if (beside && (e = obs.ensure()) != cudaSuccess) return cuda_error(e, "observation stream");
     while (done < n) {
       const int chunk = (int)std::min<long long>(n - done, 1 << 20);
@@ -714,7 +718,8 @@ struct GridImpl final : GridBase {
           e = launch_step_pair(reinterpret_cast<const StepGrid<float>*>(d_sg), d_tma, d_items, (int)items.size(), s,
                                tile_oy, cell_gain(), grid_blocks, stream);
         else if (use_tma)
-          e = launch_step_tma<T>(d_sg, d_tma, d_items, (int)items.size(), s, tile_oy, cell_gain(), grid_blocks, stream);
+          e = launch_step_tma<T>(d_sg, d_tma, d_items, (int)items.size(), s, tile_oy, cell_gain(), grid_blocks, stream,
+                                 !(overlap && s > 0 && !ev.first));
         else
           e = launch_step<T>(d_sg, d_items, (int)items.size(), s, bx, by_eff, cell_gain(), grid_blocks, stream);
         if (e != cudaSuccess) return cuda_error(e, "step kernel");

@@ -77,7 +77,8 @@ struct LaunchTimer {
 // its two resident blocks per SM); beside the TMA kernel, whose four blocks
 // per SM fill the register file, the observation blocks took step blocks'
 // places and the step ran slower than with the observation in line (140^3
-// gain grid 0.1227 -> 0.1260 ms per step, measured).
+// gain grid 0.1227 -> 0.1260 ms per step, measured).  There the observation
+// stays in line and the next step's blocks start without waiting for it.
 struct ObsOverlap {
   cudaStream_t side = nullptr;
   cudaEvent_t stepped = nullptr, done[2] = {nullptr, nullptr};

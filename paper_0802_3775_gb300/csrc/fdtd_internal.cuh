@@ -131,9 +131,11 @@ template <typename T>
 cudaError_t launch_step(const StepGrid<T>* grids, const int4* items, int nitems, int offset, int bx, int by,
                         bool gain, int grid_blocks, cudaStream_t st);
 
+// wait_prev false: the launch before it is the observation of the step before
+// on a grid of three field sets, and its blocks start without waiting for it.
 template <typename T>
 cudaError_t launch_step_tma(const StepGrid<T>* grids, const TmaGrid* maps, const int4* items, int nitems, int offset,
-                            int oy, bool gain, int grid_blocks, cudaStream_t st);
+                            int oy, bool gain, int grid_blocks, cudaStream_t st, bool wait_prev = true);
 
 template <typename T>
 size_t step_tma_smem_bytes(int oy);

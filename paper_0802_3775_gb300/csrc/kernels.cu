@@ -309,7 +309,7 @@ struct TmaThreads {
 template <typename T, bool GAIN, int OY>
 __global__ void __launch_bounds__(TmaThreads<T, OY>::NT, TmaThreads<T, OY>::MIN_BLOCKS)
     k_step_tma(const StepGrid<T>* __restrict__ grids, const TmaGrid* __restrict__ maps,
-               const int4* __restrict__ items, int nitems, int offset) {
+               const int4* __restrict__ items, int nitems, int offset, int wait_prev) {
   using L = TmaLayout<T, OY>;
   constexpr int OX = kTmaOX;
   constexpr int S = kTmaStages;
@@ -337,8 +337,12 @@ __global__ void __launch_bounds__(TmaThreads<T, OY>::NT, TmaThreads<T, OY>::MIN_
     for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
     fence_mbar_init();
   }
-  // the launch before this one (observation or step) has finished
-  grid_dependency_wait();
+  // the launch before this one (observation or step) has finished; after the
+  // observation of the step before (wait_prev 0) the block starts at once:
+  // that observation began after the step it observes had finished, and on
+  // three field sets it reads neither the set this step writes nor anything
+  // else this step touches
+  if (wait_prev) grid_dependency_wait();
   allow_dependents();
   __syncthreads();
 
@@ -627,25 +631,25 @@ int step_blocks_per_sm(bool tma, bool gain, int bx, int by) {
 
 template <typename T, bool GAIN, int OY>
 static cudaError_t launch_tma_variant(const StepGrid<T>* grids, const TmaGrid* maps, const int4* items, int nitems,
-                                      int offset, int blocks, cudaStream_t st) {
+                                      int offset, int blocks, bool wait_prev, cudaStream_t st) {
   const size_t smem = TmaLayout<T, OY>::total;
   cudaError_t e = cudaFuncSetAttribute(k_step_tma<T, GAIN, OY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return launch_programmatic(k_step_tma<T, GAIN, OY>, dim3(blocks), dim3(kTmaOX, TmaThreads<T, OY>::ROWS), smem, st,
-                             grids, maps, items, nitems, offset);
+                             grids, maps, items, nitems, offset, wait_prev ? 1 : 0);
 }
 
 template <typename T>
 cudaError_t launch_step_tma(const StepGrid<T>* grids, const TmaGrid* maps, const int4* items, int nitems, int offset,
-                            int oy, bool gain, int grid_blocks, cudaStream_t st) {
+                            int oy, bool gain, int grid_blocks, cudaStream_t st, bool wait_prev) {
   if (nitems <= 0) return cudaSuccess;
   const int blocks = (grid_blocks > 0 && grid_blocks < nitems) ? grid_blocks : nitems;
   if (oy == 4)
-    return gain ? launch_tma_variant<T, true, 4>(grids, maps, items, nitems, offset, blocks, st)
-                : launch_tma_variant<T, false, 4>(grids, maps, items, nitems, offset, blocks, st);
+    return gain ? launch_tma_variant<T, true, 4>(grids, maps, items, nitems, offset, blocks, wait_prev, st)
+                : launch_tma_variant<T, false, 4>(grids, maps, items, nitems, offset, blocks, wait_prev, st);
   if (oy == 8)
-    return gain ? launch_tma_variant<T, true, 8>(grids, maps, items, nitems, offset, blocks, st)
-                : launch_tma_variant<T, false, 8>(grids, maps, items, nitems, offset, blocks, st);
+    return gain ? launch_tma_variant<T, true, 8>(grids, maps, items, nitems, offset, blocks, wait_prev, st)
+                : launch_tma_variant<T, false, 8>(grids, maps, items, nitems, offset, blocks, wait_prev, st);
   return cudaErrorInvalidValue;
 }
 
@@ -976,7 +980,7 @@ cudaError_t launch_from_double(const double* src, T* dst, long long n, cudaStrea
   template cudaError_t launch_step<T>(const StepGrid<T>*, const int4*, int, int, int, int, bool, int,         \
                                       cudaStream_t);                                                           \
   template cudaError_t launch_step_tma<T>(const StepGrid<T>*, const TmaGrid*, const int4*, int, int, int, bool, \
-                                          int, cudaStream_t);                                                  \
+                                          int, cudaStream_t, bool);                                            \
   template cudaError_t launch_observe<T>(const ObsGrid<T>*, const int4*, int, int, cudaStream_t);             \
   template cudaError_t launch_advance<T>(StepGrid<T>*, ObsGrid<T>*, int, int, cudaStream_t);                  \
   template cudaError_t launch_gain_init<T>(const StepGrid<T>*, long long, T, T, T, cudaStream_t);             \

@@ -188,6 +188,29 @@ def test_observation_beside_the_step_equals_observation_in_line():
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("with_gain", [False, True])
+def test_tma_steps_overlapping_the_observation_equal_single_step_calls(with_gain):
+    """On the TMA kernel the blocks of step s+1 start while the in-line
+    observation of step s still runs (three field sets); the first step of
+    each call waits for everything before it.  200 steps in one call and 200
+    calls of one step give the same probes, flux series, fields, energy and
+    gain state, bit for bit."""
+    gain = inputs.GainSpec(pump=5e11, noise_amp=1e-3, init="ground") if with_gain else None
+    spec = _ragged_spec(gain)
+    runs = []
+    for calls in [[200], [1] * 200]:
+        g = gpu_grid(spec)
+        g.set_kernel("tma")
+        for n in calls:
+            g.step(n)
+        r = [g.read_probes(), g.read_flux(), g.read_fields(), np.array([g.field_energy()])]
+        if with_gain:
+            r += [g.read_gain(0), g.read_gain(3)]
+        runs.append(r)
+    for a, b in zip(runs[0], runs[1]):
+        assert np.array_equal(a, b)
+
+
 def test_paired_kernel_matches_oracle_on_ragged_grid():
     gain = inputs.GainSpec(pump=5e11, noise_amp=1e-3, init="ground")
     spec = _ragged_spec(gain)
