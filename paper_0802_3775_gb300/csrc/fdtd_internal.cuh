@@ -13,7 +13,7 @@ namespace fdtd {
 constexpr int kMaxSrc = 8;
 constexpr int kMaxProbes = 64;
 constexpr int kMaxFlux = 16;
-constexpr int kMaxFluxParts = 1024;  // blocks per flux plane (256 faces each)
+constexpr int kMaxFluxParts = 1024;  // most blocks of one flux plane
 constexpr int kEnergyBlocks = 256;
 #ifndef FDTD_TMA_STAGES
 #define FDTD_TMA_STAGES 3
