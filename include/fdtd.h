@@ -262,6 +262,17 @@ int fdtd_set_absorber(fdtd_grid* g, int32_t absorber);
  * identical results. */
 int fdtd_set_kernel(fdtd_grid* g, int32_t kind);
 
+/* Persisting L2 window of the CPML memory: on = 1 (the default) keeps the
+ * grid's CPML auxiliary arrays in a persisting L2 window on the grid's
+ * stream from its first step on.  It raises the context's persisting-L2
+ * set-aside (cudaLimitPersistingL2CacheSize) to the arrays' size, at most the
+ * device's maximum, and replaces any access-policy window the caller set on
+ * that stream; a grid destroyed or switched off (on = 0) clears the window and
+ * returns persisting lines to normal.  A cache placement of this library, no
+ * counterpart in the paper: no result changes.  Grids stepped by a batch or a
+ * server do not use it.  E_INVAL for another value. */
+int fdtd_set_l2_residency(fdtd_grid* g, int32_t on);
+
 /* The step kernel the grid's launches use under its current settings
  * (1 plain, 2 TMA, 3 paired, 4 the UPML launches), and the rows of its tile (*rows: the tile of
  * owned columns is 32 x rows for kinds 2 and 3, (bx-1) x (by-1) for kind 1).

@@ -336,6 +336,18 @@ int fdtd_set_kernel(fdtd_grid* g, int32_t kind) {
   });
 }
 
+int fdtd_set_l2_residency(fdtd_grid* g, int32_t on) {
+  return guarded([&]() -> int {
+    CHECK_GRID(g);
+    if (on != 0 && on != 1) return set_error(FDTD_E_INVAL, "L2 residency must be 0 or 1");
+    G->l2_resident = on;
+    if (!G->finalized) return FDTD_OK;  // applied at the first step
+    cudaError_t e = cudaStreamSynchronize(G->stream);
+    if (e != cudaSuccess) return fdtd::cuda_error(e, "sync");
+    return G->apply_l2_window(on != 0);
+  });
+}
+
 int fdtd_kernel_in_use(fdtd_grid* g, int32_t* kind, int32_t* rows) {
   return guarded([&]() -> int {
     CHECK_GRID(g);

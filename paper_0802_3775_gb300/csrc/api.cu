@@ -699,10 +699,61 @@ struct GridImpl final : GridBase {
     return FDTD_OK;
   }
 
+  // The CPML memory (a few per cent of the state, but read and written at
+  // latency-critical points of the slab planes) in a persisting L2 window on
+  // the grid's stream: the device's persisting set-aside is raised to its
+  // size (at most the device's maximum) and the window's hit ratio scaled to
+  // what fits.  Measured on the 184^3 passive grid 0.1126 -> 0.1098 ms per
+  // step, on the 140^3 lasing grid 0.1229 -> 0.1210 ms.
+  int apply_l2_window(bool on) override {
+    if (!d_psi || on == l2_applied) return FDTD_OK;
+    cudaError_t e;
+    cudaStreamAttrValue a{};
+    if (on) {
+      int dev = 0, max_persist = 0, max_window = 0;
+      if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+          (e = cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev)) != cudaSuccess ||
+          (e = cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev)) != cudaSuccess)
+        return cuda_error(e, "L2 attributes");
+      if (max_persist <= 0 || max_window <= 0) return FDTD_OK;  // no persisting L2 on this device
+      const size_t bytes = std::min(sizeof(T) * psi_words, (size_t)max_window);
+      size_t limit = 0;
+      if ((e = cudaDeviceGetLimit(&limit, cudaLimitPersistingL2CacheSize)) != cudaSuccess)
+        return cuda_error(e, "L2 persisting limit");
+      const size_t want = std::min(bytes, (size_t)max_persist);
+      if (limit < want && (e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want)) != cudaSuccess)
+        return cuda_error(e, "L2 persisting limit");
+      a.accessPolicyWindow.base_ptr = d_psi;
+      a.accessPolicyWindow.num_bytes = bytes;
+      a.accessPolicyWindow.hitRatio = std::min(1.0f, (float)std::max(limit, want) / (float)bytes);
+      a.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+      a.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    } else {
+      a.accessPolicyWindow.num_bytes = 0;  // no window
+    }
+    if ((e = cudaStreamSetAttribute(stream, cudaStreamAttributeAccessPolicyWindow, &a)) != cudaSuccess)
+      return cuda_error(e, "L2 access policy window");
+    if (!on) cudaCtxResetPersistingL2Cache();  // its lines back to normal
+    l2_applied = on;
+    return FDTD_OK;
+  }
+
+  ~GridImpl() override {
+    if (l2_applied) {
+      cudaStreamSynchronize(stream);
+      apply_l2_window(false);
+      cudaGetLastError();
+    }
+  }
+
   int step(long long n) override {
     cudaError_t e;
     if (tables_dirty) {
       const int r = upload_tables();
+      if (r != FDTD_OK) return r;
+    }
+    if (l2_resident && !l2_applied) {
+      const int r = apply_l2_window(true);
       if (r != FDTD_OK) return r;
     }
     n = std::min(n, std::max(0LL, step_limit - steps));

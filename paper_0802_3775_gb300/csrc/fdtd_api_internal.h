@@ -143,9 +143,14 @@ struct GridBase {
   int coupling = 0;                              // FDTD_COUPLING_CELL or FDTD_COUPLING_CENTRED
   int item_order = 0;                            // FDTD_ORDER_COSTLIEST or FDTD_ORDER_Z
   int absorber = 0;                              // FDTD_ABSORBER_CPML or FDTD_ABSORBER_UPML
+  int l2_resident = 1;                           // keep the CPML memory in a persisting L2 window
+  bool l2_applied = false;                       // the window is set on the grid's stream
   virtual int kernel_in_use_kind() const { return 0; }
   bool tables_dirty = false;                     // device records stale (stepped by a batch)
 
+  // Set (on) or clear (off) the persisting L2 window of the CPML memory on
+  // the grid's stream; no-op for a grid without CPML memory.
+  virtual int apply_l2_window(bool on) { (void)on; return FDTD_OK; }
   virtual ~GridBase() { mem.release_all(); }
   virtual int precision() const = 0;
   virtual size_t word() const = 0;

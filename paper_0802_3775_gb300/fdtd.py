@@ -79,6 +79,7 @@ SIGNATURES = {
                             C.POINTER(C.c_int32)],
     "fdtd_set_launch": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
     "fdtd_set_kernel": [_P, C.c_int32],
+    "fdtd_set_l2_residency": [_P, C.c_int32],
     "fdtd_kernel_in_use": [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "fdtd_autotune": [_P, C.c_int32, C.POINTER(TuneResult)],
     "fdtd_batch_autotune": [_P, C.c_int32, C.POINTER(TuneResult)],
@@ -301,6 +302,10 @@ class Grid:
         3 paired TMA-staged kernel (binary32 grids)."""
         kinds = {"auto": 0, "plain": 1, "tma": 2, "pair": 3}
         check(self._lib.fdtd_set_kernel(self.h, int(kinds.get(kind, kind))))
+
+    def set_l2_residency(self, on):
+        """Keep the CPML memory in a persisting L2 window (default on)."""
+        check(self._lib.fdtd_set_l2_residency(self.h, 1 if on else 0))
 
     def autotune(self, trial_steps=10):
         """Time the candidate launch shapes from the current state (restored

@@ -64,7 +64,7 @@ def test_null_and_range_checks_without_gpu(lib):
     assert L.fdtd_version().startswith(b"fdtd-gb300")
     # the variant and launch options reject a null grid before looking at anything else
     for fn, arg in (("fdtd_set_gain_coupling", 1), ("fdtd_set_absorber", 1), ("fdtd_set_item_order", 1),
-                    ("fdtd_set_wait_limit", 0)):
+                    ("fdtd_set_wait_limit", 0), ("fdtd_set_l2_residency", 1)):
         assert getattr(L, fn)(None, arg) == -1, fn
         assert b"null" in L.fdtd_last_error()
     # the allocation-free energy checks its arguments before touching the device

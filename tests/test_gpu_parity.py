@@ -211,6 +211,30 @@ def test_tma_steps_overlapping_the_observation_equal_single_step_calls(with_gain
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("kernel", ["pair", "tma", "plain"])
+def test_l2_residency_changes_no_result(kernel):
+    """The persisting L2 window of the CPML memory is a cache placement: with
+    it (the default), without it, and switched off after 60 steps, the grid
+    gives the same fields, probes, flux and energy, bit for bit."""
+    gain = inputs.GainSpec(pump=5e11, noise_amp=1e-3, init="ground") if kernel == "tma" else None
+    spec = _ragged_spec(gain)
+    runs = []
+    for mode in ["on", "off", "switch"]:
+        g = gpu_grid(spec)
+        g.set_kernel(kernel)
+        if mode == "off":
+            g.set_l2_residency(False)
+        g.step(60)
+        if mode == "switch":
+            g.set_l2_residency(False)
+        g.step(60)
+        runs.append([g.read_fields(), g.read_probes(), g.read_flux(), np.array([g.field_energy()])])
+        g.close()
+    for other in runs[1:]:
+        for a, b in zip(other, runs[0]):
+            assert np.array_equal(a, b)
+
+
 def test_paired_kernel_matches_oracle_on_ragged_grid():
     gain = inputs.GainSpec(pump=5e11, noise_amp=1e-3, init="ground")
     spec = _ragged_spec(gain)
