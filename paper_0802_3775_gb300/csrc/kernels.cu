@@ -582,12 +582,22 @@ __global__ void __launch_bounds__(TmaThreads<T, OY>::NT, TmaThreads<T, OY>::MIN_
                         hz - sHz[oh - 1], hy - sHy[oh - 1], hx - sHx[oh - HW], eox, eoy, eoz, enx, eny, enz, &pre);
         // E^{n+1} and H~^{n+1/2} straight to set (n+1)%3 (a warp row: one contiguous segment)
         T* const* Fo = G.F[fo];
-        Fo[0][cidx] = enx;
-        Fo[1][cidx] = eny;
-        Fo[2][cidx] = enz;
-        Fo[3][cidx] = hx;
-        Fo[4][cidx] = hy;
-        Fo[5][cidx] = hz;
+        if (FDTD_STREAM_STORES) {
+          // no reader in this launch: the evict-first hint (see fdtd_internal.cuh)
+          __stcs(Fo[0] + cidx, enx);
+          __stcs(Fo[1] + cidx, eny);
+          __stcs(Fo[2] + cidx, enz);
+          __stcs(Fo[3] + cidx, hx);
+          __stcs(Fo[4] + cidx, hy);
+          __stcs(Fo[5] + cidx, hz);
+        } else {
+          Fo[0][cidx] = enx;
+          Fo[1][cidx] = eny;
+          Fo[2][cidx] = enz;
+          Fo[3][cidx] = hx;
+          Fo[4][cidx] = hy;
+          Fo[5][cidx] = hz;
+        }
       }
       hPx = hx;
       hPy = hy;

@@ -86,6 +86,19 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 #endif
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 __device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+// new field values: no reader in this launch (FDTD_STREAM_STORES: the evict-first hint)
+__device__ __forceinline__ void st2_out(float* p, float2 v) {
+  if (FDTD_STREAM_STORES)
+    __stcs(reinterpret_cast<float2*>(p), v);
+  else
+    st2(p, v);
+}
+__device__ __forceinline__ void st1_out(float* p, float v) {
+  if (FDTD_STREAM_STORES)
+    __stcs(p, v);
+  else
+    *p = v;
+}
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 
 // CPML memory of the planes ahead staged per thread by cp.async (1), or read
@@ -919,19 +932,19 @@ __global__ void __launch_bounds__(PairThreads<OY, RY>::NT, pair_min_blocks<GAIN,
             const long long cidx = (long long)pc[r].j * px + pc[r].i0 + (long long)k * pstride;
             float* const* Fo = G.F[fo];
             if (pc[r].own1) {
-              st2(Fo[0] + cidx, enx);
-              st2(Fo[1] + cidx, eny);
-              st2(Fo[2] + cidx, enz);
-              st2(Fo[3] + cidx, hx[r]);
-              st2(Fo[4] + cidx, hy[r]);
-              st2(Fo[5] + cidx, hz[r]);
+              st2_out(Fo[0] + cidx, enx);
+              st2_out(Fo[1] + cidx, eny);
+              st2_out(Fo[2] + cidx, enz);
+              st2_out(Fo[3] + cidx, hx[r]);
+              st2_out(Fo[4] + cidx, hy[r]);
+              st2_out(Fo[5] + cidx, hz[r]);
             } else {
-              Fo[0][cidx] = enx.x;
-              Fo[1][cidx] = eny.x;
-              Fo[2][cidx] = enz.x;
-              Fo[3][cidx] = hx[r].x;
-              Fo[4][cidx] = hy[r].x;
-              Fo[5][cidx] = hz[r].x;
+              st1_out(Fo[0] + cidx, enx.x);
+              st1_out(Fo[1] + cidx, eny.x);
+              st1_out(Fo[2] + cidx, enz.x);
+              st1_out(Fo[3] + cidx, hx[r].x);
+              st1_out(Fo[4] + cidx, hy[r].x);
+              st1_out(Fo[5] + cidx, hz[r].x);
             }
           }
         }
