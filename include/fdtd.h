@@ -264,13 +264,14 @@ int fdtd_set_kernel(fdtd_grid* g, int32_t kind);
 
 /* Persisting L2 window of the CPML memory: on = 1 (the default) keeps the
  * grid's CPML auxiliary arrays in a persisting L2 window on the grid's
- * stream from its first step on.  It raises the context's persisting-L2
- * set-aside (cudaLimitPersistingL2CacheSize) to the arrays' size, at most the
- * device's maximum, and replaces any access-policy window the caller set on
- * that stream; a grid destroyed or switched off (on = 0) clears the window and
- * returns persisting lines to normal.  A cache placement of this library, no
- * counterpart in the paper: no result changes.  Grids stepped by a batch or a
- * server do not use it.  E_INVAL for another value. */
+ * stream while it steps.  One grid per device holds the window at a time:
+ * the one that stepped alone most recently (another grid's step, a batch's
+ * step, switching it off or destroying the grid clears the window and returns
+ * its lines to normal).  It raises the context's persisting-L2 set-aside
+ * (cudaLimitPersistingL2CacheSize) to the arrays' size, at most the device's
+ * maximum, and replaces any access-policy window the caller set on that
+ * stream.  A cache placement of this library, no counterpart in the paper:
+ * no result changes.  E_INVAL for another value. */
 int fdtd_set_l2_residency(fdtd_grid* g, int32_t on);
 
 /* The step kernel the grid's launches use under its current settings

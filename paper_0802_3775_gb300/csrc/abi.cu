@@ -341,10 +341,11 @@ int fdtd_set_l2_residency(fdtd_grid* g, int32_t on) {
     CHECK_GRID(g);
     if (on != 0 && on != 1) return set_error(FDTD_E_INVAL, "L2 residency must be 0 or 1");
     G->l2_resident = on;
-    if (!G->finalized) return FDTD_OK;  // applied at the first step
+    if (on) return FDTD_OK;  // taken at the grid's next step
     cudaError_t e = cudaStreamSynchronize(G->stream);
     if (e != cudaSuccess) return fdtd::cuda_error(e, "sync");
-    return G->apply_l2_window(on != 0);
+    fdtd::l2_forget(G);
+    return FDTD_OK;
   });
 }
 

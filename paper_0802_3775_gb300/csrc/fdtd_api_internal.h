@@ -205,6 +205,14 @@ struct GridBase {
   }
 };
 
+// The device's persisting L2 set-aside serves one grid at a time: the grid
+// stepping alone most recently on that device, if it keeps its CPML memory in
+// L2.  l2_claim(g) hands it to g (clearing the previous holder's window and
+// returning its lines to normal); l2_claim(nullptr) releases it (a batch
+// steps, or a grid switches the option off); l2_forget(g) before g goes away.
+void l2_claim(GridBase* g);
+void l2_forget(GridBase* g);
+
 GridBase* make_grid(const fdtd_grid_desc& d);
 int init_grid(GridBase* g);
 

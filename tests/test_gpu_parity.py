@@ -235,6 +235,36 @@ def test_l2_residency_changes_no_result(kernel):
             assert np.array_equal(a, b)
 
 
+def test_l2_window_passes_between_grids_and_batches():
+    """Two grids stepped in turn take the persisting L2 window from each
+    other, a batch step releases it, and a destroyed holder gives it back:
+    each grid's results equal those of the same grid stepped with the window
+    off, bit for bit."""
+    from paper_0802_3775_gb300.fdtd import Batch
+    spec_a = _ragged_spec(None)
+    spec_b = small_opal(precision="f32", source="dipole", seed=5)
+    ref = {}
+    for name, spec in (("a", spec_a), ("b", spec_b)):
+        g = gpu_grid(spec)
+        g.set_l2_residency(False)
+        g.step(90)
+        ref[name] = [g.read_fields(), g.read_probes(), g.read_flux()]
+        g.close()
+    a, b, c = gpu_grid(spec_a), gpu_grid(spec_b), gpu_grid(spec_b)
+    batch = Batch([c])
+    for n in [30, 30]:
+        a.step(n)
+        b.step(n)
+        batch.step(5)
+    a.step(30)
+    a.close()  # the holder goes away
+    b.step(30)
+    assert all(np.array_equal(x, y) for x, y in zip([b.read_fields(), b.read_probes(), b.read_flux()], ref["b"]))
+    a2 = gpu_grid(spec_a)
+    a2.step(90)
+    assert all(np.array_equal(x, y) for x, y in zip([a2.read_fields(), a2.read_probes(), a2.read_flux()], ref["a"]))
+
+
 def test_paired_kernel_matches_oracle_on_ragged_grid():
     gain = inputs.GainSpec(pump=5e11, noise_amp=1e-3, init="ground")
     spec = _ragged_spec(gain)
