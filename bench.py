@@ -248,7 +248,9 @@ def timed_workload(args, specs, world, dist, steps, warmup, sample_clocks=True):
     tune = None
     if not args.no_autotune and args.kernel == "auto" and not args.by and not args.zdepth and not args.order:
         # launch shape picked by timing the candidates on this workload (state restored)
-        tune = stepper.autotune(trial_steps=10 if len(grids) == 1 else 4)
+        # trials long enough that run-to-run noise does not pick the shape
+        # (single grids: 12 shapes x 42 steps, about 60 ms on the 184^3 grid)
+        tune = stepper.autotune(trial_steps=40 if len(grids) == 1 else 8)
     stepper.step(warmup)
     stepper.sync()
 
