@@ -758,7 +758,7 @@ struct GridImpl final : GridBase {
       const int r = upload_tables();
       if (r != FDTD_OK) return r;
     }
-    if (l2_resident && !l2_applied) l2_claim(this);
+    if (l2_resident && !l2_applied && !stream_capturing(stream)) l2_claim(this);
     n = std::min(n, std::max(0LL, step_limit - steps));
     long long done = 0;
     // observation beside the next step's launch (paired kernel), else in line;
@@ -996,6 +996,15 @@ void l2_claim(GridBase* g) {
   owner = nullptr;
   if (g && g->apply_l2_window(true) == FDTD_OK && g->l2_applied) owner = g;
   cudaGetLastError();  // a cache placement: failures leave the grid without a window
+}
+
+bool stream_capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs != cudaStreamCaptureStatusNone;
 }
 
 void l2_forget(GridBase* g) {

@@ -275,7 +275,7 @@ struct BatchImpl final : BatchBase {
       const int r = build();
       if (r != FDTD_OK) return r;
     }
-    l2_claim(nullptr);  // no grid's CPML memory keeps L2 while the batch steps
+    if (!stream_capturing(stream)) l2_claim(nullptr);  // no grid's CPML memory keeps L2 while the batch steps
     long long done = 0;
     if (graph_steps > 0 && !timer.on && n >= graph_steps) {
       if (graph_built_for != graph_steps) {

@@ -212,6 +212,8 @@ struct GridBase {
 // steps, or a grid switches the option off); l2_forget(g) before g goes away.
 void l2_claim(GridBase* g);
 void l2_forget(GridBase* g);
+// The stream is capturing a graph (no limit or attribute change may happen then).
+bool stream_capturing(cudaStream_t st);
 
 GridBase* make_grid(const fdtd_grid_desc& d);
 int init_grid(GridBase* g);
